@@ -1,0 +1,203 @@
+"""CPU oracle for synchronous LP refinement under the (lambda-1) metric.
+
+TEST INFRASTRUCTURE ONLY: the plain sequential statement of what the CUDA path computes.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It shares no code with the CUDA library and never imports it.
+
+The arithmetic lives in ``hgp_oracle.c`` (definitions of Sec. 2, gain of Sec. 5, label
+propagation of Sec. 6 in the synchronous sub-round form); this module only builds it with
+gcc and marshals arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hgp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, portable flags).
+
+    ``HGP_ORACLE_LIB`` names an already built oracle library to use instead (the mutation
+    tests point it at deliberately broken copies)."""
+    if os.environ.get("HGP_ORACLE_LIB"):
+        return os.environ["HGP_ORACLE_LIB"]
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, f64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+        lib.oracle_create.restype = P
+        lib.oracle_create.argtypes = [i32, i32, P, P, P, P, i32, f64, P, i32, u64]
+        lib.oracle_destroy.argtypes = [P]
+        lib.oracle_refine.restype = ctypes.c_int
+        lib.oracle_refine.argtypes = [P, i32, P, P, i64, P]
+        lib.oracle_gain.restype = i64
+        lib.oracle_gain.argtypes = [P, i32, i32]
+        lib.oracle_candidates.argtypes = [P, i32, P, P]
+        lib.oracle_objective.restype = i64
+        lib.oracle_objective.argtypes = [P]
+        lib.oracle_lmax_of.restype = i64
+        lib.oracle_lmax_of.argtypes = [P]
+        lib.oracle_round_of.restype = i64
+        lib.oracle_round_of.argtypes = [P]
+        lib.oracle_lmax.restype = i64
+        lib.oracle_lmax.argtypes = [i64, i32, f64]
+        lib.oracle_mix64.restype = u64
+        lib.oracle_mix64.argtypes = [u64]
+        lib.oracle_subround_of.restype = i32
+        lib.oracle_subround_of.argtypes = [u64, i64, i32, i32]
+        for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
+            getattr(lib, name).argtypes = [P, P]
+        lib.oracle_sample_candidates.restype = ctypes.c_int
+        lib.oracle_sample_candidates.argtypes = [i32, i32, P, P, P, P, i32, f64, P, i32, u64,
+                                                 i32, i32, P, P, P]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _c(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def lmax(total_weight: int, k: int, eps: float) -> int:
+    return int(_load().oracle_lmax(int(total_weight), int(k), float(eps)))
+
+
+def mix64(x: int) -> int:
+    return int(_load().oracle_mix64(x))
+
+
+def subround_of(seed: int, rnd: int, u: int, S: int) -> int:
+    return int(_load().oracle_subround_of(seed, rnd, u, S))
+
+
+class Oracle:
+    """Sequential oracle state for one hypergraph and partition."""
+
+    def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None,
+                 subrounds: int = 4, seed: int = 0):
+        lib = _load()
+        self._lib = lib
+        self.n, self.m, self.k = int(n), int(m), int(k)
+        self.subrounds = int(subrounds)
+        self._keep = [_c(net_off, np.int64), _c(pins, np.int32), _c(vertex_w, np.int32),
+                      _c(net_w, np.int32), _c(part, np.int32)]
+        off, pn, vw, nw, pt = self._keep
+        self._h = lib.oracle_create(self.n, self.m, _ptr(off), _ptr(pn), _ptr(vw), _ptr(nw),
+                                    self.k, float(eps), _ptr(pt), self.subrounds, int(seed))
+        if not self._h:
+            raise ValueError("oracle_create rejected the input")
+        self._keep = None
+
+    @classmethod
+    def from_hypergraph(cls, hg, subrounds: int = 4, seed: int = 0, part=None):
+        return cls(hg.n, hg.m, hg.net_off, hg.pins, hg.k, hg.eps,
+                   hg.part if part is None else part, hg.vertex_w, hg.net_w, subrounds, seed)
+
+    def close(self):
+        if self._h:
+            self._lib.oracle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refine(self, rounds: int, log_moves: bool = False, max_moves: int = 1 << 20):
+        """Runs `rounds` rounds. Returns (stats [rounds x 5] int64, moves or None).
+
+        moves: int64 [count x 4] = (global sub-round index, u, from, to)."""
+        stats = np.zeros((rounds, len(STAT_FIELDS)), dtype=np.int64)
+        moves = np.zeros((max_moves, 4), dtype=np.int64) if log_moves else None
+        cnt = ctypes.c_int64(0)
+        rc = self._lib.oracle_refine(self._h, int(rounds), _ptr(stats), _ptr(moves),
+                                     int(max_moves if log_moves else 0), ctypes.byref(cnt))
+        if rc != 0:
+            raise MemoryError("oracle_refine failed")
+        if log_moves:
+            if cnt.value > max_moves:
+                raise ValueError("move log truncated")
+            moves = moves[:cnt.value].copy()
+        return stats, moves
+
+    def gain(self, u: int, i: int) -> int:
+        return int(self._lib.oracle_gain(self._h, int(u), int(i)))
+
+    def candidates(self, s: int):
+        t = np.zeros(self.n, dtype=np.int32)
+        g = np.zeros(self.n, dtype=np.int64)
+        self._lib.oracle_candidates(self._h, int(s), _ptr(t), _ptr(g))
+        return t, g
+
+    def objective(self) -> int:
+        return int(self._lib.oracle_objective(self._h))
+
+    @property
+    def lmax(self) -> int:
+        return int(self._lib.oracle_lmax_of(self._h))
+
+    @property
+    def round(self) -> int:
+        return int(self._lib.oracle_round_of(self._h))
+
+    def partition(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int32)
+        self._lib.oracle_get_partition(self._h, _ptr(out))
+        return out
+
+    def block_weights(self) -> np.ndarray:
+        out = np.zeros(self.k, dtype=np.int64)
+        self._lib.oracle_get_block_weights(self._h, _ptr(out))
+        return out
+
+    def phi(self) -> np.ndarray:
+        out = np.zeros((self.m, self.k), dtype=np.int64)
+        self._lib.oracle_get_phi(self._h, _ptr(out))
+        return out
+
+
+def sample_candidates(hg, sample, s: int = 0, subrounds: int = 4, seed: int = 0, part=None):
+    """Round-0 candidates (target, gain) of sub-round s for the distinct vertices `sample`,
+    computed from the input alone (no full Phi table)."""
+    lib = _load()
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    t = np.zeros(sample.size, dtype=np.int32)
+    g = np.zeros(sample.size, dtype=np.int64)
+    off, pn = _c(hg.net_off, np.int64), _c(hg.pins, np.int32)
+    vw, nw = _c(hg.vertex_w, np.int32), _c(hg.net_w, np.int32)
+    pt = _c(hg.part if part is None else part, np.int32)
+    rc = lib.oracle_sample_candidates(hg.n, hg.m, _ptr(off), _ptr(pn), _ptr(vw), _ptr(nw),
+                                      hg.k, float(hg.eps), _ptr(pt), int(subrounds), int(seed),
+                                      int(s), int(sample.size), _ptr(sample), _ptr(t), _ptr(g))
+    if rc != 0:
+        raise MemoryError("oracle_sample_candidates failed")
+    return t, g

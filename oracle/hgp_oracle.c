@@ -1,0 +1,400 @@
+/*
+ * CPU oracle for synchronous size-constrained label-propagation refinement under the
+ * connectivity (lambda-1) metric.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, sequential statement of what
+ * the CUDA path must compute.  Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it.  It shares no code, header, table or helper with the CUDA
+ * library, and it never reads anything the CUDA library produced.
+ *
+ * Everything is integer arithmetic (int64 pin counts, weights and gains), so results are
+ * exact and must agree bit for bit with the device path.
+ *
+ * Definitions followed (paper Sec. 2 "Preliminaries"):
+ *   H = (V, E, c, omega), positive integer weights; I(v) the incident nets of v.
+ *   k-way partition Pi : V -> {0..k-1} (the paper numbers blocks 1..k).
+ *   L_max = (1 + eps) * ceil(c(V) / k); read here as floor((1+eps)*ceil(c(V)/k)) computed
+ *   in IEEE double, since block weights are integers.
+ *   Phi(e, V_i) = |V_i intersect e|; Lambda(e) = {i : Phi(e,i) > 0}; lambda(e) = |Lambda(e)|.
+ *   (lambda - 1)(Pi) = sum_e (lambda(e) - 1) * omega(e); an empty net (lambda = 0) counts 0.
+ * Gain (Sec. 5, "Parallel Gain Calculation"):
+ *   g_i(u) = b(u) - p_i(u),  b(u) = omega({e in I(u) : Phi(e, Pi(u)) = 1}),
+ *                            p_i(u) = omega({e in I(u) : Phi(e, i) = 0}).
+ * Label propagation (Sec. 6), in the deterministic synchronous form:
+ *   round r: a vertex is eligible if it is the first round since creation, or if one of its
+ *   incident nets had a pin moved in round r-1 (the paper's "u and its neighbours").
+ *   The round is split into S sub-rounds; vertex u is active in sub-round
+ *   splitmix64_finalizer(seed ^ (r << 32 | u)) mod S.  In a sub-round, every active eligible
+ *   vertex picks the block with the highest positive gain whose weight (frozen at the start
+ *   of the sub-round) plus c(u) stays within L_max; ties go to the smaller block id.
+ *   Candidates are then approved per target block in (gain desc, vertex id asc) order while
+ *   the inclusive prefix of their weights fits into L_max - w(t).  All approved moves are
+ *   applied, Phi and the block weights are updated, and the objective is recomputed.
+ *
+ * Build: gcc -O2 -shared -fPIC -o liboracle.so hgp_oracle.c
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef struct {
+    /* hypergraph (copied) */
+    int32_t n, m, k;
+    int64_t *net_off;      /* [m+1] */
+    int32_t *pins;         /* [P]   */
+    int64_t *vw;           /* [n]   vertex weights c(v) */
+    int64_t *nw;           /* [m]   net weights omega(e) */
+    int64_t *vtx_off;      /* [n+1] incident-net lists I(v) */
+    int32_t *inc;          /* [P]   */
+    /* parameters */
+    int64_t lmax;
+    int32_t subrounds;
+    uint64_t seed;
+    /* state */
+    int32_t *part;         /* Pi */
+    int64_t *phi;          /* [m*k] Phi(e,i) */
+    int64_t *bw;           /* [k]  block weights c(V_i) */
+    int64_t round;         /* global round counter */
+    int all_eligible;      /* 1 until the first round has run */
+    uint8_t *moved_prev;   /* [m]  net had a pin moved in the previous round */
+    uint8_t *moved_cur;    /* [m]  net had a pin moved in the current round */
+    /* sub-round scratch */
+    int32_t *cand_t;       /* [n]  chosen target or -1 */
+    int64_t *cand_g;       /* [n]  its gain */
+    uint8_t *approved;     /* [n]  */
+    int32_t *order;        /* [n]  */
+} oracle_t;
+
+/* Per-round statistics, in this order: objective after the round, number of candidates,
+ * number of approved moves, number of eligible vertices, heaviest block weight. */
+enum { ST_OBJ = 0, ST_CAND, ST_APPROVED, ST_ELIGIBLE, ST_MAXW, ST_COUNT };
+
+int64_t oracle_lmax(int64_t total_weight, int32_t k, double eps)
+{
+    int64_t avg = (total_weight + k - 1) / k;             /* ceil(c(V)/k), Sec. 2 */
+    return (int64_t)floor((1.0 + eps) * (double)avg);
+}
+
+/* SplitMix64 output function (Steele, Lea, Flood: "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014). */
+uint64_t oracle_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* Sub-round of vertex u in round r: mix64(seed ^ (r << 32 | u)) mod S. */
+int32_t oracle_subround_of(uint64_t seed, int64_t round, int32_t u, int32_t S)
+{
+    uint64_t z = oracle_mix64(seed ^ (((uint64_t)round << 32) | (uint64_t)(uint32_t)u));
+    return (int32_t)(z % (uint64_t)S);
+}
+
+static int64_t objective_from_phi(const oracle_t *o)
+{
+    int64_t obj = 0;
+    for (int32_t e = 0; e < o->m; ++e) {
+        int64_t lambda = 0;
+        for (int32_t i = 0; i < o->k; ++i)
+            if (o->phi[(int64_t)e * o->k + i] > 0) lambda++;
+        if (lambda > 0) obj += (lambda - 1) * o->nw[e];
+    }
+    return obj;
+}
+
+void oracle_destroy(oracle_t *o)
+{
+    if (!o) return;
+    free(o->net_off); free(o->pins); free(o->vw); free(o->nw); free(o->vtx_off);
+    free(o->inc); free(o->part); free(o->phi); free(o->bw); free(o->moved_prev);
+    free(o->moved_cur); free(o->cand_t); free(o->cand_g); free(o->approved); free(o->order);
+    free(o);
+}
+
+/* Returns NULL on allocation failure or invalid input. vertex_w / net_w may be NULL
+ * (unit weights).  part is copied. */
+oracle_t *oracle_create(int32_t n, int32_t m, const int64_t *net_off, const int32_t *pins,
+                        const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+                        const int32_t *part, int32_t subrounds, uint64_t seed)
+{
+    if (n < 0 || m < 0 || k < 2 || subrounds < 1) return NULL;
+    oracle_t *o = (oracle_t *)calloc(1, sizeof(oracle_t));
+    if (!o) return NULL;
+    int64_t P = net_off[m];
+    o->n = n; o->m = m; o->k = k; o->subrounds = subrounds; o->seed = seed;
+    o->net_off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+    o->pins = (int32_t *)malloc(sizeof(int32_t) * ((size_t)P + 1));
+    o->vw = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    o->nw = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+    o->vtx_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    o->inc = (int32_t *)malloc(sizeof(int32_t) * ((size_t)P + 1));
+    o->part = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    o->phi = (int64_t *)calloc((size_t)m * k + 1, sizeof(int64_t));
+    o->bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    o->moved_prev = (uint8_t *)calloc((size_t)m + 1, 1);
+    o->moved_cur = (uint8_t *)calloc((size_t)m + 1, 1);
+    o->cand_t = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    o->cand_g = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    o->approved = (uint8_t *)calloc((size_t)n + 1, 1);
+    o->order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    if (!o->net_off || !o->pins || !o->vw || !o->nw || !o->vtx_off || !o->inc || !o->part ||
+        !o->phi || !o->bw || !o->moved_prev || !o->moved_cur || !o->cand_t || !o->cand_g ||
+        !o->approved || !o->order) {
+        oracle_destroy(o);
+        return NULL;
+    }
+    memcpy(o->net_off, net_off, sizeof(int64_t) * ((size_t)m + 1));
+    if (P) memcpy(o->pins, pins, sizeof(int32_t) * (size_t)P);
+    for (int32_t v = 0; v < n; ++v) o->vw[v] = vertex_w ? vertex_w[v] : 1;
+    for (int32_t e = 0; e < m; ++e) o->nw[e] = net_w ? net_w[e] : 1;
+    for (int32_t v = 0; v < n; ++v) {
+        if (part[v] < 0 || part[v] >= k) { oracle_destroy(o); return NULL; }
+        o->part[v] = part[v];
+    }
+
+    /* incident nets I(v): count degrees, prefix sum, fill in net order */
+    for (int64_t j = 0; j < P; ++j) o->vtx_off[pins[j] + 1]++;
+    for (int32_t v = 0; v < n; ++v) o->vtx_off[v + 1] += o->vtx_off[v];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+        if (!fill) { oracle_destroy(o); return NULL; }
+        memcpy(fill, o->vtx_off, sizeof(int64_t) * ((size_t)n + 1));
+        for (int32_t e = 0; e < m; ++e)
+            for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j)
+                o->inc[fill[pins[j]]++] = e;
+        free(fill);
+    }
+
+    /* Phi(e, i) by counting pins; block weights c(V_i) */
+    for (int32_t e = 0; e < m; ++e)
+        for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j)
+            o->phi[(int64_t)e * k + o->part[pins[j]]]++;
+    int64_t total = 0;
+    for (int32_t v = 0; v < n; ++v) { o->bw[o->part[v]] += o->vw[v]; total += o->vw[v]; }
+    o->lmax = oracle_lmax(total, k, eps);
+    o->round = 0;
+    o->all_eligible = 1;
+    return o;
+}
+
+/* g_i(u) = b(u) - p_i(u), Sec. 5, against the current Phi. */
+int64_t oracle_gain(const oracle_t *o, int32_t u, int32_t i)
+{
+    int32_t a = o->part[u];
+    int64_t b = 0, p = 0;
+    for (int64_t j = o->vtx_off[u]; j < o->vtx_off[u + 1]; ++j) {
+        int32_t e = o->inc[j];
+        if (o->phi[(int64_t)e * o->k + a] == 1) b += o->nw[e];
+        if (o->phi[(int64_t)e * o->k + i] == 0) p += o->nw[e];
+    }
+    return b - p;
+}
+
+static int eligible(const oracle_t *o, int32_t u)
+{
+    if (o->all_eligible) return 1;
+    for (int64_t j = o->vtx_off[u]; j < o->vtx_off[u + 1]; ++j)
+        if (o->moved_prev[o->inc[j]]) return 1;
+    return 0;
+}
+
+/* Best feasible positive-gain target of u against the frozen state (Sec. 6): the block
+ * with the highest gain, smallest id on ties; -1 if no block has positive gain and room. */
+static void best_move(const oracle_t *o, int32_t u, int32_t *t_out, int64_t *g_out)
+{
+    int32_t a = o->part[u];
+    int32_t best_t = -1;
+    int64_t best_g = 0;
+    for (int32_t i = 0; i < o->k; ++i) {
+        if (i == a) continue;
+        int64_t g = oracle_gain(o, u, i);
+        if (g > best_g && o->bw[i] + o->vw[u] <= o->lmax) { best_t = i; best_g = g; }
+    }
+    *t_out = best_t;
+    *g_out = best_g;
+}
+
+static const oracle_t *g_sort_ctx;
+static int by_gain_desc_id_asc(const void *x, const void *y)
+{
+    int32_t u = *(const int32_t *)x, v = *(const int32_t *)y;
+    int64_t gu = g_sort_ctx->cand_g[u], gv = g_sort_ctx->cand_g[v];
+    if (gu != gv) return gu > gv ? -1 : 1;
+    return (u > v) - (u < v);
+}
+
+/* Candidates of sub-round s of the NEXT round against the current state, without
+ * applying anything.  target[u] = -1 for inactive, ineligible or non-candidate vertices. */
+void oracle_candidates(const oracle_t *o, int32_t s, int32_t *target, int64_t *gain)
+{
+    for (int32_t u = 0; u < o->n; ++u) {
+        target[u] = -1;
+        gain[u] = 0;
+        if (oracle_subround_of(o->seed, o->round, u, o->subrounds) != s) continue;
+        if (!eligible(o, u)) continue;
+        best_move(o, u, &target[u], &gain[u]);
+    }
+}
+
+/* Runs `rounds` synchronous LP rounds.  stats: NULL or [rounds * ST_COUNT].
+ * moves: NULL or [max_moves * 4] receiving (global sub-round index, u, from, to) for each
+ * applied move in application order; *num_moves receives the count (may exceed max_moves,
+ * in which case the log is truncated). */
+int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
+                  int64_t max_moves, int64_t *num_moves)
+{
+    const int32_t n = o->n, m = o->m, k = o->k, S = o->subrounds;
+    int64_t logged = 0;
+    for (int32_t rr = 0; rr < rounds; ++rr) {
+        const int64_t r = o->round;
+        int64_t n_cand = 0, n_appr = 0, n_elig = 0;
+        memset(o->moved_cur, 0, (size_t)m);
+        /* eligibility is fixed for the whole round: it depends only on the previous round */
+        uint8_t *elig_copy = (uint8_t *)malloc((size_t)n + 1);
+        if (!elig_copy) return -1;
+        for (int32_t u = 0; u < n; ++u) { elig_copy[u] = (uint8_t)eligible(o, u); n_elig += elig_copy[u]; }
+
+        for (int32_t s = 0; s < S; ++s) {
+            /* (1) candidates against the state frozen at the start of the sub-round */
+            int32_t cnt = 0;
+            for (int32_t u = 0; u < n; ++u) {
+                o->cand_t[u] = -1;
+                o->cand_g[u] = 0;
+                if (!elig_copy[u] || oracle_subround_of(o->seed, r, u, S) != s) continue;
+                best_move(o, u, &o->cand_t[u], &o->cand_g[u]);
+                if (o->cand_t[u] >= 0) { o->order[cnt++] = u; n_cand++; }
+            }
+            /* (2) approval per target block: (gain desc, id asc), inclusive prefix sums */
+            g_sort_ctx = o;
+            qsort(o->order, (size_t)cnt, sizeof(int32_t), by_gain_desc_id_asc);
+            for (int32_t u = 0; u < n; ++u) o->approved[u] = 0;
+            for (int32_t t = 0; t < k; ++t) {
+                int64_t acc = 0;
+                for (int32_t j = 0; j < cnt; ++j) {
+                    int32_t u = o->order[j];
+                    if (o->cand_t[u] != t) continue;
+                    acc += o->vw[u];
+                    if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;
+                }
+            }
+            /* (3) apply every approved move (ascending vertex id) */
+            for (int32_t u = 0; u < n; ++u) {
+                if (!o->approved[u]) continue;
+                int32_t a = o->part[u], t = o->cand_t[u];
+                o->part[u] = t;
+                o->bw[a] -= o->vw[u];
+                o->bw[t] += o->vw[u];
+                for (int64_t j = o->vtx_off[u]; j < o->vtx_off[u + 1]; ++j) {
+                    int32_t e = o->inc[j];
+                    o->phi[(int64_t)e * k + a]--;
+                    o->phi[(int64_t)e * k + t]++;
+                    o->moved_cur[e] = 1;
+                }
+                if (moves && logged < max_moves) {
+                    int64_t *mv = moves + 4 * logged;
+                    mv[0] = r * S + s; mv[1] = u; mv[2] = a; mv[3] = t;
+                }
+                logged++;
+                n_appr++;
+            }
+        }
+        free(elig_copy);
+        memcpy(o->moved_prev, o->moved_cur, (size_t)m);
+        o->all_eligible = 0;
+        o->round++;
+        if (stats) {
+            int64_t maxw = 0;
+            for (int32_t i = 0; i < k; ++i) if (o->bw[i] > maxw) maxw = o->bw[i];
+            int64_t *st = stats + (int64_t)rr * ST_COUNT;
+            st[ST_OBJ] = objective_from_phi(o);
+            st[ST_CAND] = n_cand;
+            st[ST_APPROVED] = n_appr;
+            st[ST_ELIGIBLE] = n_elig;
+            st[ST_MAXW] = maxw;
+        }
+    }
+    if (num_moves) *num_moves = logged;
+    return 0;
+}
+
+int64_t oracle_objective(const oracle_t *o) { return objective_from_phi(o); }
+int64_t oracle_lmax_of(const oracle_t *o) { return o->lmax; }
+int64_t oracle_round_of(const oracle_t *o) { return o->round; }
+
+void oracle_get_partition(const oracle_t *o, int32_t *out)
+{
+    memcpy(out, o->part, sizeof(int32_t) * (size_t)o->n);
+}
+
+void oracle_get_block_weights(const oracle_t *o, int64_t *out)
+{
+    memcpy(out, o->bw, sizeof(int64_t) * (size_t)o->k);
+}
+
+void oracle_get_phi(const oracle_t *o, int64_t *out)
+{
+    memcpy(out, o->phi, sizeof(int64_t) * (size_t)o->m * (size_t)o->k);
+}
+
+/* Candidates of round 0, sub-round s, for a sample of vertices, straight from the input
+ * (no full Phi table): Phi(e, .) is counted from the pins of each net incident to a
+ * sampled vertex.  Used to check full-size instances whose Phi table would not fit the
+ * host.  Requires the sampled vertices to be distinct.  Returns 0, or -1 on allocation
+ * failure. */
+int oracle_sample_candidates(int32_t n, int32_t m, const int64_t *net_off, const int32_t *pins,
+                             const int32_t *vertex_w, const int32_t *net_w, int32_t k,
+                             double eps, const int32_t *part, int32_t subrounds, uint64_t seed,
+                             int32_t s, int32_t count, const int32_t *sample,
+                             int32_t *target, int64_t *gain)
+{
+    int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    int32_t *slot = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int64_t *phi_row = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    /* per sampled vertex: b, and p_i accumulated over its incident nets */
+    int64_t *b = (int64_t *)calloc((size_t)count + 1, sizeof(int64_t));
+    int64_t *p = (int64_t *)calloc(((size_t)count + 1) * (size_t)k, sizeof(int64_t));
+    if (!bw || !slot || !phi_row || !b || !p) {
+        free(bw); free(slot); free(phi_row); free(b); free(p);
+        return -1;
+    }
+    int64_t total = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t c = vertex_w ? vertex_w[v] : 1;
+        bw[part[v]] += c;
+        total += c;
+        slot[v] = -1;
+    }
+    int64_t lmax = oracle_lmax(total, k, eps);
+    for (int32_t j = 0; j < count; ++j) slot[sample[j]] = j;
+    for (int32_t e = 0; e < m; ++e) {
+        int any = 0;
+        for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) if (slot[pins[j]] >= 0) { any = 1; break; }
+        if (!any) continue;
+        for (int32_t i = 0; i < k; ++i) phi_row[i] = 0;
+        for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) phi_row[part[pins[j]]]++;
+        int64_t w = net_w ? net_w[e] : 1;
+        for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) {
+            int32_t q = slot[pins[j]];
+            if (q < 0) continue;
+            if (phi_row[part[pins[j]]] == 1) b[q] += w;
+            for (int32_t i = 0; i < k; ++i) if (phi_row[i] == 0) p[(int64_t)q * k + i] += w;
+        }
+    }
+    for (int32_t q = 0; q < count; ++q) {
+        int32_t u = sample[q];
+        target[q] = -1;
+        gain[q] = 0;
+        if (oracle_subround_of(seed, 0, u, subrounds) != s) continue;
+        int32_t a = part[u];
+        int64_t c = vertex_w ? vertex_w[u] : 1;
+        for (int32_t i = 0; i < k; ++i) {
+            if (i == a) continue;
+            int64_t g = b[q] - p[(int64_t)q * k + i];
+            if (g > gain[q] && bw[i] + c <= lmax) { target[q] = i; gain[q] = g; }
+        }
+    }
+    free(bw); free(slot); free(phi_row); free(b); free(p);
+    return 0;
+}

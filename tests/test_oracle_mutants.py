@@ -1,0 +1,80 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case copies the oracle source, plants one mistake (a dropped term, a wrong sign, a
+wrong index or comparison, a transposed operand), builds it, and runs the pin suite
+(tests/test_oracle_pins.py) against the broken copy.  The pin suite must fail for every
+mutant.  The committed oracle is never modified.
+"""
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "hgp_oracle.c")
+
+# (name, exact text in the oracle source, replacement)
+MUTANTS = [
+    ("b uses Phi==2", "if (o->phi[(int64_t)e * o->k + a] == 1) b += o->nw[e];",
+     "if (o->phi[(int64_t)e * o->k + a] == 2) b += o->nw[e];"),
+    ("p_i uses Phi==1", "if (o->phi[(int64_t)e * o->k + i] == 0) p += o->nw[e];",
+     "if (o->phi[(int64_t)e * o->k + i] == 1) p += o->nw[e];"),
+    ("gain sign", "return b - p;", "return p - b;"),
+    ("b drops net weight", "b += o->nw[e];", "b += 1;"),
+    ("tie to larger block", "if (g > best_g && o->bw[i]", "if (g >= best_g && g > 0 && o->bw[i]"),
+    ("strict capacity", "o->bw[i] + o->vw[u] <= o->lmax", "o->bw[i] + o->vw[u] < o->lmax"),
+    ("capacity ignores c(u)", "o->bw[i] + o->vw[u] <= o->lmax", "o->bw[i] <= o->lmax"),
+    ("approval gain ascending", "if (gu != gv) return gu > gv ? -1 : 1;",
+     "if (gu != gv) return gu < gv ? -1 : 1;"),
+    ("approval id descending", "return (u > v) - (u < v);", "return (u < v) - (u > v);"),
+    ("exclusive prefix", "acc += o->vw[u];\n                    if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;",
+     "if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;\n                    acc += o->vw[u];"),
+    ("Phi update swapped", "o->phi[(int64_t)e * k + a]--;\n                    o->phi[(int64_t)e * k + t]++;",
+     "o->phi[(int64_t)e * k + a]++;\n                    o->phi[(int64_t)e * k + t]--;"),
+    ("block weight sign", "o->bw[a] -= o->vw[u];", "o->bw[a] += o->vw[u];"),
+    ("always eligible", "if (o->all_eligible) return 1;", "return 1;"),
+    ("never eligible after round 0", "if (o->moved_prev[o->inc[j]]) return 1;", "(void)j;"),
+    ("lmax without ceil", "int64_t avg = (total_weight + k - 1) / k;", "int64_t avg = total_weight / k;"),
+    ("objective counts lambda", "if (lambda > 0) obj += (lambda - 1) * o->nw[e];",
+     "if (lambda > 0) obj += lambda * o->nw[e];"),
+    ("objective drops weight", "if (lambda > 0) obj += (lambda - 1) * o->nw[e];",
+     "if (lambda > 0) obj += (lambda - 1);"),
+    ("hash shift", "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;", "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;"),
+    ("hash round/vertex swapped", "seed ^ (((uint64_t)round << 32) | (uint64_t)(uint32_t)u)",
+     "seed ^ (((uint64_t)u << 32) | (uint64_t)(uint32_t)round)"),
+    ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
+     "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
+]
+
+
+def _run_mutant(name, old, new, workdir):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    mutated = src.replace(old, new, 1)
+    d = tempfile.mkdtemp(dir=workdir)
+    c = os.path.join(d, "m.c")
+    so = os.path.join(d, "m.so")
+    open(c, "w").write(mutated)
+    subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-o", so, c, "-lm"])
+    env = dict(os.environ, HGP_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode
+
+
+def test_every_planted_mistake_is_caught():
+    # the last entry is a no-op rewrite: it must NOT be caught (sanity of the harness)
+    work = tempfile.mkdtemp(prefix="oracle_mutants_")
+    try:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+            results = list(ex.map(lambda m: _run_mutant(*m, work), MUTANTS))
+    finally:
+        shutil.rmtree(work, ignore_errors=True)
+    survived = [name for name, rc in results[:-1] if rc == 0]
+    assert not survived, f"pins did not catch: {survived}"
+    assert results[-1][1] == 0, "an equivalent rewrite of the oracle was flagged"
