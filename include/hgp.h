@@ -1,0 +1,167 @@
+/*
+ * hgp.h — C ABI of libhgp: GPU label-propagation refinement of a k-way hypergraph
+ * partition under the connectivity (lambda-1) metric, for NVIDIA GB300 (sm_103a).
+ *
+ * The problem statement is the one of "Scalable Shared-Memory Hypergraph Partitioning"
+ * (Gottesbüren, Heuer, Sanders, Schlag), Sec. 2: a weighted hypergraph H = (V, E, c, omega)
+ * with positive weights, a k-way partition Pi : V -> {0..k-1} (the paper numbers blocks
+ * 1..k), the balance bound L_max = (1+eps) * ceil(c(V)/k), the pin counts Phi(e, V_i), the
+ * connectivity sets Lambda(e), and the objective (lambda-1)(Pi) = sum_e (lambda(e)-1) omega(e).
+ * Refinement is the size-constrained label propagation of Sec. 6, with the gain
+ * g_i(u) = b(u) - p_i(u) of Sec. 5, run in a deterministic synchronous form:
+ *
+ *   A round r is split into S sub-rounds.  Vertex u is active in sub-round
+ *   splitmix64(seed ^ (r << 32 | u)) mod S (SplitMix64 output function).  It is eligible in
+ *   the first round after creation (or after hgp_set_partition) and afterwards iff one of its
+ *   incident nets had a pin moved in round r-1.  Every active eligible vertex picks the block
+ *   with the highest positive gain whose weight, frozen at the start of the sub-round, plus
+ *   c(u) is at most L_max; ties go to the smaller block id.  Candidates are approved per target
+ *   block in (gain desc, vertex id asc) order while the inclusive prefix sum of their weights
+ *   fits into L_max - w(t).  All approved moves are applied at once.
+ *
+ * All arithmetic is integer; results are bit-identical for any launch configuration and any
+ * run.  Reading of the real-valued L_max: floor((1.0 + eps) * ceil(c(V)/k)) in IEEE double.
+ * Empty nets contribute 0 to the objective.
+ *
+ * Conventions for every function:
+ *   - Return value: an hgp_status (0 = success).  No function aborts, prints or exits.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of
+ *     the current device.  Input arrays are owned by the caller and copied during the call;
+ *     output arrays are owned by the caller.
+ *   - A handle is used by one host thread at a time.  All device work is queued on the
+ *     handle's stream (hgp_options.cuda_stream, or a stream the library creates); functions
+ *     that return data to host memory synchronise that stream before returning.
+ */
+#ifndef HGP_H
+#define HGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HGP_OK = 0,
+    HGP_ERR_INVALID = 1,      /* an argument or the hypergraph violates a stated rule */
+    HGP_ERR_OOM = 2,          /* device or host allocation failed */
+    HGP_ERR_UNSUPPORTED = 3,  /* k > 64, >= 2^31 pins, a vertex with sum of incident net
+                                 weights >= 2^31, or more than 64 sub-rounds */
+    HGP_ERR_CUDA = 4,         /* a CUDA call failed; the handle should be destroyed */
+    HGP_ERR_TIMEOUT = 5,      /* a device-side wait gave up (batched persistent mode) */
+    HGP_ERR_INTERNAL = 6      /* check mode found the maintained objective differing from
+                                 the one recomputed from Phi */
+} hgp_status;
+
+typedef struct hgp_handle hgp_handle;
+typedef struct hgp_batch hgp_batch;
+
+/* Options.  Zero-initialised fields select the defaults given in brackets. */
+typedef struct {
+    int32_t subrounds;   /* S, 1..64 [4] */
+    int32_t phi_width;   /* bytes per Phi entry: 1, 2 or 4; 0 = auto [0]: 1 if every net has
+                            at most 255 pins, else 2.  Nets larger than the width can count
+                            (255 or 65535 pins) keep 4-byte rows in a separate wide table. */
+    uint64_t seed;       /* sub-round hash seed [0] */
+    int32_t debug;       /* bit 0 (check mode): hgp_refine recomputes the objective from the
+                            Phi table after the call and returns HGP_ERR_INTERNAL if it differs
+                            from the incrementally maintained one [0] */
+    int32_t graph;       /* 1: replay refine() calls of the same round count as a CUDA graph [0] */
+    void *cuda_stream;   /* cudaStream_t to run on, or NULL for a library-owned stream */
+} hgp_options;
+
+/* Per-round statistics written by hgp_refine. */
+typedef struct {
+    int64_t objective;        /* (lambda-1)(Pi) after the round (Sec. 2) */
+    int64_t candidates;       /* vertices that chose a target in the round */
+    int64_t approved;         /* moves applied in the round */
+    int64_t eligible;         /* eligible vertices in the round */
+    int64_t max_block_weight; /* max_i c(V_i) after the round */
+} hgp_round_stats;
+
+/* Fills *opt with the defaults. */
+void hgp_default_options(hgp_options *opt);
+
+/* Human-readable name of a status code (static string). */
+const char *hgp_strerror(int code);
+
+/*
+ * Creates a handle from a hypergraph in net->pins CSR form (paper Sec. 2 notation;
+ * Sec. 3.2 describes the same adjacency arrays), copying all inputs to the device.
+ *
+ *   n, m          number of vertices and nets, n >= 1, m >= 0.
+ *   net_offsets   host int64[m+1]: pins of net e are pins[net_offsets[e] .. net_offsets[e+1]);
+ *                 net_offsets[0] = 0, non-decreasing, net_offsets[m] = P < 2^31.
+ *   pins          host int32[P]: vertex ids in [0, n), strictly increasing within each net.
+ *   vertex_w      host int32[n] with every c(v) >= 1, or NULL for unit weights.
+ *   net_w         host int32[m] with every omega(e) >= 1, or NULL for unit weights.
+ *   k             number of blocks, 2..64.   eps: balance parameter, 0 < eps < 1 (Sec. 2).
+ *   initial_part  host int32[n] with values in [0, k); need not be balanced.
+ *   opt           NULL for defaults.
+ *   out           receives the handle; set to NULL on any error (nothing leaks).
+ * Errors: HGP_ERR_INVALID for any violated rule above or null required pointers;
+ * HGP_ERR_UNSUPPORTED for k > 64, P >= 2^31, S > 64, or a vertex whose incident net weights
+ * sum to 2^31 or more; HGP_ERR_OOM; HGP_ERR_CUDA.
+ */
+int hgp_create(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
+               const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+               const int32_t *initial_part, const hgp_options *opt, hgp_handle **out);
+
+/* Same as hgp_create, but every array argument is a DEVICE pointer (copied device to
+ * device; the caller may free its buffers after the call returns). */
+int hgp_create_device(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
+                      const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+                      const int32_t *initial_part, const hgp_options *opt, hgp_handle **out);
+
+/*
+ * Runs `rounds` (>= 0) synchronous label-propagation rounds (Sec. 6) on the handle's stream.
+ * stats: NULL, or host hgp_round_stats[rounds] filled on return (the call then synchronises).
+ * With stats == NULL the call returns after queuing the work; a later call that returns data
+ * synchronises.  Round numbering and eligibility continue across calls, so refine(a) followed
+ * by refine(b) equals refine(a+b).
+ */
+int hgp_refine(hgp_handle *h, int32_t rounds, hgp_round_stats *stats);
+
+/* Replaces the partition (host int32[n], or DEVICE pointer if on_device != 0), rebuilds Phi,
+ * Lambda, block weights and the objective, and restarts round numbering at 0 with every
+ * vertex eligible, exactly as if the handle had been created with this partition. */
+int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device);
+
+/* (lambda-1)(Pi) as maintained incrementally (Sec. 2). */
+int hgp_objective(hgp_handle *h, int64_t *out);
+
+/* (lambda-1)(Pi) recomputed from scratch from the Phi table (check mode). */
+int hgp_objective_from_phi(hgp_handle *h, int64_t *out);
+
+/* Current partition into host int32[n] (or a device pointer with on_device != 0). */
+int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device);
+
+/* Block weights c(V_i) into host int64[k]. */
+int hgp_get_block_weights(hgp_handle *h, int64_t *w);
+
+/* Phi(e, V_i) widened to host int32[m*k], row-major by net in input order (Sec. 5.1). */
+int hgp_get_phi(hgp_handle *h, int32_t *phi);
+
+/* Connectivity sets Lambda(e) as host uint64[m] bitsets (bit i = block i). */
+int hgp_get_lambda(hgp_handle *h, uint64_t *lam);
+
+/* Sizes and derived constants: n, m, k, P, L_max, Phi width in bytes, number of wide nets,
+ * next round number.  Any pointer may be NULL. */
+int hgp_get_info(hgp_handle *h, int32_t *n, int32_t *m, int32_t *k, int64_t *pins,
+                 int64_t *lmax, int32_t *phi_width, int32_t *wide_nets, int64_t *next_round);
+
+/*
+ * Debug export of the gain step alone: computes, against the current state, the candidates of
+ * sub-round s (0 <= s < S) of the next round, without applying anything.  target: host
+ * int32[n] (-1 for vertices that are inactive, ineligible or without a feasible positive-gain
+ * block); gain: host int64[n] (0 where target is -1).
+ */
+int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain);
+
+/* Frees all device memory of the handle (NULL is allowed). */
+void hgp_destroy(hgp_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGP_H */

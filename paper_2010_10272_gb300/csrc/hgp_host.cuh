@@ -1,0 +1,48 @@
+// Host-side handle of libhgp (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hgp_internal.cuh"
+
+struct hgp_handle {
+    hgp::Dev d{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t seed = 0;
+    int32_t debug = 0;
+    int32_t graph = 0;
+    int64_t next_round = 0;       // global round counter r
+    bool all_eligible = true;     // first round after creation / set_partition
+    int32_t n_wide = 0;
+    int64_t max_vertex_netweight = 0;   // max_u sum_{e in I(u)} omega(e)
+    int64_t total_weight = 0;
+    int32_t stats_cap = 0;
+    int64_t *h_stats = nullptr;   // pinned host copy of the stats buffer
+    // memory owned by the handle
+    void *allocs[40] = {};
+    int n_allocs = 0;
+    // CUDA-graph cache: one refine() of `graph_rounds` rounds
+    cudaGraphExec_t graph_exec = nullptr;
+    int32_t graph_rounds = 0;
+    int32_t *d_round = nullptr;   // device copy of the round counter (graph mode)
+};
+
+namespace hgp {
+
+inline int status_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return HGP_OK;
+    if (e == cudaErrorMemoryAllocation) return HGP_ERR_OOM;
+    return HGP_ERR_CUDA;
+}
+
+// refine-side entry points used by the C ABI layer (hgp_refine.cu)
+int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats);
+int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain);
+int ensure_stats(hgp_handle *h, int32_t rounds);
+cudaError_t objective_from_phi(hgp_handle *h, int64_t *d_out);
+
+}  // namespace hgp

@@ -1,0 +1,854 @@
+// libhgp: creation, validation, CSR transpose, state initialisation and getters.
+//
+// Setup builds, on the device, everything the refinement rounds read:
+//   * the vertex -> incident nets CSR I(v) from the net -> pins CSR (Sec. 2; the paper
+//     builds the same two adjacency arrays with prefix sums, Sec. 3.2);
+//   * Phi(e, i) from the partition (Sec. 2 / Sec. 5.1), Lambda(e), S1(e) and omega(e) in the
+//     per-net record, the block weights and the (lambda-1) objective (Sec. 2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "hgp_host.cuh"
+
+using namespace hgp;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------ prefix sums (int32)
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp_tot, int32_t *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int32_t s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_tot[lane] = s - t;
+        if (lane == 31) *total = s;
+    }
+    __syncthreads();
+    const int32_t r = warp_tot[wid] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int32_t *in, int64_t count, int32_t *sums)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < count) s += in[base + i];
+    block_exclusive_scan(s, wt, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int32_t *sums, int64_t nb)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t tot;
+    int32_t carry = 0;
+    for (int64_t b = 0; b < nb; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int32_t v = i < nb ? sums[i] : 0;
+        const int32_t ex = block_exclusive_scan(v, wt, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_final(const int32_t *in, int32_t *out, int64_t count, const int32_t *sums)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < count ? in[base + i] : 0;
+        s += v[i];
+    }
+    int32_t run = sums[blockIdx.x] + block_exclusive_scan(s, wt, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < count) out[base + i] = run;
+        run += v[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = sums[blockIdx.x] + tot;
+}
+
+// ------------------------------------------------------------------ validation
+__global__ void k_check_offsets(const int64_t *off64, int32_t *off32, int32_t m, int64_t P, int32_t *err)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = off64[e];
+        bool bad = (e == 0 && a != 0) || (e == m && a != P) || a < 0 || a > P;
+        if (e < m && off64[e + 1] < a) bad = true;
+        if (bad) atomicOr(err, ERR_INVALID);
+        off32[e] = (int32_t)(a < 0 ? 0 : (a > P ? P : a));
+    }
+}
+
+// warp per net: pins in range and strictly increasing; largest net size
+__global__ void k_check_pins(const int32_t *off, const int32_t *pins, int32_t m, int32_t n,
+                             int32_t *err, int32_t *max_size)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int32_t local_max = 0;
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        const int32_t b = off[e], end = off[e + 1];
+        local_max = max(local_max, end - b);
+        bool bad = false;
+        for (int32_t j = b + lane; j < end; j += 32) {
+            const int32_t v = pins[j];
+            if (v < 0 || v >= n) bad = true;
+            if (j + 1 < end && pins[j + 1] <= v) bad = true;
+        }
+        if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, ERR_INVALID);
+    }
+    if (lane == 0) atomicMax(max_size, local_max);
+}
+
+__global__ void k_check_vertices(const int32_t *vw, const int32_t *part_in, int32_t n, int32_t k,
+                                 int32_t *err)
+{
+    bool bad = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (vw && vw[v] < 1) bad = true;
+        if (part_in) {
+            const int32_t p = part_in[v];
+            if (p < 0 || p >= k) bad = true;
+        }
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
+}
+
+__global__ void k_check_nets(const int32_t *nw, int32_t m, int32_t *err)
+{
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (nw[e] < 1) bad = true;
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
+}
+
+// ------------------------------------------------------------------ transpose
+__global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[pins[j]], 1);
+}
+
+__global__ void k_scatter(const int32_t *off, const int32_t *pins, int32_t m, int32_t *fill, int32_t *inc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        const int32_t b = off[e], end = off[e + 1];
+        for (int32_t j = b + lane; j < end; j += 32) {
+            const int32_t pos = atomicAdd(&fill[pins[j]], 1);
+            inc[pos] = (int32_t)e;
+        }
+    }
+}
+
+// W(u) = sum of incident net weights must stay below 2^31 (int32 gain arithmetic)
+__global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, const int32_t *nw,
+                                   int32_t n, int32_t *err, unsigned long long *max_w)
+{
+    unsigned long long local = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int32_t j = vtx_off[v]; j < vtx_off[v + 1]; ++j) s += nw ? nw[inc[j]] : 1;
+        if (s >= (int64_t)1 << 31) atomicOr(err, ERR_UNSUPPORTED);
+        local = max(local, (unsigned long long)s);
+    }
+    for (int o = 16; o; o >>= 1) local = max(local, __shfl_xor_sync(kFull, local, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_w, local);
+}
+
+__global__ void k_wide_flags(const int32_t *off, int32_t m, int32_t narrow_max, int32_t *flags)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        flags[e] = (off[e + 1] - off[e]) > narrow_max ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ state initialisation
+__global__ void k_copy_part(const int32_t *in, uint8_t *part, int32_t n)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        part[v] = (uint8_t)in[v];
+}
+
+__global__ void k_block_weights(Dev d)
+{
+    __shared__ unsigned long long w[64];
+    if (threadIdx.x < 64) w[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < d.n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&w[d.part[v]], (unsigned long long)(d.vw ? d.vw[v] : 1));
+    __syncthreads();
+    if (threadIdx.x < d.k && w[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[threadIdx.x]), w[threadIdx.x]);
+}
+
+// Warp per net: counts Phi(e, .) from the partition, writes the Phi row, the record
+// (Lambda, S1, omega, stamp) and adds (lambda(e) - 1) * omega(e) to the objective.
+template <typename Rec>
+__global__ void k_init_nets(Dev d)
+{
+    __shared__ int32_t cnt[kWarps][64];
+    __shared__ long long part_obj[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    long long obj = 0;
+    for (int64_t e = (int64_t)blockIdx.x * kWarps + wid; e < d.m; e += warps) {
+        cnt[wid][lane] = 0;
+        cnt[wid][lane + 32] = 0;
+        __syncwarp();
+        const int32_t b = d.net_off[e], end = d.net_off[e + 1];
+        for (int32_t base = b; base < end; base += 32) {
+            const int32_t j = base + lane;
+            const bool act = j < end;
+            const unsigned mask = __ballot_sync(kFull, act);
+            if (act) {
+                const int blk = d.part[d.pins[j]];
+                const unsigned peers = __match_any_sync(mask, blk);
+                if (lane == __ffs(peers) - 1) cnt[wid][blk] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        const int32_t size = end - b;
+        const int32_t wv = d.nw ? d.nw[e] : 1;
+        const bool wide = d.widx != nullptr && size > (d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff));
+        const int32_t wrow = wide ? d.widx[e] : 0;
+        for (int i = lane; i < d.k; i += 32) phi_set(d, (int32_t)e, i, cnt[wid][i], wide, wrow);
+        const unsigned lo_lam = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] > 0);
+        const unsigned lo_s1 = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] == 1);
+        const unsigned hi_lam = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] > 0);
+        const unsigned hi_s1 = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] == 1);
+        if (lane == 0) {
+            const int32_t wf = wv | (wide ? (int32_t)kWideFlag : 0);
+            Rec *rec = reinterpret_cast<Rec *>(d.rec) + e;
+            if constexpr (sizeof(Rec) == 16) {
+                Rec r;
+                r.s1 = lo_s1;
+                r.w = wf;
+                r.mv = kNever * 2;
+                r.lam = lo_lam;
+                *rec = r;
+            } else {
+                Rec r;
+                r.s1 = (uint64_t)lo_s1 | ((uint64_t)hi_s1 << 32);
+                r.w = wf;
+                r.mv = kNever * 2;
+                r.lam = (uint64_t)lo_lam | ((uint64_t)hi_lam << 32);
+                r.w2 = wf;
+                r.pad = 0;
+                *rec = r;
+            }
+            const int lambda = __popc(lo_lam) + __popc(hi_lam);
+            if (lambda > 0) obj += (long long)(lambda - 1) * wv;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) part_obj[wid] = obj;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int w = 0; w < kWarps; ++w) s += part_obj[w];
+        if (s) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)s);
+    }
+}
+
+// ------------------------------------------------------------------ getters
+__global__ void k_obj_from_phi(Dev d, unsigned long long *out)
+{
+    long long s = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t size = d.net_off[e + 1] - d.net_off[e];
+        const bool wide = d.widx != nullptr && size > (d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff));
+        const int32_t wrow = wide ? d.widx[e] : 0;
+        int lambda = 0;
+        for (int i = 0; i < d.k; ++i) lambda += phi_get(d, (int32_t)e, i, wide, wrow) > 0;
+        if (lambda > 0) s += (long long)(lambda - 1) * (d.nw ? d.nw[e] : 1);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, (unsigned long long)s);
+}
+
+__global__ void k_widen_phi(Dev d, int32_t *out)
+{
+    const int64_t total = (int64_t)d.m * d.k;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = (int32_t)(x / d.k), i = (int32_t)(x % d.k);
+        const int32_t size = d.net_off[e + 1] - d.net_off[e];
+        const bool wide = d.widx != nullptr && size > (d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff));
+        out[x] = phi_get(d, e, i, wide, wide ? d.widx[e] : 0);
+    }
+}
+
+template <typename Rec>
+__global__ void k_get_lambda(Dev d, uint64_t *out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (uint64_t)reinterpret_cast<const Rec *>(d.rec)[e].lam;
+}
+
+__global__ void k_part_to_i32(const uint8_t *part, int32_t *out, int32_t n)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = part[v];
+}
+
+// ------------------------------------------------------------------ host helpers
+int grid_for(int64_t work, int threads, int cap = 152 * 32)
+{
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <typename T>
+cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
+{
+    *p = nullptr;
+    if (count < 1) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return e;
+    }
+    h->allocs[h->n_allocs++] = q;
+    *p = reinterpret_cast<T *>(q);
+    return cudaSuccess;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t _e = (call);                   \
+        if (_e != cudaSuccess) {                   \
+            (void)cudaGetLastError();              \
+            return status_of(_e);                  \
+        }                                          \
+    } while (0)
+
+int init_state(hgp_handle *h)
+{
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(d.bw, 0, sizeof(int64_t) * d.k, st));
+    CK(cudaMemsetAsync(d.obj, 0, sizeof(int64_t), st));
+    k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d);
+    CK(cudaGetLastError());
+    const int g = grid_for((int64_t)d.m * 32, kThreads, 152 * 16);
+    if (d.k <= 32) k_init_nets<Rec16><<<g, kThreads, 0, st>>>(d);
+    else k_init_nets<Rec32><<<g, kThreads, 0, st>>>(d);
+    CK(cudaGetLastError());
+    h->next_round = 0;
+    h->all_eligible = true;
+    return HGP_OK;
+}
+
+int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
+                const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+                const int32_t *initial_part, const hgp_options *opt, hgp_handle **out, bool on_device)
+{
+    if (!out) return HGP_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || m < 0 || !net_offsets || !initial_part || (m > 0 && !pins)) return HGP_ERR_INVALID;
+    if (k < 2 || !(eps > 0.0 && eps < 1.0)) return HGP_ERR_INVALID;
+    if (k > 64) return HGP_ERR_UNSUPPORTED;
+    hgp_options o;
+    hgp_default_options(&o);
+    if (opt) o = *opt;
+    if (o.subrounds == 0) o.subrounds = 4;
+    if (o.subrounds < 0) return HGP_ERR_INVALID;
+    if (o.subrounds > 64) return HGP_ERR_UNSUPPORTED;
+    if (o.phi_width != 0 && o.phi_width != 1 && o.phi_width != 2 && o.phi_width != 4) return HGP_ERR_INVALID;
+
+    int64_t P = 0;
+    if (on_device) {
+        if (cudaMemcpy(&P, net_offsets + m, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return HGP_ERR_INVALID;
+        }
+    } else {
+        P = net_offsets[m];
+    }
+    if (P < 0) return HGP_ERR_INVALID;
+    if (P >= ((int64_t)1 << 31)) return HGP_ERR_UNSUPPORTED;
+
+    hgp_handle *h = new (std::nothrow) hgp_handle();
+    if (!h) return HGP_ERR_OOM;
+    int rc = HGP_OK;
+    auto fail = [&](int code) {
+        hgp_destroy(h);
+        return code;
+    };
+    Dev &d = h->d;
+    cudaGetDevice(&h->device);
+    if (o.cuda_stream) {
+        h->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(HGP_ERR_CUDA);
+        }
+        h->own_stream = true;
+    }
+    cudaStream_t st = h->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    h->seed = o.seed;
+    h->debug = o.debug;
+    h->graph = o.graph;
+    d.n = n;
+    d.m = m;
+    d.k = k;
+    d.P = (int32_t)P;
+    d.S = o.subrounds;
+    d.n_ranges = (n + kRange - 1) / kRange;
+    d.n_tiles = (d.n_ranges + kWarps - 1) / kWarps;
+
+#define CKF(call)                                  \
+    do {                                           \
+        cudaError_t _e = (call);                   \
+        if (_e != cudaSuccess) {                   \
+            (void)cudaGetLastError();              \
+            return fail(status_of(_e));            \
+        }                                          \
+    } while (0)
+
+    // ---- inputs
+    int64_t *off64 = nullptr;
+    int32_t *part_in = nullptr, *tmp = nullptr, *misc32 = nullptr;
+    int32_t *net_off = nullptr, *pins_d = nullptr, *vw_d = nullptr, *nw_d = nullptr;
+    CKF(dalloc(h, &off64, (int64_t)m + 1));
+    CKF(dalloc(h, &net_off, (int64_t)m + 1));
+    CKF(dalloc(h, &pins_d, P));
+    CKF(dalloc(h, &part_in, n));
+    CKF(dalloc(h, &misc32, 8));   // err, max net size
+    CKF(cudaMemsetAsync(misc32, 0, 8 * sizeof(int32_t), st));
+    d.err = misc32;
+    int32_t *max_size_d = misc32 + 1;
+    CKF(cudaMemcpyAsync(off64, net_offsets, sizeof(int64_t) * ((size_t)m + 1), kind, st));
+    if (P) CKF(cudaMemcpyAsync(pins_d, pins, sizeof(int32_t) * (size_t)P, kind, st));
+    CKF(cudaMemcpyAsync(part_in, initial_part, sizeof(int32_t) * (size_t)n, kind, st));
+    if (vertex_w) {
+        CKF(dalloc(h, &vw_d, n));
+        CKF(cudaMemcpyAsync(vw_d, vertex_w, sizeof(int32_t) * (size_t)n, kind, st));
+    }
+    if (net_w) {
+        CKF(dalloc(h, &nw_d, m));
+        CKF(cudaMemcpyAsync(nw_d, net_w, sizeof(int32_t) * (size_t)m, kind, st));
+    }
+    d.net_off = net_off;
+    d.pins = pins_d;
+    d.vw = vw_d;
+    d.nw = nw_d;
+
+    // ---- validation
+    k_check_offsets<<<grid_for((int64_t)m + 1, 256), 256, 0, st>>>(off64, net_off, m, P, d.err);
+    k_check_vertices<<<grid_for(n, 256), 256, 0, st>>>(vw_d, part_in, n, k, d.err);
+    if (nw_d) k_check_nets<<<grid_for(m, 256), 256, 0, st>>>(nw_d, m, d.err);
+    CKF(cudaGetLastError());
+    int32_t host_err[2] = {0, 0};
+    CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKF(cudaStreamSynchronize(st));
+    if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
+    if (m > 0) {
+        k_check_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d);
+        CKF(cudaGetLastError());
+    }
+    CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKF(cudaStreamSynchronize(st));
+    if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
+    const int32_t max_size = host_err[1];
+
+    // ---- Phi width: 1 byte if every net fits, else 2 bytes; bigger nets go to the wide table
+    int w = o.phi_width;
+    if (w == 0) w = max_size <= 255 ? 1 : 2;
+    d.phi_w = w;
+    const int32_t narrow_max = w == 1 ? 255 : (w == 2 ? 65535 : 0x7fffffff);
+
+    // ---- scan scratch (shared by the scans below)
+    const int64_t scan_count = ((int64_t)(n > m ? n : m) + 1);
+    const int64_t nb = (scan_count + kScanChunk - 1) / kScanChunk;
+    int32_t *block_sums = nullptr;
+    CKF(dalloc(h, &block_sums, nb + 1));
+    auto scan = [&](const int32_t *in, int32_t *outp, int64_t count) -> cudaError_t {
+        const int64_t blocks = (count + kScanChunk - 1) / kScanChunk;
+        const int64_t bl = blocks < 1 ? 1 : blocks;
+        k_scan_reduce<<<(unsigned)bl, kScanThreads, 0, st>>>(in, count, block_sums);
+        k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, bl);
+        k_scan_final<<<(unsigned)bl, kScanThreads, 0, st>>>(in, outp, count, block_sums);
+        return cudaGetLastError();
+    };
+
+    // ---- wide nets
+    CKF(dalloc(h, &tmp, (int64_t)(n > m ? n : m) + 1));
+    if (max_size > narrow_max) {
+        int32_t *widx = nullptr;
+        CKF(dalloc(h, &widx, (int64_t)m + 1));
+        k_wide_flags<<<grid_for(m, 256), 256, 0, st>>>(net_off, m, narrow_max, tmp);
+        CKF(scan(tmp, widx, m));
+        int32_t nwide = 0;
+        CKF(cudaMemcpyAsync(&nwide, widx + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CKF(cudaStreamSynchronize(st));
+        h->n_wide = nwide;
+        d.widx = widx;
+        int32_t *pw = nullptr;
+        CKF(dalloc(h, &pw, (int64_t)nwide * k));
+        CKF(cudaMemsetAsync(pw, 0, sizeof(int32_t) * (size_t)nwide * k, st));
+        d.phi_wide = pw;
+    }
+
+    // ---- vertex -> nets CSR
+    int32_t *vtx_off = nullptr, *inc = nullptr;
+    CKF(dalloc(h, &vtx_off, (int64_t)n + 1));
+    CKF(dalloc(h, &inc, P));
+    CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+    if (P) k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp);
+    CKF(scan(tmp, vtx_off, n));
+    CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    if (m > 0) k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, tmp, inc);
+    CKF(cudaGetLastError());
+    d.vtx_off = vtx_off;
+    d.inc = inc;
+
+    unsigned long long *maxw_d = reinterpret_cast<unsigned long long *>(misc32 + 2);
+    CKF(cudaMemsetAsync(maxw_d, 0, sizeof(unsigned long long), st));
+    k_vertex_netweight<<<grid_for(n, 256), 256, 0, st>>>(vtx_off, inc, nw_d, n, d.err, maxw_d);
+    CKF(cudaGetLastError());
+    unsigned long long maxw = 0;
+    CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(&maxw, maxw_d, sizeof(maxw), cudaMemcpyDeviceToHost, st));
+    CKF(cudaStreamSynchronize(st));
+    if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
+    h->max_vertex_netweight = (int64_t)maxw;
+
+    // ---- state
+    uint8_t *part = nullptr;
+    CKF(dalloc(h, &part, n));
+    k_copy_part<<<grid_for(n, 256), 256, 0, st>>>(part_in, part, n);
+    d.part = part;
+    const int64_t entries = (int64_t)m * k;
+    const int64_t words = (entries * w + 3) / 4;
+    uint32_t *phi = nullptr;
+    CKF(dalloc(h, &phi, words));
+    CKF(cudaMemsetAsync(phi, 0, sizeof(uint32_t) * (size_t)(words < 1 ? 1 : words), st));
+    d.phi = phi;
+    const size_t rec_bytes = k <= 32 ? sizeof(Rec16) : sizeof(Rec32);
+    uint4 *rec = nullptr;
+    CKF(dalloc(h, &rec, (int64_t)m * (int64_t)(rec_bytes / 16)));
+    d.rec = rec;
+    int64_t *small = nullptr;
+    CKF(dalloc(h, &small, 2 * 64 + 8));
+    d.bw = small;
+    d.obj = small + 64;
+
+    // ---- per-sub-round scratch
+    uint8_t *sub_list = nullptr;
+    uint16_t *sub_start = nullptr;
+    uint64_t *cand = nullptr;
+    int32_t *cand_cnt = nullptr;
+    int64_t *tot = nullptr, *tie = nullptr;
+    unsigned long long *hist = nullptr;
+    Sel *sel = nullptr;
+    CKF(dalloc(h, &sub_list, (int64_t)d.n_ranges * kRange));
+    CKF(dalloc(h, &sub_start, (int64_t)d.n_ranges * (d.S + 1)));
+    CKF(dalloc(h, &cand, (int64_t)d.n_ranges * kRange));
+    CKF(dalloc(h, &cand_cnt, d.n_ranges));
+    CKF(dalloc(h, &tot, 64));
+    CKF(dalloc(h, &hist, (int64_t)k * kBins));
+    CKF(dalloc(h, &sel, 64));
+    CKF(dalloc(h, &tie, (int64_t)k * d.n_tiles));
+    CKF(cudaMemsetAsync(tot, 0, sizeof(int64_t) * 64, st));
+    CKF(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (size_t)k * kBins, st));
+    d.sub_list = sub_list;
+    d.sub_start = sub_start;
+    d.cand = cand;
+    d.cand_cnt = cand_cnt;
+    d.tot = tot;
+    d.hist = hist;
+    d.sel = sel;
+    d.tie = tie;
+    CKF(dalloc(h, &h->d_round, 4));
+
+    rc = init_state(h);
+    if (rc != HGP_OK) return fail(rc);
+
+    // ---- L_max = floor((1 + eps) * ceil(c(V) / k))  (Sec. 2)
+    int64_t bw[64];
+    CKF(cudaMemcpyAsync(bw, d.bw, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, st));
+    CKF(cudaStreamSynchronize(st));
+    int64_t total = 0;
+    for (int i = 0; i < k; ++i) total += bw[i];
+    h->total_weight = total;
+    const int64_t avg = (total + k - 1) / k;
+    d.lmax = (int64_t)floor((1.0 + eps) * (double)avg);
+
+    // the int64 offsets and the int32 partition copy are no longer needed
+    for (int i = 0; i < h->n_allocs; ++i) {
+        if (h->allocs[i] == off64 || h->allocs[i] == part_in || h->allocs[i] == block_sums ||
+            h->allocs[i] == tmp) {
+            cudaFree(h->allocs[i]);
+            h->allocs[i] = nullptr;
+        }
+    }
+    rc = ensure_stats(h, 16);
+    if (rc != HGP_OK) return fail(rc);
+    *out = h;
+    return HGP_OK;
+#undef CKF
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void hgp_default_options(hgp_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->subrounds = 4;
+}
+
+const char *hgp_strerror(int code)
+{
+    switch (code) {
+    case HGP_OK: return "ok";
+    case HGP_ERR_INVALID: return "invalid argument";
+    case HGP_ERR_OOM: return "out of memory";
+    case HGP_ERR_UNSUPPORTED: return "unsupported size or parameter";
+    case HGP_ERR_CUDA: return "CUDA error";
+    case HGP_ERR_TIMEOUT: return "device wait timed out";
+    case HGP_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int hgp_create(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
+               const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+               const int32_t *initial_part, const hgp_options *opt, hgp_handle **out)
+{
+    return create_impl(n, m, net_offsets, pins, vertex_w, net_w, k, eps, initial_part, opt, out, false);
+}
+
+int hgp_create_device(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
+                      const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+                      const int32_t *initial_part, const hgp_options *opt, hgp_handle **out)
+{
+    return create_impl(n, m, net_offsets, pins, vertex_w, net_w, k, eps, initial_part, opt, out, true);
+}
+
+void hgp_destroy(hgp_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    for (int i = 0; i < h->n_allocs; ++i)
+        if (h->allocs[i]) cudaFree(h->allocs[i]);
+    if (h->d.stats) cudaFree(h->d.stats);
+    if (h->h_stats) cudaFreeHost(h->h_stats);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    (void)cudaGetLastError();
+    delete h;
+}
+
+int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
+{
+    if (!h || !part) return HGP_ERR_INVALID;
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    int32_t *tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    int rc = HGP_OK;
+    int32_t err = 0;
+    cudaError_t e = cudaMemcpyAsync(tmp, part, sizeof(int32_t) * (size_t)d.n,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) {
+        k_check_vertices<<<grid_for(d.n, 256), 256, 0, st>>>(nullptr, tmp, d.n, d.k, d.err);
+        e = cudaMemcpyAsync(&err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && (err & ERR_INVALID)) rc = HGP_ERR_INVALID;
+    if (e == cudaSuccess && rc == HGP_OK) {
+        k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(tmp, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    if (rc != HGP_OK) return rc;
+    return init_state(h);
+}
+
+int hgp_objective(hgp_handle *h, int64_t *out)
+{
+    if (!h || !out) return HGP_ERR_INVALID;
+    CK(cudaMemcpyAsync(out, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return HGP_OK;
+}
+
+int hgp_objective_from_phi(hgp_handle *h, int64_t *out)
+{
+    if (!h || !out) return HGP_ERR_INVALID;
+    unsigned long long *tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(*tmp), h->stream));
+    cudaError_t e = objective_from_phi(h, reinterpret_cast<int64_t *>(tmp));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    CK(e);
+    return HGP_OK;
+}
+
+int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
+{
+    if (!h || !part) return HGP_ERR_INVALID;
+    Dev &d = h->d;
+    cudaStream_t st = h->stream;
+    if (on_device) {
+        k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, part, d.n);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        return HGP_OK;
+    }
+    int32_t *tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, tmp, d.n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part, tmp, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(tmp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    CK(e);
+    return HGP_OK;
+}
+
+int hgp_get_block_weights(hgp_handle *h, int64_t *w)
+{
+    if (!h || !w) return HGP_ERR_INVALID;
+    CK(cudaMemcpyAsync(w, h->d.bw, sizeof(int64_t) * h->d.k, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return HGP_OK;
+}
+
+int hgp_get_phi(hgp_handle *h, int32_t *phi)
+{
+    if (!h || !phi) return HGP_ERR_INVALID;
+    Dev &d = h->d;
+    const int64_t total = (int64_t)d.m * d.k;
+    if (total == 0) return HGP_OK;
+    int32_t *tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)total, h->stream));
+    k_widen_phi<<<grid_for(total, 256), 256, 0, h->stream>>>(d, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi, tmp, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    CK(e);
+    return HGP_OK;
+}
+
+int hgp_get_lambda(hgp_handle *h, uint64_t *lam)
+{
+    if (!h || !lam) return HGP_ERR_INVALID;
+    Dev &d = h->d;
+    if (d.m == 0) return HGP_OK;
+    uint64_t *tmp = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint64_t) * (size_t)d.m, h->stream));
+    if (d.k <= 32) k_get_lambda<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp);
+    else k_get_lambda<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lam, tmp, sizeof(uint64_t) * (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    CK(e);
+    return HGP_OK;
+}
+
+int hgp_get_info(hgp_handle *h, int32_t *n, int32_t *m, int32_t *k, int64_t *pins, int64_t *lmax,
+                 int32_t *phi_width, int32_t *wide_nets, int64_t *next_round)
+{
+    if (!h) return HGP_ERR_INVALID;
+    if (n) *n = h->d.n;
+    if (m) *m = h->d.m;
+    if (k) *k = h->d.k;
+    if (pins) *pins = h->d.P;
+    if (lmax) *lmax = h->d.lmax;
+    if (phi_width) *phi_width = h->d.phi_w;
+    if (wide_nets) *wide_nets = h->n_wide;
+    if (next_round) *next_round = h->next_round;
+    return HGP_OK;
+}
+
+int hgp_refine(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
+{
+    if (!h || rounds < 0) return HGP_ERR_INVALID;
+    return refine_rounds(h, rounds, stats);
+}
+
+int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
+{
+    if (!h || !target || !gain || s < 0 || s >= h->d.S) return HGP_ERR_INVALID;
+    return debug_candidates(h, s, target, gain);
+}
+
+}  // extern "C"
+
+namespace hgp {
+
+cudaError_t objective_from_phi(hgp_handle *h, int64_t *d_out)
+{
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(int64_t), h->stream);
+    if (e != cudaSuccess) return e;
+    k_obj_from_phi<<<grid_for(h->d.m, 256), 256, 0, h->stream>>>(h->d, reinterpret_cast<unsigned long long *>(d_out));
+    return cudaGetLastError();
+}
+
+}  // namespace hgp

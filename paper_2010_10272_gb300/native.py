@@ -1,0 +1,243 @@
+"""ctypes binding of libhgp (include/hgp.h).  Argument marshalling only.
+
+Host arrays are numpy arrays; device arrays are torch CUDA tensors (their data pointers are
+passed through).  Streams are torch streams or raw cudaStream_t integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhgp.so")
+_lock = threading.Lock()
+_lib = None
+
+STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight")
+
+HGP_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "CUDA", 5: "TIMEOUT",
+                6: "INTERNAL"}
+
+
+class HGPError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({strerror(code)})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("subrounds", ctypes.c_int32), ("phi_width", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("debug", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in STAT_FIELDS]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Loads libhgp.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libhgp.so not built ({_LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.hgp_default_options.argtypes = [P]
+        lib.hgp_default_options.restype = None
+        lib.hgp_strerror.argtypes = [ctypes.c_int]
+        lib.hgp_strerror.restype = ctypes.c_char_p
+        for name in ("hgp_create", "hgp_create_device"):
+            fn = getattr(lib, name)
+            fn.argtypes = [i32, i32, P, P, P, P, i32, f64, P, P, P]
+            fn.restype = ctypes.c_int
+        lib.hgp_refine.argtypes = [P, i32, P]
+        lib.hgp_set_partition.argtypes = [P, P, i32]
+        lib.hgp_objective.argtypes = [P, P]
+        lib.hgp_objective_from_phi.argtypes = [P, P]
+        lib.hgp_get_partition.argtypes = [P, P, i32]
+        lib.hgp_get_block_weights.argtypes = [P, P]
+        lib.hgp_get_phi.argtypes = [P, P]
+        lib.hgp_get_lambda.argtypes = [P, P]
+        lib.hgp_get_info.argtypes = [P, P, P, P, P, P, P, P, P]
+        lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
+        for name in ("hgp_refine", "hgp_set_partition", "hgp_objective", "hgp_objective_from_phi",
+                     "hgp_get_partition", "hgp_get_block_weights", "hgp_get_phi", "hgp_get_lambda",
+                     "hgp_get_info", "hgp_debug_candidates"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.hgp_destroy.argtypes = [P]
+        lib.hgp_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load_library().hgp_strerror(int(code)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def default_options() -> Options:
+    o = Options()
+    load_library().hgp_default_options(ctypes.byref(o))
+    return o
+
+
+def _check(code: int, what: str):
+    if code != HGP_OK:
+        raise HGPError(code, what)
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class HGP:
+    """One hypergraph + partition resident on the GPU (a handle of libhgp).
+
+    Host inputs are numpy arrays: net_off int64[m+1], pins int32[P], part int32[n],
+    vertex_w / net_w int32 or None.  With ``device=True`` every array is a torch CUDA tensor
+    of the same dtype instead.
+    """
+
+    def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None, *,
+                 subrounds: int = 4, seed: int = 0, phi_width: int = 0, debug: int = 0,
+                 graph: int = 0, stream=None, device: bool = False):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        o = default_options()
+        o.subrounds, o.phi_width, o.seed = int(subrounds), int(phi_width), int(seed)
+        o.debug, o.graph = int(debug), int(graph)
+        sh = _stream_handle(stream)
+        o.cuda_stream = ctypes.c_void_p(sh) if sh else None
+        self.n, self.m, self.k = int(n), int(m), int(k)
+        if device:
+            args = [_dptr(net_off), _dptr(pins), _dptr(vertex_w), _dptr(net_w)]
+            pt = _dptr(part)
+            fn = self._lib.hgp_create_device
+        else:
+            keep = [_host(net_off, np.int64), _host(pins, np.int32), _host(vertex_w, np.int32),
+                    _host(net_w, np.int32), _host(part, np.int32)]
+            args = [_hptr(x) for x in keep[:4]]
+            pt = _hptr(keep[4])
+            fn = self._lib.hgp_create
+        rc = fn(self.n, self.m, *args, self.k, float(eps), pt, ctypes.byref(o), ctypes.byref(self._h))
+        _check(rc, "hgp_create")
+
+    @classmethod
+    def from_hypergraph(cls, hg, part=None, **kw):
+        return cls(hg.n, hg.m, hg.net_off, hg.pins, hg.k, hg.eps,
+                   hg.part if part is None else part, hg.vertex_w, hg.net_w, **kw)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.hgp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- refinement
+    def refine(self, rounds: int, stats: bool = True):
+        """Runs `rounds` LP rounds; returns int64 [rounds x 5] statistics (or None)."""
+        if stats:
+            buf = (RoundStats * max(1, rounds))()
+            _check(self._lib.hgp_refine(self._h, int(rounds), buf), "hgp_refine")
+            return np.array([[getattr(buf[i], f) for f in STAT_FIELDS] for i in range(rounds)],
+                            dtype=np.int64).reshape(rounds, len(STAT_FIELDS))
+        _check(self._lib.hgp_refine(self._h, int(rounds), None), "hgp_refine")
+        return None
+
+    def set_partition(self, part, device: bool = False):
+        if device:
+            _check(self._lib.hgp_set_partition(self._h, _dptr(part), 1), "hgp_set_partition")
+        else:
+            p = _host(part, np.int32)
+            _check(self._lib.hgp_set_partition(self._h, _hptr(p), 0), "hgp_set_partition")
+
+    # -- results
+    def objective(self) -> int:
+        out = ctypes.c_int64()
+        _check(self._lib.hgp_objective(self._h, ctypes.byref(out)), "hgp_objective")
+        return out.value
+
+    def objective_from_phi(self) -> int:
+        out = ctypes.c_int64()
+        _check(self._lib.hgp_objective_from_phi(self._h, ctypes.byref(out)), "hgp_objective_from_phi")
+        return out.value
+
+    def partition(self, out_device=None) -> Optional[np.ndarray]:
+        if out_device is not None:
+            _check(self._lib.hgp_get_partition(self._h, _dptr(out_device), 1), "hgp_get_partition")
+            return None
+        out = np.empty(self.n, dtype=np.int32)
+        _check(self._lib.hgp_get_partition(self._h, _hptr(out), 0), "hgp_get_partition")
+        return out
+
+    def block_weights(self) -> np.ndarray:
+        out = np.empty(self.k, dtype=np.int64)
+        _check(self._lib.hgp_get_block_weights(self._h, _hptr(out)), "hgp_get_block_weights")
+        return out
+
+    def phi(self) -> np.ndarray:
+        out = np.empty((self.m, self.k), dtype=np.int32)
+        _check(self._lib.hgp_get_phi(self._h, _hptr(out)), "hgp_get_phi")
+        return out
+
+    def lam(self) -> np.ndarray:
+        out = np.empty(self.m, dtype=np.uint64)
+        _check(self._lib.hgp_get_lambda(self._h, _hptr(out)), "hgp_get_lambda")
+        return out
+
+    def info(self) -> dict:
+        vals = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(),
+                ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
+        _check(self._lib.hgp_get_info(self._h, *[ctypes.byref(v) for v in vals]), "hgp_get_info")
+        keys = ("n", "m", "k", "pins", "lmax", "phi_width", "wide_nets", "next_round")
+        return {kk: v.value for kk, v in zip(keys, vals)}
+
+    def debug_candidates(self, s: int):
+        t = np.empty(self.n, dtype=np.int32)
+        g = np.empty(self.n, dtype=np.int64)
+        _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
+               "hgp_debug_candidates")
+        return t, g

@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Every quantity is integer, so the bar is bit-exact: partition, Phi table, Lambda bitsets,
+block weights, objective and per-round (objective, candidates, approved, eligible, max
+block weight).  Sizes span several 2048-vertex tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from golden_io import load_all
+from paper_2010_10272_gb300 import HGP
+from parity_util import compare_state, run_both
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = load_all()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_10272_gb300 import build as b
+    b.build()
+    import oracle as o
+    o.build()
+
+
+
+
+# ---------------------------------------------------------------- hand-derived fixtures
+@pytest.mark.parametrize("g", GOLDEN, ids=[g.name for g in GOLDEN])
+def test_golden(g):
+    h = HGP(g.n, g.m, g.net_off, g.pins, g.k, g.eps, g.part, g.vertex_w, g.net_w,
+            subrounds=g.subrounds, seed=g.seed)
+    assert h.info()["lmax"] == g.lmax
+    assert h.objective() == g.objective
+    stats = h.refine(len(g.rounds))
+    assert [tuple(r) for r in stats.tolist()] == list(g.rounds)
+    np.testing.assert_array_equal(h.partition(), g.final)
+
+
+# ---------------------------------------------------------------- seeded random instances
+CASES = [
+    # (seed, n, m, k, max_size, weighted, S, phi_width)
+    (1, 5000, 4000, 2, 6, False, 4, 0),
+    (2, 7001, 6000, 3, 8, True, 1, 0),
+    (3, 6143, 9000, 8, 12, False, 4, 0),
+    (4, 9999, 8000, 16, 10, True, 7, 2),
+    (5, 4097, 5000, 31, 9, False, 2, 4),
+    (6, 4500, 5000, 32, 9, True, 3, 0),
+    (7, 6000, 5500, 33, 9, False, 4, 1),
+    (8, 8191, 7000, 64, 12, True, 5, 0),
+    (9, 3000, 2000, 64, 40, False, 64, 2),
+    (10, 2049, 2500, 5, 300, True, 4, 1),    # nets > 255 pins -> wide tier with 1-byte Phi
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"s{c[0]}-n{c[1]}-k{c[3]}-S{c[6]}-w{c[7]}" for c in CASES])
+def test_random_instances(case):
+    seed, n, m, k, max_size, weighted, S, w = case
+    hg = synth.random_small(seed, n, m, k, max_size=max_size, weighted=weighted, rounds=4)
+    h, o, _ = run_both(hg, rounds=4, S=S, seed=seed, phi_width=w)
+    if case[0] == 10:
+        assert h.info()["wide_nets"] > 0
+
+
+def test_small_config_full_size():
+    hg = synth.config_small()
+    run_both(hg, S=4)
+
+
+def test_batch_members():
+    for hg in synth.config_batch(count=6, n_hi=20_000):
+        run_both(hg, S=4)
+
+
+def test_powerlaw_scaled_with_wide_tier():
+    hg = synth.config_powerlaw(scale=0.002)          # n = m = 100k, k = 64, weighted nets
+    h, o, _ = run_both(hg, S=4, phi_width=1, check_phi=False)
+    assert h.info()["wide_nets"] > 0
+
+
+def test_powerlaw_scaled_u16():
+    hg = synth.config_powerlaw(scale=0.004)
+    h, _, stats = run_both(hg, S=4, check_phi=False)
+    assert h.info()["phi_width"] == 2
+    assert stats[0, 2] > 0
+
+
+# ---------------------------------------------------------------- approval edge cases
+def test_saturated_blocks_and_large_gains():
+    """Net weights up to 2^20 push gains past the 4094 exact histogram bins, so the
+    threshold is resolved digit by digit; a tight eps saturates every block."""
+    rng = np.random.default_rng(11)
+    hg = synth.random_small(11, 6000, 7000, 4, max_size=5, weighted=False, eps=0.01, rounds=5)
+    hg.net_w = rng.integers(1, 1 << 20, size=hg.m, dtype=np.int32)
+    hg.vertex_w = rng.integers(1, 3, size=hg.n, dtype=np.int32)
+    run_both(hg, S=2)
+
+
+def test_ties_everywhere_unit_weights():
+    # many equal gains and unit weights: ties at the threshold span many tiles
+    hg = synth.planted(3, 60_000, 60_000, 2, synth.poisson_sizes(2.0), 0.9, 0.45, eps=0.001, rounds=3)
+    run_both(hg, S=1)
+
+
+def test_unbalanced_start():
+    hg = synth.random_small(12, 5000, 5000, 6, max_size=6, weighted=True, eps=0.03, rounds=5)
+    part = hg.part.copy()
+    part[: hg.n // 2] = 0
+    run_both(hg, S=3, part=part)
+
+
+# ---------------------------------------------------------------- degenerate inputs
+def test_degenerate_nets_and_vertices():
+    # empty nets, single-pin nets, isolated vertices, a hub vertex in every other net
+    rng = np.random.default_rng(5)
+    n, m, k = 3000, 4000, 4
+    nets = []
+    for e in range(m):
+        r = e % 5
+        if r == 0:
+            nets.append([])
+        elif r == 1:
+            nets.append([int(rng.integers(0, n))])
+        else:
+            s = set(rng.choice(n - 100, size=int(rng.integers(2, 8)), replace=False).tolist())
+            if e % 2 == 0:
+                s.add(n - 1)          # hub
+            nets.append(sorted(s))
+    off = np.zeros(m + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(x) for x in nets])
+    pins = np.array([v for x in nets for v in x], dtype=np.int32)
+    part = rng.integers(0, k, size=n).astype(np.int32)
+    hg = synth.Hypergraph("degenerate", n, m, k, 0.05, off, pins, part, None, None, 4)
+    run_both(hg, S=2)
+
+
+def test_no_nets_and_single_vertex():
+    for n, m in ((1, 0), (5, 0), (1, 3)):
+        off = np.zeros(m + 1, dtype=np.int64)
+        if m == 3:
+            off[:] = [0, 0, 1, 1]
+        pins = np.zeros(int(off[-1]), dtype=np.int32)
+        hg = synth.Hypergraph("tiny", n, m, 2, 0.5, off, pins, np.zeros(n, np.int32), None, None, 2)
+        run_both(hg, S=1)
+
+
+def test_all_vertices_in_one_block_k64():
+    hg = synth.random_small(13, 3000, 3000, 64, max_size=6, rounds=3)
+    run_both(hg, S=4, part=np.zeros(hg.n, np.int32))
+
+
+# ---------------------------------------------------------------- gain step alone
+@pytest.mark.parametrize("k,S,weighted", [(2, 4, False), (8, 3, True), (64, 2, True), (33, 1, False)])
+def test_candidates_match_oracle(k, S, weighted):
+    hg = synth.random_small(20 + k, 9000, 8000, k, max_size=10, weighted=weighted)
+    h = HGP.from_hypergraph(hg, subrounds=S, seed=3)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=3)
+    for step in range(2):
+        for s in range(S):
+            t_h, g_h = h.debug_candidates(s)
+            t_o, g_o = o.candidates(s)
+            np.testing.assert_array_equal(t_h, t_o)
+            np.testing.assert_array_equal(g_h, g_o)
+        h.refine(1)
+        o.refine(1)
+
+
+# ---------------------------------------------------------------- API semantics
+def test_refine_split_equals_whole():
+    hg = synth.random_small(30, 8000, 8000, 8, max_size=8, weighted=True, rounds=6)
+    run_both(hg, rounds=6, S=4, chunks=[1, 2, 3])
+    run_both(hg, rounds=6, S=4, chunks=[6])
+
+
+def test_repeat_runs_identical():
+    hg = synth.random_small(31, 10000, 9000, 16, max_size=8, weighted=True, rounds=4)
+    res = []
+    for _ in range(3):
+        h = HGP.from_hypergraph(hg, subrounds=4, seed=9)
+        st = h.refine(4)
+        res.append((st, h.partition(), h.phi()))
+    for st, p, phi in res[1:]:
+        np.testing.assert_array_equal(st, res[0][0])
+        np.testing.assert_array_equal(p, res[0][1])
+        np.testing.assert_array_equal(phi, res[0][2])
+
+
+def test_set_partition_equals_fresh_create():
+    hg = synth.random_small(32, 6000, 6000, 4, max_size=7, rounds=3)
+    h = HGP.from_hypergraph(hg, subrounds=4)
+    h.refine(3)
+    h.set_partition(hg.part)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    compare_state(h, o)
+    np.testing.assert_array_equal(h.refine(3), o.refine(3)[0])
+    compare_state(h, o)
+
+
+def test_device_inputs_and_stream():
+    hg = synth.random_small(33, 5000, 5000, 8, max_size=7, weighted=True, rounds=3)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    s = torch.cuda.Stream()
+    h = HGP(hg.n, hg.m, t(hg.net_off), t(hg.pins), hg.k, hg.eps, t(hg.part), t(hg.vertex_w),
+            t(hg.net_w), subrounds=4, device=True, stream=s)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    np.testing.assert_array_equal(h.refine(3), o.refine(3)[0])
+    out = torch.empty(hg.n, dtype=torch.int32, device=dev)
+    h.partition(out_device=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), o.partition())
+
+
+def test_check_mode():
+    hg = synth.random_small(34, 4000, 4000, 5, max_size=7, weighted=True, rounds=3)
+    h = HGP.from_hypergraph(hg, subrounds=2, debug=1)
+    h.refine(3)
+
+
+# ---------------------------------------------------------------- error codes
+def _err(fn):
+    from paper_2010_10272_gb300 import HGPError
+    with pytest.raises(HGPError) as ei:
+        fn()
+    return ei.value.code
+
+
+def test_error_codes():
+    off = np.array([0, 2, 3], dtype=np.int64)
+    pins = np.array([0, 1, 2], dtype=np.int32)
+    part = np.array([0, 1, 0], dtype=np.int32)
+    ok = dict(n=3, m=2, net_off=off, pins=pins, k=2, eps=0.1, part=part)
+
+    def mk(**kw):
+        a = dict(ok)
+        a.update(kw)
+        return lambda: HGP(a["n"], a["m"], a["net_off"], a["pins"], a["k"], a["eps"], a["part"],
+                           a.get("vertex_w"), a.get("net_w"), subrounds=a.get("subrounds", 4))
+    HGP(3, 2, off, pins, 2, 0.1, part).close()
+    assert _err(mk(k=1)) == 1
+    assert _err(mk(k=65)) == 3
+    assert _err(mk(eps=0.0)) == 1
+    assert _err(mk(eps=1.0)) == 1
+    assert _err(mk(part=np.array([0, 2, 0], np.int32))) == 1
+    assert _err(mk(pins=np.array([0, 5, 2], np.int32))) == 1                   # out of range
+    assert _err(mk(pins=np.array([1, 0, 2], np.int32))) == 1                   # not increasing
+    assert _err(mk(pins=np.array([1, 1, 2], np.int32))) == 1                   # duplicate
+    assert _err(mk(net_off=np.array([0, 3, 2], np.int64))) == 1                # decreasing
+    assert _err(mk(net_off=np.array([1, 2, 3], np.int64))) == 1                # not from 0
+    assert _err(mk(vertex_w=np.array([1, 0, 1], np.int32))) == 1
+    assert _err(mk(net_w=np.array([1, -3], np.int32))) == 1
+    assert _err(mk(subrounds=65)) == 3
+    # vertex 1 lies in both nets; their weights sum to 2^31 -> unsupported
+    assert _err(mk(net_w=np.array([1 << 30, 1 << 30], np.int32),
+                   pins=np.array([0, 1, 1, 2], np.int32),
+                   net_off=np.array([0, 2, 4], np.int64))) == 3
