@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark of GPU label-propagation refinement (LP-refine pins/s per round).
+
+A step is one refinement of `rounds` synchronous LP rounds (every row of the hot path:
+sub-round lists, gain + best target, approval, apply with Phi/Lambda/objective update) of
+the whole instance, started from the instance's start partition.  The partition is reset on
+the device between steps, outside the timed region.  value = pins x rounds / step time,
+i.e. P divided by the mean wall time of one round, summed over ranks (replicas).
+
+Default workload: the large power-law instance (n = m = 5*10^7, |e| = min(2 + Zipf(2.1),
+10^5), k = 64, net weights U{1..10}, 5 rounds), ~3.4*10^8 pins, far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload powerlaw|rownet|small]
+  python bench.py --impl reference     # the CPU oracle on a bounded sample, same metric
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "LP-refine pins/s per round, % HBM roofline; batched vs plain; p50/p99 latency"
+UNIT = "pins/s"
+CACHE = os.environ.get("HGP_SYNTH_CACHE", "/tmp/hgp_synth_cache")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "powerlaw": (synth.config_powerlaw, "power-law n=m=5e7 |e|=min(2+Zipf(2.1),1e5) k=64 omega=U{1..10}"),
+    "rownet": (synth.config_rownet, "row-net 2e6 x 2e6 nnz/row=1+Poisson(9) banded k=8"),
+    "small": (synth.config_small, "planted n=m=1e4 k=2 |e|=2+Poisson(4)"),
+}
+# bounded oracle sample per workload: same recipe, smaller scale
+SAMPLE_SCALE = {"powerlaw": 0.01, "rownet": 0.1, "small": 1.0}
+
+
+# ------------------------------------------------------------------------------ inputs
+def load_instance(name: str, scale: float):
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, f"{name}_{scale:g}.npz")
+    fn = WORKLOADS[name][0]
+    if os.path.exists(path):
+        try:
+            z = np.load(path, allow_pickle=False)
+            meta = json.loads(str(z["meta"]))
+            return synth.Hypergraph(meta["name"], meta["n"], meta["m"], meta["k"], meta["eps"],
+                                    z["net_off"], z["pins"], z["part"],
+                                    z["vertex_w"] if "vertex_w" in z.files else None,
+                                    z["net_w"] if "net_w" in z.files else None, meta["rounds"])
+        except Exception:
+            pass
+    hg = fn(scale=scale)
+    arrays = {"net_off": hg.net_off, "pins": hg.pins, "part": hg.part}
+    if hg.vertex_w is not None:
+        arrays["vertex_w"] = hg.vertex_w
+    if hg.net_w is not None:
+        arrays["net_w"] = hg.net_w
+    meta = dict(n=hg.n, m=hg.m, k=hg.k, eps=hg.eps, rounds=hg.rounds, name=hg.name)
+    try:
+        tmp = path + f".tmp{os.getpid()}.npz"
+        np.savez(tmp, meta=json.dumps(meta), **arrays)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return hg
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ helpers
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(hg, info, stats, S):
+    """Algorithmic bytes per launch of the gain and apply kernels (the data the method must
+    move, without sector over-fetch), averaged over the launches of one refinement.
+
+    gain, per active vertex: vtx_off 4 B + Pi 1 B + c 4 B (0 if unit); per visited
+    incidence: net id 4 B + omega 4 B (0 if unit) + Lambda ceil(k/8) B rounded to 4 or 8
+    + Phi(e,a) w B + moved flag 1 B.  Every vertex is active once per round and visits all
+    its incidences, so one round = n vertices and P incidences.
+    apply, per approved move: Pi write 1 B + 2 block-weight atomics 16 B + candidate 8 B;
+    per moved incidence: net id 4 B + Phi(e,a), Phi(e,t) read+write 4w B + Lambda/S1
+    read-modify-write 2 x 2 x lam B + moved flag 1 B.
+    """
+    k, w = info["k"], info["phi_width"]
+    lam = 4 if k <= 32 else 8
+    per_vertex = 4 + 1 + (4 if hg.vertex_w is not None else 0)
+    per_inc = 4 + (4 if hg.net_w is not None else 0) + lam + w + 1
+    rounds = stats.shape[0]
+    gain_total = rounds * (hg.n * per_vertex + info["pins"] * per_inc)
+    moved_pins = int(stats[:, 5].sum())
+    approved = int(stats[:, 2].sum())
+    apply_total = approved * (1 + 16 + 8) + moved_pins * (4 + 4 * w + 4 * lam + 1)
+    launches = rounds * S
+    return {"gain": gain_total / launches, "apply": apply_total / launches}
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """dram bytes per launch recorded in profiles/ for `kernel` on `workload`, if the kernel
+    source has not changed since the capture (its sha256 is stored with the figure)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    src = os.path.join(ROOT, "paper_2010_10272_gb300", "csrc", "hgp_refine.cu")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if cur != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() and args.impl != "reference" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ oracle
+def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None):
+    """Times the CPU oracle (single thread) on a bounded sample of the workload: the same
+    recipe at a smaller scale, `rounds` rounds per step from the start partition."""
+    import oracle
+    scale = SAMPLE_SCALE[workload]
+    hg = load_instance(workload, scale)
+    rounds = rounds_override or hg.rounds
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+        t1 = time.perf_counter()
+        o.refine(rounds)
+        t2 = time.perf_counter()
+        o.close()
+        if i >= warmup:
+            times.append(t2 - t1)
+    per_step = statistics.mean(times)
+    value = hg.num_pins * rounds / per_step
+    sample = (f"{hg.name}: P={hg.num_pins} pins, {rounds} rounds per step from the start "
+              f"partition (scale {scale:g} of the workload), oracle creation excluded")
+    return value, per_step, sample, hg
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1], "sample": sample, "rounds": hg.rounds,
+                   "subrounds": 4},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2010_10272_gb300 import HGP, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    t_gen = time.perf_counter()
+    hg = load_instance(args.workload, args.scale)
+    t_gen = time.perf_counter() - t_gen
+    R, S = hg.rounds, args.subrounds
+    P = hg.num_pins
+
+    to_dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d_off, d_pins, d_part = to_dev(hg.net_off), to_dev(hg.pins), to_dev(hg.part)
+    d_vw, d_nw = to_dev(hg.vertex_w), to_dev(hg.net_w)
+    stream = torch.cuda.current_stream(dev)
+    h = HGP(hg.n, hg.m, d_off, d_pins, hg.k, hg.eps, d_part, d_vw, d_nw, subrounds=S, device=True,
+            stream=stream)
+    info = h.info()
+    del d_off, d_pins, d_vw, d_nw
+
+    def step(timed_events=None):
+        h.set_partition(d_part, device=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        if timed_events is not None:
+            timed_events[0].record(stream)
+        st = h.refine(R)
+        if timed_events is not None:
+            timed_events[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    h.set_profiling(True)
+    ms, launches, stats = [], 0, None
+    for _ in range(args.steps):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        l0 = h.launch_count()
+        st = step(ev)
+        launches += h.launch_count() - l0
+        ms.append(ev[0].elapsed_time(ev[1]))
+        stats = st
+    clocks = sampler.stop()
+    prof = h.profile()
+    h.set_profiling(False)
+
+    total_ms = max_over_ranks(sum(ms), world)
+    value = world * args.steps * P * R / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant kernel (gain or apply), from the live per-phase events
+    algo = algorithmic_bytes(hg, info, stats, S)
+    peak, peak_kind = measured_peak_hbm()
+    kern = max(("gain", "apply"), key=lambda kk: prof[kk][0])
+    kname = {"gain": "k_gain", "apply": "k_apply"}[kern]
+    avg_ms = prof[kern][0] / max(1, prof[kern][1])
+    achieved = algo[kern] / (avg_ms / 1e3) / 1e9
+    traffic = traffic_from_profile(kname, args.workload)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": traffic, "algorithmic_bytes_per_launch": algo[kern],
+                "avg_launch_ms": avg_ms}
+    phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+              for k, v in prof.items()}
+    other = "apply" if kern == "gain" else "gain"
+    o_ms = prof[other][0] / max(1, prof[other][1])
+    phases["frac_of_peak_other"] = {"kernel": f"k_{other}",
+                                   "achieved_gbs": algo[other] / (o_ms / 1e3) / 1e9,
+                                   "frac": algo[other] / (o_ms / 1e3) / 1e9 / peak}
+
+    # end to end through the C ABI with host buffers: create (H2D + setup) + refine + result D2H
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hp = [pin(hg.net_off), pin(hg.pins), pin(hg.part), pin(hg.vertex_w), pin(hg.net_w)]
+        h2d = sum(a.nbytes for a in hp if a is not None)
+        d2h = hg.n * 4 + R * 8 * 6
+        del h
+        torch.cuda.empty_cache()
+        times = []
+        for i in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            h2 = HGP(hg.n, hg.m, hp[0], hp[1], hg.k, hg.eps, hp[2], hp[3], hp[4], subrounds=S,
+                     stream=stream)
+            h2.refine(R)
+            part_out = h2.partition()
+            t1 = time.perf_counter()
+            h2.close()
+            if i > 0:
+                times.append(t1 - t0)
+            del part_out
+        e2e_t = max_over_ranks(statistics.mean(times), world)
+        e2e = {"value": world * P * R / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1e3, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, cstep, sample, _ = oracle_sample(args.workload, 1, 0)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1], "n": hg.n, "m": hg.m, "pins": P,
+                   "k": hg.k, "eps": hg.eps, "rounds": R, "subrounds": S,
+                   "phi_width": info["phi_width"], "wide_nets": info["wide_nets"],
+                   "lmax": info["lmax"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (instance state ~10 GB resident in HBM)",
+                   "step": f"reset start partition (untimed) + {R} LP rounds"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "phases": phases,
+        "rounds_stats": {"objective": stats[:, 0].tolist(), "approved": stats[:, 2].tolist(),
+                         "eligible": stats[:, 3].tolist(), "moved_pins": stats[:, 5].tolist()},
+        "setup_s": {"generate_or_load": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="powerlaw")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--subrounds", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -77,7 +77,17 @@ typedef struct {
     int64_t approved;         /* moves applied in the round */
     int64_t eligible;         /* eligible vertices in the round */
     int64_t max_block_weight; /* max_i c(V_i) after the round */
+    int64_t moved_pins;       /* sum of d(u) over the vertices moved in the round */
 } hgp_round_stats;
+
+/* Device time per phase of the rounds, from CUDA events recorded on the handle's stream
+ * around each kernel while profiling is on (hgp_set_profiling).  Phases: 0 sub-round lists,
+ * 1 gain and best target, 2 approval, 3 apply (Phi, Lambda, objective), 4 end of round. */
+#define HGP_PHASES 5
+typedef struct {
+    double ms[HGP_PHASES];         /* accumulated milliseconds */
+    int64_t launches[HGP_PHASES];  /* kernel launches accumulated into ms[] */
+} hgp_profile;
 
 /* Fills *opt with the defaults. */
 void hgp_default_options(hgp_options *opt);
@@ -157,6 +167,16 @@ int hgp_get_info(hgp_handle *h, int32_t *n, int32_t *m, int32_t *k, int64_t *pin
  * block); gain: host int64[n] (0 where target is -1).
  */
 int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain);
+
+/* Turns per-phase event timing on (enable != 0) or off, and clears the accumulated profile.
+ * While on, hgp_refine synchronises the handle's stream before returning. */
+int hgp_set_profiling(hgp_handle *h, int32_t enable);
+
+/* Profile accumulated since profiling was last enabled. */
+int hgp_get_profile(hgp_handle *h, hgp_profile *out);
+
+/* Number of kernels the handle has launched since creation (all phases, setup included). */
+int hgp_get_launch_count(hgp_handle *h, int64_t *out);
 
 /* Frees all device memory of the handle (NULL is allowed). */
 void hgp_destroy(hgp_handle *h);

@@ -28,6 +28,18 @@ struct hgp_handle {
     cudaGraphExec_t graph_exec = nullptr;
     int32_t graph_rounds = 0;
     int32_t *d_round = nullptr;   // device copy of the round counter (graph mode)
+    // kernel launches since creation, and per-phase event timing
+    int64_t launches = 0;
+    int grid_gain = 0;            // persistent grid sizes (CTAs), set at first launch
+    int grid_apply = 0;
+    bool profiling = false;
+    double prof_ms[HGP_PHASES] = {};
+    int64_t prof_launches[HGP_PHASES] = {};
+    cudaEvent_t *events = nullptr;  // pool, 2 per timed phase instance
+    int32_t n_events = 0;
+    int32_t events_used = 0;
+    int32_t *event_phase = nullptr; // phase of each event pair
+    int32_t *event_count = nullptr; // kernel launches inside each event pair
 };
 
 namespace hgp {

@@ -59,7 +59,7 @@ struct Sel {
 };
 
 enum { SEL_ALL = 0, SEL_THRESH = 1, SEL_REFINE = 2 };
-enum { ST_OBJ = 0, ST_CAND = 1, ST_APPR = 2, ST_ELIG = 3, ST_MAXW = 4, ST_N = 5 };
+enum { ST_OBJ = 0, ST_CAND = 1, ST_APPR = 2, ST_ELIG = 3, ST_MAXW = 4, ST_MOVED = 5, ST_N = 6 };
 enum { ERR_INVALID = 1, ERR_UNSUPPORTED = 2 };
 
 struct Dev {

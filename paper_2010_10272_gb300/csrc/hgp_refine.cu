@@ -25,8 +25,11 @@
 //                  the matching bit, so the final bits are right whatever the order).
 //   k_round_end    per-round objective and heaviest block.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
+
+#include <new>
 
 #include "hgp_host.cuh"
 
@@ -109,6 +112,11 @@ template <> struct RecIO<Rec16> {
         s1 = q.x; w = (int32_t)q.y; mv = (int32_t)q.z; lam = q.w; has_lam = true;
     }
     __device__ static Lam load_lam(const Rec16 *r) { return __ldg(&r->lam); }
+    __device__ static void load_full(const Rec16 *r, Lam &s1, int32_t &w, int32_t &mv, Lam &lam)
+    {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(r));
+        s1 = q.x; w = (int32_t)q.y; mv = (int32_t)q.z; lam = q.w;
+    }
     __device__ static void load_b(const Rec16 *r, Lam &lam, int32_t &w)
     {
         const uint4 q = __ldg(reinterpret_cast<const uint4 *>(r));
@@ -124,6 +132,13 @@ template <> struct RecIO<Rec32> {
         s1 = (uint64_t)q.x | ((uint64_t)q.y << 32); w = (int32_t)q.z; mv = (int32_t)q.w;
         lam = 0; has_lam = false;
     }
+    __device__ static void load_full(const Rec32 *r, Lam &s1, int32_t &w, int32_t &mv, Lam &lam)
+    {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(r));
+        const uint2 l = __ldg(reinterpret_cast<const uint2 *>(&r->lam));
+        s1 = (uint64_t)q.x | ((uint64_t)q.y << 32); w = (int32_t)q.z; mv = (int32_t)q.w;
+        lam = (uint64_t)l.x | ((uint64_t)l.y << 32);
+    }
     __device__ static Lam load_lam(const Rec32 *r)
     {
         const uint2 q = __ldg(reinterpret_cast<const uint2 *>(&r->lam));
@@ -136,12 +151,121 @@ template <> struct RecIO<Rec32> {
     }
 };
 
+template <typename Lam> __device__ __forceinline__ uint32_t lo32(Lam x) { return (uint32_t)x; }
+template <typename Lam> __device__ __forceinline__ uint32_t hi32(Lam x)
+{
+    return sizeof(Lam) == 8 ? (uint32_t)((uint64_t)x >> 32) : 0u;
+}
+
+constexpr int kCache = 256;   // incidences per chunk whose (Lambda, omega) stay in shared memory
+
+template <typename Lam>
+struct alignas(16) GainWarp {
+    Lam lamc[kCache];            // Lambda(e) of the chunk's incidences, in flattened order
+    int32_t wc[kCache];          // omega(e)
+    unsigned long long T[32];
+    int32_t W[32], b[32], jb[32], a[32], elig[32];
+    int32_t off[33];
+};
+static_assert(sizeof(GainWarp<uint32_t>) % 16 == 0 && sizeof(GainWarp<uint64_t>) % 16 == 0, "GainWarp alignment");
+static_assert(offsetof(GainWarp<uint32_t>, T) % 8 == 0 && offsetof(GainWarp<uint64_t>, T) % 8 == 0, "GainWarp alignment");
+
+__device__ __forceinline__ int slot_of(const int32_t *off, int32_t i)
+{
+    int v = 0;
+#pragma unroll
+    for (int st = 16; st; st >>= 1)
+        if (off[v + st] <= i) v += st;
+    return v;
+}
+
+// Connectivity of one vertex to every block of T, held as NP bit planes (bit t of plane p is
+// bit p of conn_t), accumulated with a ripple-carry adder on whole bitsets: adding omega(e) to
+// every block of Lambda(e) & T costs O(NP) word operations, whatever the number of blocks.
+// Returns the block of T with the largest conn_t (smallest id among equals) and its value.
+// Requires conn_t <= W(u) < 2^NP.
+template <typename Lam, typename Rec, int NP, bool UNIT>
+__device__ __forceinline__ void bitsliced_best(const GainWarp<Lam> &g, const Rec *recs, const int32_t *inc,
+                                               int32_t i_begin, int32_t i_end, int32_t jb, int32_t off,
+                                               Lam T, int &t_out, int32_t &conn_out)
+{
+    Lam c[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) c[p] = 0;
+    for (int32_t i = i_begin; i < i_end; ++i) {
+        Lam lam;
+        int32_t w;
+        if (i < kCache) {
+            lam = g.lamc[i];
+            w = g.wc[i];
+        } else {
+            RecIO<Rec>::load_b(recs + __ldg(&inc[jb + (i - off)]), lam, w);
+            w &= 0x7fffffff;
+        }
+        const Lam x = lam & T;
+        if (UNIT) {
+            Lam carry = x;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const Lam t = c[p] & carry;
+                c[p] ^= carry;
+                carry = t;
+            }
+        } else {
+            Lam carry = 0;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const Lam ad = ((w >> p) & 1) ? x : (Lam)0;
+                const Lam cp = c[p];
+                c[p] = cp ^ ad ^ carry;
+                carry = (cp & ad) | (carry & (cp ^ ad));
+            }
+        }
+    }
+    Lam C = T;
+#pragma unroll
+    for (int p = NP - 1; p >= 0; --p) {
+        const Lam m = C & c[p];
+        C = m ? m : C;
+    }
+    const int t = lam_bits_ctz(C);
+    int32_t v = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) v |= (int32_t)((c[p] >> t) & 1) << p;
+    t_out = t;
+    conn_out = v;
+}
+
+template <typename Lam, typename Rec, bool UNIT>
+__device__ __forceinline__ void best_by_planes(int np, const GainWarp<Lam> &g, const Rec *recs,
+                                               const int32_t *inc, int32_t ib, int32_t ie, int32_t jb,
+                                               int32_t off, Lam T, int &t, int32_t &conn)
+{
+    if (np <= 4) bitsliced_best<Lam, Rec, 4, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
+    else if (np <= 6) bitsliced_best<Lam, Rec, 6, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
+    else if (np <= 8) bitsliced_best<Lam, Rec, 8, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
+    else bitsliced_best<Lam, Rec, 11, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
+}
+
+constexpr int32_t kPlaneMaxW = 2047;   // W(u) up to this uses bit planes (NP <= 11)
+
+// Persistent: each warp walks warp ranges with a grid stride and takes the vertices of
+// sub-round s of a range 32 at a time (one slot per lane).
+//   pass A  flattened over the chunk's incidences (every record gather issued at once): W,
+//           b(u) (Sec. 5), eligibility (Sec. 6) and T = union of Lambda(e) over the nets with
+//           Phi(e,a) = 1, minus a and the blocks without room for c(u); (Lambda, omega) of each
+//           incidence is kept in shared memory.  Only blocks in T can have a positive gain,
+//           since g_t <= omega({e : Phi(e,a) = 1, t in Lambda(e)}).
+//   pass B  per vertex, conn_t = omega({e in I(u) : t in Lambda(e)}) for all t in T at once in
+//           bit planes, and the arg-max of g_t = b(u) - W + conn_t.
+// A vertex whose incident net weights exceed kPlaneMaxW uses a warp-cooperative pass instead.
 template <typename Rec>
-__global__ void __launch_bounds__(kThreads) k_gain(Dev d, int32_t r, int32_t s, int32_t all_elig,
-                                                   unsigned long long *st_row)
+__global__ void __launch_bounds__(kThreads, 4) k_gain(Dev d, int32_t r, int32_t s, int32_t all_elig,
+                                                      unsigned long long *st_row)
 {
     typedef typename RecIO<Rec>::Lam Lam;
-    extern __shared__ int32_t acc[];   // [k][kThreads]: per-thread connectivity accumulators
+    constexpr bool kWide = sizeof(Lam) == 8;
+    __shared__ GainWarp<Lam> ws[kWarps];
     __shared__ long long slack[64];
     __shared__ unsigned long long tot_s[64];
     __shared__ unsigned long long cnt_s[2];
@@ -156,86 +280,169 @@ __global__ void __launch_bounds__(kThreads) k_gain(Dev d, int32_t r, int32_t s, 
     {
         const unsigned lo = __ballot_sync(kFull, slack[lane] >= 1);
         const unsigned hi = __ballot_sync(kFull, slack[lane + 32] >= 1);
-        if (sizeof(Lam) == 8) feas1 = (Lam)((uint64_t)lo | ((uint64_t)hi << 32));
+        if (kWide) feas1 = (Lam)((uint64_t)lo | ((uint64_t)hi << 32));
         else feas1 = (Lam)lo;
     }
+    GainWarp<Lam> &g = ws[wid];
     const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
-    const int32_t range = blockIdx.x * kWarps + wid;
-    if (range < d.n_ranges) {
-        const int32_t base = range * kRange;
+    const bool unit = d.nw == nullptr;
+    int32_t nelig = 0, ncand = 0;
+    for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
+        const int32_t rbase = range * kRange;
         const uint16_t *ss = d.sub_start + (int64_t)range * (d.S + 1);
         const int32_t beg = ss[s], cnt = (int32_t)ss[s + 1] - beg;
         const uint8_t *list = d.sub_list + (int64_t)range * kRange + beg;
         uint64_t *out = d.cand + (int64_t)range * kRange;
-        int32_t nout = 0, nelig = 0;
+        int32_t nout = 0;
         for (int32_t c0 = 0; c0 < cnt; c0 += 32) {
             const int32_t idx = c0 + lane;
-            int32_t t_best = -1, g_best = 0, cu = 1, ul = 0;
-            bool elig = false;
-            if (idx < cnt) {
+            const bool valid = idx < cnt;
+            int32_t ul = 0, cu = 1, deg = 0, jb = 0, a = 0;
+            if (valid) {
                 ul = list[idx];
-                const int32_t u = base + ul;
-                const int a = d.part[u];
+                const int32_t u = rbase + ul;
+                a = d.part[u];
                 cu = d.vw ? d.vw[u] : 1;
-                const int32_t jb = d.vtx_off[u], je = d.vtx_off[u + 1];
-                int32_t W = 0, b = 0;
-                Lam T = 0;
-                elig = all_elig != 0;
-                // pass A: W, b(u), eligibility, candidate blocks
-                for (int32_t j = jb; j < je; ++j) {
-                    const int32_t e = __ldg(&d.inc[j]);
-                    Lam s1, lam;
-                    int32_t w, mv;
-                    bool has_lam;
-                    RecIO<Rec>::load_a(recs + e, s1, w, mv, lam, has_lam);
-                    w &= 0x7fffffff;
-                    W += w;
-                    if ((s1 >> a) & 1) {
-                        b += w;
-                        T |= has_lam ? lam : RecIO<Rec>::load_lam(recs + e);
-                    }
-                    elig = elig || moved_in_prev_round(mv, r);
+                jb = d.vtx_off[u];
+                deg = d.vtx_off[u + 1] - jb;
+            }
+            g.a[lane] = a;
+            g.jb[lane] = jb;
+            g.W[lane] = 0;
+            g.b[lane] = 0;
+            g.T[lane] = 0;
+            g.elig[lane] = all_elig;
+            int32_t incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t total = __shfl_sync(kFull, incl, 31);
+            const int32_t my_off = incl - deg;
+            g.off[lane] = my_off;
+            if (lane == 31) g.off[32] = total;
+            __syncwarp();
+            // ---- pass A over the flattened incidences
+            for (int32_t i0 = 0; i0 < total; i0 += 64) {
+                const int32_t i1 = i0 + lane, i2 = i0 + 32 + lane;
+                int v1 = 0, v2 = 0, e1 = 0, e2 = 0;
+                if (i1 < total) {
+                    v1 = slot_of(g.off, i1);
+                    e1 = __ldg(&d.inc[g.jb[v1] + (i1 - g.off[v1])]);
                 }
-                if (elig) {
-                    T &= ~((Lam)1 << a);
-                    if (d.vw) {
-                        for (Lam x = T; x; x &= x - 1) {
-                            const int t = lam_bits_ctz(x);
-                            if (slack[t] < cu) T &= ~((Lam)1 << t);
-                        }
-                    } else {
-                        T &= feas1;
-                    }
+                if (i2 < total) {
+                    v2 = slot_of(g.off, i2);
+                    e2 = __ldg(&d.inc[g.jb[v2] + (i2 - g.off[v2])]);
                 }
-                if (elig && T) {
-                    // pass B: conn_t = omega({e in I(u) : t in Lambda(e)}) for t in T; a net
-                    // covering more than half of T is counted as base minus its complement
-                    const int nT = lam_popc(T);
-                    for (Lam x = T; x; x &= x - 1) acc[lam_bits_ctz(x) * kThreads + tid] = 0;
-                    int32_t cbase = 0;
-                    for (int32_t j = jb; j < je; ++j) {
-                        const int32_t e = __ldg(&d.inc[j]);
-                        Lam lam;
-                        int32_t w;
-                        RecIO<Rec>::load_b(recs + e, lam, w);
+                Lam s11 = 0, lam1 = 0, s12 = 0, lam2 = 0;
+                int32_t w1 = 0, mv1 = 0, w2 = 0, mv2 = 0;
+                if (i1 < total) RecIO<Rec>::load_full(recs + e1, s11, w1, mv1, lam1);
+                if (i2 < total) RecIO<Rec>::load_full(recs + e2, s12, w2, mv2, lam2);
+                if (i1 < total) {
+                    w1 &= 0x7fffffff;
+                    if (i1 < kCache) { g.lamc[i1] = lam1; g.wc[i1] = w1; }
+                    atomicAdd(&g.W[v1], w1);
+                    if ((s11 >> g.a[v1]) & 1) {
+                        atomicAdd(&g.b[v1], w1);
+                        atomicOr(&g.T[v1], (unsigned long long)lam1);
+                    }
+                    if (moved_in_prev_round(mv1, r)) g.elig[v1] = 1;
+                }
+                if (i2 < total) {
+                    w2 &= 0x7fffffff;
+                    if (i2 < kCache) { g.lamc[i2] = lam2; g.wc[i2] = w2; }
+                    atomicAdd(&g.W[v2], w2);
+                    if ((s12 >> g.a[v2]) & 1) {
+                        atomicAdd(&g.b[v2], w2);
+                        atomicOr(&g.T[v2], (unsigned long long)lam2);
+                    }
+                    if (moved_in_prev_round(mv2, r)) g.elig[v2] = 1;
+                }
+            }
+            __syncwarp();
+            // ---- per vertex: eligibility, candidate blocks, best block
+            const int32_t W = g.W[lane], b = g.b[lane];
+            const bool elig = valid && g.elig[lane] != 0;
+            Lam T = elig ? (Lam)g.T[lane] : (Lam)0;
+            T &= ~((Lam)1 << a);
+            if (d.vw) {
+                for (Lam x = T; x; x &= x - 1) {
+                    const int t = lam_bits_ctz(x);
+                    if (slack[t] < cu) T &= ~((Lam)1 << t);
+                }
+            } else {
+                T &= feas1;
+            }
+            const bool plane_path = T != 0 && W <= kPlaneMaxW;
+            const bool coop_path = T != 0 && W > kPlaneMaxW;
+            int32_t t_best = -1, g_best = 0;
+            const int32_t bw_ = b - W;
+            const unsigned wmax = __reduce_max_sync(kFull, plane_path ? (unsigned)W : 0u);
+            if (plane_path) {
+                const int np = 32 - __clz((int)wmax);   // 2^np > wmax >= conn_t
+                int t;
+                int32_t conn;
+                if (unit) best_by_planes<Lam, Rec, true>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn);
+                else best_by_planes<Lam, Rec, false>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn);
+                const int32_t gg = bw_ + conn;
+                if (gg > 0) {
+                    t_best = t;
+                    g_best = gg;
+                }
+            }
+            // ---- warp-cooperative pass for vertices with large incident net weight
+            unsigned hm = __ballot_sync(kFull, coop_path);
+            while (hm) {
+                const int src = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const int32_t hjb = __shfl_sync(kFull, jb, src), hje = hjb + __shfl_sync(kFull, deg, src);
+                const int32_t hbw = __shfl_sync(kFull, bw_, src);
+                const uint32_t Tlo = __shfl_sync(kFull, lo32(T), src);
+                const uint32_t Thi = kWide ? __shfl_sync(kFull, hi32(T), src) : 0u;
+                int32_t acc0 = 0, acc1 = 0;
+                for (int32_t j0 = hjb; j0 < hje; j0 += 32) {
+                    const int32_t j = j0 + lane;
+                    Lam lam = 0;
+                    int32_t w = 0;
+                    if (j < hje) {
+                        RecIO<Rec>::load_b(recs + __ldg(&d.inc[j]), lam, w);
                         w &= 0x7fffffff;
-                        const Lam in = lam & T;
-                        if (2 * lam_popc(in) <= nT) {
-                            for (Lam x = in; x; x &= x - 1) acc[lam_bits_ctz(x) * kThreads + tid] += w;
-                        } else {
-                            cbase += w;
-                            for (Lam x = T & ~lam; x; x &= x - 1) acc[lam_bits_ctz(x) * kThreads + tid] -= w;
+                    }
+                    const int nn = min(32, hje - j0);
+                    const uint32_t llo = lo32(lam), lhi = hi32(lam);
+                    for (int q = 0; q < nn; ++q) {
+                        const uint32_t bl = __shfl_sync(kFull, llo, q);
+                        const int32_t wi = __shfl_sync(kFull, w, q);
+                        acc0 += ((bl >> lane) & 1) ? wi : 0;
+                        if (kWide) {
+                            const uint32_t bh = __shfl_sync(kFull, lhi, q);
+                            acc1 += ((bh >> lane) & 1) ? wi : 0;
                         }
                     }
-                    const int32_t bw_ = b - W;
-                    for (Lam x = T; x; x &= x - 1) {
-                        const int t = lam_bits_ctz(x);
-                        const int32_t g = bw_ + (cbase + acc[t * kThreads + tid]);
-                        if (g > g_best) {
-                            g_best = g;
-                            t_best = t;
-                        }
+                }
+                // key = gain << 8 | (255 - block): the larger key is the higher gain, then the
+                // smaller block
+                unsigned long long key = 0;
+                if ((Tlo >> lane) & 1) {
+                    const int32_t gg = hbw + acc0;
+                    if (gg > 0) key = ((unsigned long long)(uint32_t)gg << 8) | (unsigned long long)(255 - lane);
+                }
+                if (kWide && ((Thi >> lane) & 1)) {
+                    const int32_t gg = hbw + acc1;
+                    if (gg > 0) {
+                        const unsigned long long k2 = ((unsigned long long)(uint32_t)gg << 8) | (unsigned long long)(255 - (lane + 32));
+                        key = k2 > key ? k2 : key;
                     }
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(kFull, key, o);
+                    key = y > key ? y : key;
+                }
+                if (lane == src && key) {
+                    t_best = 255 - (int)(key & 0xFF);
+                    g_best = (int32_t)(key >> 8);
                 }
             }
             nelig += __popc(__ballot_sync(kFull, elig));
@@ -246,12 +453,14 @@ __global__ void __launch_bounds__(kThreads) k_gain(Dev d, int32_t r, int32_t s, 
                 atomicAdd(&tot_s[t_best], (unsigned long long)cu);
             }
             nout += __popc(cm);
+            __syncwarp();
         }
-        if (lane == 0) {
-            d.cand_cnt[range] = nout;
-            atomicAdd(&cnt_s[0], (unsigned long long)nelig);
-            atomicAdd(&cnt_s[1], (unsigned long long)nout);
-        }
+        if (lane == 0) d.cand_cnt[range] = nout;
+        ncand += nout;
+    }
+    if (lane == 0) {
+        if (nelig) atomicAdd(&cnt_s[0], (unsigned long long)nelig);
+        if (ncand) atomicAdd(&cnt_s[1], (unsigned long long)ncand);
     }
     __syncthreads();
     if (tid < d.k && tot_s[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&d.tot[tid]), tot_s[tid]);
@@ -504,18 +713,46 @@ __global__ void __launch_bounds__(1024) k_tie_scan(Dev d)
 
 // ------------------------------------------------------------------ apply
 template <typename Rec>
-__global__ void __launch_bounds__(kThreads) k_apply(Dev d, int32_t r, unsigned long long *st_row)
+__device__ __forceinline__ void apply_pin(const Dev &d, Rec *rc, int32_t w, bool wide, int32_t oa,
+                                          int32_t ot, typename RecIO<Rec>::Lam ba,
+                                          typename RecIO<Rec>::Lam bt, int32_t r, long long &dobj)
+{
+    typedef typename RecIO<Rec>::Lam Lam;
+    (void)d;
+    (void)wide;
+    // a step of a pin count 1->0 or 0->1 flips its Lambda bit and changes the objective by
+    // omega(e); a step into or out of the value 1 flips its S1 bit
+    const Lam lx = (oa == 1 ? ba : (Lam)0) | (ot == 0 ? bt : (Lam)0);
+    const Lam sx = ((oa == 1 || oa == 2) ? ba : (Lam)0) | ((ot == 0 || ot == 1) ? bt : (Lam)0);
+    if (sizeof(Lam) == 8) {
+        if (lx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->lam), (unsigned long long)lx);
+        if (sx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->s1), (unsigned long long)sx);
+    } else {
+        if (lx) atomicXor(reinterpret_cast<unsigned int *>(&rc->lam), (unsigned int)lx);
+        if (sx) atomicXor(reinterpret_cast<unsigned int *>(&rc->s1), (unsigned int)sx);
+    }
+    dobj += (ot == 0 ? w : 0) - (oa == 1 ? w : 0);
+    stamp_moved(&rc->mv, r);
+}
+
+// Persistent: each warp walks warp ranges with a grid stride and applies the approved moves
+// of its range.  Ties at a block's threshold gain are approved in vertex-id order: the warp
+// starts from the tile's exclusive tie prefix and adds the ties of the earlier ranges of the
+// same tile itself, so warps never wait for each other.
+template <typename Rec>
+__global__ void __launch_bounds__(kThreads, 5) k_apply(Dev d, int32_t r, unsigned long long *st_row)
 {
     typedef typename RecIO<Rec>::Lam Lam;
     __shared__ int mode[64];
     __shared__ int32_t gthr[64];
     __shared__ long long rem[64];
-    __shared__ unsigned long long wtie[kWarps][64];
     __shared__ unsigned long long run[kWarps][64];
     __shared__ unsigned long long bwd[64];
-    __shared__ unsigned long long objd, napp;
+    __shared__ unsigned long long objd, napp, mpins;
+    __shared__ int any_thr;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int tile = blockIdx.x;
+    if (tid == 0) { objd = 0; napp = 0; mpins = 0; any_thr = 0; }
+    __syncthreads();
     if (tid < 64) {
         int md = SEL_ALL;
         if (tid < d.k) {
@@ -526,103 +763,112 @@ __global__ void __launch_bounds__(kThreads) k_apply(Dev d, int32_t r, unsigned l
         }
         mode[tid] = md;
         bwd[tid] = 0;
-    }
-    for (int i = tid; i < kWarps * 64; i += kThreads) (&wtie[0][0])[i] = 0;
-    if (tid == 0) { objd = 0; napp = 0; }
-    __syncthreads();
-    const int32_t range = tile * kWarps + wid;
-    const int32_t ncand = range < d.n_ranges ? d.cand_cnt[range] : 0;
-    const uint64_t *cand = d.cand + (int64_t)range * kRange;
-    // pass 1: tie weight per block in this warp's range
-    for (int i = lane; i < ncand; i += 32) {
-        int t, ul;
-        int32_t g;
-        decode(cand[i], t, g, ul);
-        if (mode[t] == SEL_THRESH && g == gthr[t])
-            atomicAdd(&wtie[wid][t], d.vw ? (unsigned long long)d.vw[range * kRange + ul] : 1ull);
+        if (md == SEL_THRESH) any_thr = 1;
     }
     __syncthreads();
-    for (int t = lane; t < d.k; t += 32) {
-        unsigned long long s = 0;
-        if (mode[t] == SEL_THRESH) {
-            s = (unsigned long long)d.tie[(int64_t)t * d.n_tiles + tile];
-            for (int w = 0; w < wid; ++w) s += wtie[w][t];
-        }
-        run[wid][t] = s;
-    }
-    __syncwarp();
     Rec *recs = reinterpret_cast<Rec *>(d.rec);
     long long dobj = 0;
-    int32_t nappr = 0;
-    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
-        const int idx = c0 + lane;
-        int t = 0, ul = 0;
-        int32_t g = 0;
-        unsigned long long cw = 1;
-        bool appr = false, tie = false;
-        if (idx < ncand) {
-            decode(cand[idx], t, g, ul);
-            if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
-            const int md = mode[t];
-            if (md == SEL_ALL || g > gthr[t]) appr = true;
-            else if (g == gthr[t]) tie = true;
-        }
-        // ties in id order: exclusive prefix so far + own weight must fit the budget
-        unsigned tm = __ballot_sync(kFull, tie);
-        while (tm) {
-            const int l = __ffs(tm) - 1;
-            tm &= tm - 1;
-            if (lane == l) {
-                appr = (long long)(run[wid][t] + cw) <= rem[t];
-                run[wid][t] += cw;
+    int32_t nappr = 0, npins = 0;
+    for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
+        const int32_t ncand = d.cand_cnt[range];
+        if (ncand == 0) continue;
+        const uint64_t *cand = d.cand + (int64_t)range * kRange;
+        if (any_thr) {
+            const int32_t tile = range / kWarps;
+            for (int t = lane; t < 64; t += 32)
+                run[wid][t] = (t < d.k && mode[t] == SEL_THRESH)
+                                  ? (unsigned long long)d.tie[(int64_t)t * d.n_tiles + tile] : 0ull;
+            __syncwarp();
+            for (int32_t pr = tile * kWarps; pr < range; ++pr) {
+                const int32_t n2 = d.cand_cnt[pr];
+                const uint64_t *c2 = d.cand + (int64_t)pr * kRange;
+                for (int i = lane; i < n2; i += 32) {
+                    int t, ul;
+                    int32_t g;
+                    decode(c2[i], t, g, ul);
+                    if (mode[t] == SEL_THRESH && g == gthr[t])
+                        atomicAdd(&run[wid][t], d.vw ? (unsigned long long)d.vw[pr * kRange + ul] : 1ull);
+                }
             }
             __syncwarp();
         }
-        if (appr) {
-            const int32_t u = range * kRange + ul;
-            const int a = d.part[u];
-            d.part[u] = (uint8_t)t;
-            atomicAdd(&bwd[a], (unsigned long long)(-(long long)cw));
-            atomicAdd(&bwd[t], cw);
-            const Lam ba = (Lam)1 << a, bt = (Lam)1 << t;
-            const int32_t jb = d.vtx_off[u], je = d.vtx_off[u + 1];
-            for (int32_t j = jb; j < je; ++j) {
-                const int32_t e = d.inc[j];
-                Rec *rc = recs + e;
-                const int32_t wf = rc->w;
-                const int32_t w = wf & 0x7fffffff;
-                const bool wide = wf < 0;
-                const int32_t wrow = wide ? d.widx[e] : 0;
-                const int32_t oa = phi_add(d, e, a, -1, wide, wrow);
-                const int32_t ot = phi_add(d, e, t, +1, wide, wrow);
-                const Lam lx = (oa == 1 ? ba : (Lam)0) | (ot == 0 ? bt : (Lam)0);
-                const Lam sx = ((oa == 1 || oa == 2) ? ba : (Lam)0) | ((ot == 0 || ot == 1) ? bt : (Lam)0);
-                if (sizeof(Lam) == 8) {
-                    if (lx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->lam), (unsigned long long)lx);
-                    if (sx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->s1), (unsigned long long)sx);
-                } else {
-                    if (lx) atomicXor(reinterpret_cast<unsigned int *>(&rc->lam), (unsigned int)lx);
-                    if (sx) atomicXor(reinterpret_cast<unsigned int *>(&rc->s1), (unsigned int)sx);
-                }
-                dobj += (ot == 0 ? w : 0) - (oa == 1 ? w : 0);
-                stamp_moved(&rc->mv, r);
+        for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+            const int idx = c0 + lane;
+            int t = 0, ul = 0;
+            int32_t g = 0;
+            unsigned long long cw = 1;
+            bool appr = false, tie = false;
+            if (idx < ncand) {
+                decode(cand[idx], t, g, ul);
+                if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
+                const int md = mode[t];
+                if (md == SEL_ALL || g > gthr[t]) appr = true;
+                else if (g == gthr[t]) tie = true;
             }
-            ++nappr;
+            // ties in id order: exclusive prefix so far + own weight must fit the budget
+            unsigned tm = __ballot_sync(kFull, tie);
+            while (tm) {
+                const int l = __ffs(tm) - 1;
+                tm &= tm - 1;
+                if (lane == l) {
+                    appr = (long long)(run[wid][t] + cw) <= rem[t];
+                    run[wid][t] += cw;
+                }
+                __syncwarp();
+            }
+            if (appr) {
+                const int32_t u = range * kRange + ul;
+                const int a = d.part[u];
+                d.part[u] = (uint8_t)t;
+                atomicAdd(&bwd[a], (unsigned long long)(-(long long)cw));
+                atomicAdd(&bwd[t], cw);
+                const Lam ba = (Lam)1 << a, bt = (Lam)1 << t;
+                const int32_t jb = d.vtx_off[u], je = d.vtx_off[u + 1];
+                int32_t j = jb;
+                for (; j + 1 < je; j += 2) {
+                    const int32_t e0 = d.inc[j], e1 = d.inc[j + 1];
+                    Rec *r0 = recs + e0, *r1 = recs + e1;
+                    const int32_t wf0 = r0->w, wf1 = r1->w;
+                    const bool wd0 = wf0 < 0, wd1 = wf1 < 0;
+                    const int32_t wr0 = wd0 ? d.widx[e0] : 0, wr1 = wd1 ? d.widx[e1] : 0;
+                    const int32_t oa0 = phi_add(d, e0, a, -1, wd0, wr0);
+                    const int32_t ot0 = phi_add(d, e0, t, +1, wd0, wr0);
+                    const int32_t oa1 = phi_add(d, e1, a, -1, wd1, wr1);
+                    const int32_t ot1 = phi_add(d, e1, t, +1, wd1, wr1);
+                    apply_pin<Rec>(d, r0, wf0 & 0x7fffffff, wd0, oa0, ot0, ba, bt, r, dobj);
+                    apply_pin<Rec>(d, r1, wf1 & 0x7fffffff, wd1, oa1, ot1, ba, bt, r, dobj);
+                }
+                if (j < je) {
+                    const int32_t e0 = d.inc[j];
+                    Rec *r0 = recs + e0;
+                    const int32_t wf0 = r0->w;
+                    const bool wd0 = wf0 < 0;
+                    const int32_t wr0 = wd0 ? d.widx[e0] : 0;
+                    const int32_t oa0 = phi_add(d, e0, a, -1, wd0, wr0);
+                    const int32_t ot0 = phi_add(d, e0, t, +1, wd0, wr0);
+                    apply_pin<Rec>(d, r0, wf0 & 0x7fffffff, wd0, oa0, ot0, ba, bt, r, dobj);
+                }
+                ++nappr;
+                npins += je - jb;
+            }
         }
     }
     for (int o = 16; o; o >>= 1) {
         dobj += __shfl_xor_sync(kFull, dobj, o);
         nappr += __shfl_xor_sync(kFull, nappr, o);
+        npins += __shfl_xor_sync(kFull, npins, o);
     }
     if (lane == 0) {
         if (dobj) atomicAdd(&objd, (unsigned long long)dobj);
         if (nappr) atomicAdd(&napp, (unsigned long long)nappr);
+        if (npins) atomicAdd(&mpins, (unsigned long long)npins);
     }
     __syncthreads();
     if (tid < d.k && bwd[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[tid]), bwd[tid]);
     if (tid == 0) {
         if (objd) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), objd);
         if (napp) atomicAdd(st_row + ST_APPR, napp);
+        if (mpins) atomicAdd(st_row + ST_MOVED, mpins);
     }
 }
 
@@ -652,49 +898,128 @@ __global__ void k_expand_candidates(Dev d, int32_t *target, int64_t *gain)
 }
 
 // ------------------------------------------------------------------ host side
-template <typename Rec>
-cudaError_t set_gain_smem(int k)
+// Persistent grid: as many CTAs as fit on the device at once, never more than the work.
+template <typename K>
+int persistent_grid(hgp_handle *h, K kernel)
 {
-    static int done[2] = {0, 0};
-    const int slot = sizeof(Rec) == 16 ? 0 : 1;
-    (void)k;
-    if (done[slot]) return cudaSuccess;
-    const int bytes = (sizeof(Rec) == 16 ? 32 : 64) * kThreads * (int)sizeof(int32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_gain<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done[slot] = 1;
-    return e;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+    (void)cudaGetLastError();
+    int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (h->d.n_ranges + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    return (int)(g < 1 ? 1 : g);
 }
 
 template <typename Rec>
 cudaError_t launch_gain(hgp_handle *h, int32_t r, int32_t s, bool all_elig, unsigned long long *st_row)
 {
-    cudaError_t e = set_gain_smem<Rec>(h->d.k);
-    if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)h->d.k * kThreads * sizeof(int32_t);
-    k_gain<Rec><<<h->d.n_tiles, kThreads, smem, h->stream>>>(h->d, r, s, all_elig ? 1 : 0, st_row);
+    if (!h->grid_gain) h->grid_gain = persistent_grid(h, k_gain<Rec>);
+    k_gain<Rec><<<h->grid_gain, kThreads, 0, h->stream>>>(h->d, r, s, all_elig ? 1 : 0, st_row);
+    h->launches++;
     return cudaGetLastError();
+}
+
+template <typename Rec>
+cudaError_t launch_apply(hgp_handle *h, int32_t r, unsigned long long *st_row)
+{
+    if (!h->grid_apply) h->grid_apply = persistent_grid(h, k_apply<Rec>);
+    k_apply<Rec><<<h->grid_apply, kThreads, 0, h->stream>>>(h->d, r, st_row);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+// Per-phase event timing (profiling mode): a pair of events around each phase instance.
+enum { PH_PREP = 0, PH_GAIN = 1, PH_APPROVE = 2, PH_APPLY = 3, PH_END = 4 };
+
+cudaError_t phase_begin(hgp_handle *h)
+{
+    if (!h->profiling) return cudaSuccess;
+    if (h->events_used + 2 > h->n_events) {
+        // grow the pool (existing events stay valid; pending pairs are kept)
+        const int32_t cap = h->n_events ? h->n_events * 2 : 256;
+        cudaEvent_t *ev = new (std::nothrow) cudaEvent_t[cap];
+        int32_t *ph = new (std::nothrow) int32_t[cap / 2];
+        int32_t *ct = new (std::nothrow) int32_t[cap / 2];
+        if (!ev || !ph || !ct) {
+            delete[] ev; delete[] ph; delete[] ct;
+            return cudaErrorMemoryAllocation;
+        }
+        for (int32_t i = 0; i < h->n_events; ++i) ev[i] = h->events[i];
+        for (int32_t i = 0; i < h->n_events / 2; ++i) { ph[i] = h->event_phase[i]; ct[i] = h->event_count[i]; }
+        for (int32_t i = h->n_events; i < cap; ++i) {
+            cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) {
+                for (int32_t j = h->n_events; j < i; ++j) cudaEventDestroy(ev[j]);
+                delete[] ev; delete[] ph; delete[] ct;
+                return e;
+            }
+        }
+        delete[] h->events; delete[] h->event_phase; delete[] h->event_count;
+        h->events = ev; h->event_phase = ph; h->event_count = ct;
+        h->n_events = cap;
+    }
+    return cudaEventRecord(h->events[h->events_used], h->stream);
+}
+
+cudaError_t phase_end(hgp_handle *h, int phase, int32_t launches)
+{
+    if (!h->profiling) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(h->events[h->events_used + 1], h->stream);
+    h->event_phase[h->events_used / 2] = phase;
+    h->event_count[h->events_used / 2] = launches;
+    h->events_used += 2;
+    return e;
+}
+
+cudaError_t collect_profile(hgp_handle *h)
+{
+    if (!h->profiling || h->events_used == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (int32_t i = 0; i + 1 < h->events_used && e == cudaSuccess; i += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]);
+        h->prof_ms[h->event_phase[i / 2]] += ms;
+        h->prof_launches[h->event_phase[i / 2]] += h->event_count[i / 2];
+    }
+    h->events_used = 0;
+    return e;
 }
 
 cudaError_t launch_subround(hgp_handle *h, int32_t r, int32_t s, bool all_elig, unsigned long long *st_row)
 {
     Dev &d = h->d;
     cudaStream_t st = h->stream;
-    cudaError_t e = d.k <= 32 ? launch_gain<Rec16>(h, r, s, all_elig, st_row)
-                              : launch_gain<Rec32>(h, r, s, all_elig, st_row);
+    cudaError_t e = phase_begin(h);
+    if (e == cudaSuccess)
+        e = d.k <= 32 ? launch_gain<Rec16>(h, r, s, all_elig, st_row) : launch_gain<Rec32>(h, r, s, all_elig, st_row);
+    if (e == cudaSuccess) e = phase_end(h, PH_GAIN, 1);
     if (e != cudaSuccess) return e;
+    e = phase_begin(h);
+    if (e != cudaSuccess) return e;
+    int32_t n = 0;
     k_hist<<<d.n_tiles, kThreads, 0, st>>>(d, 0);
     k_select<<<d.k, kThreads, 0, st>>>(d, 0);
+    n += 2;
     if (h->max_vertex_netweight >= kBins - 1) {
         for (int level = 1; level <= 3; ++level) {
             k_hist<<<d.n_tiles, kThreads, 0, st>>>(d, level);
             k_select<<<d.k, kThreads, 0, st>>>(d, level);
+            n += 2;
         }
     }
     k_tie_sum<<<d.n_tiles, kThreads, 0, st>>>(d);
     k_tie_scan<<<d.k, 1024, 0, st>>>(d);
-    if (d.k <= 32) k_apply<Rec16><<<d.n_tiles, kThreads, 0, st>>>(d, r, st_row);
-    else k_apply<Rec32><<<d.n_tiles, kThreads, 0, st>>>(d, r, st_row);
-    return cudaGetLastError();
+    n += 2;
+    h->launches += n;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = phase_end(h, PH_APPROVE, n);
+    if (e == cudaSuccess) e = phase_begin(h);
+    if (e != cudaSuccess) return e;
+    e = d.k <= 32 ? launch_apply<Rec16>(h, r, st_row) : launch_apply<Rec32>(h, r, st_row);
+    if (e == cudaSuccess) e = phase_end(h, PH_APPLY, 1);
+    return e;
 }
 
 }  // namespace
@@ -735,15 +1060,23 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
     for (int32_t rr = 0; rr < rounds && e == cudaSuccess; ++rr) {
         const int32_t r = (int32_t)(h->next_round + rr);
         unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
+        e = phase_begin(h);
+        if (e != cudaSuccess) break;
         k_round_prep<<<d.n_tiles, kThreads, 0, st>>>(d, r, h->seed);
+        h->launches++;
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = phase_end(h, PH_PREP, 1);
         for (int32_t s = 0; s < d.S && e == cudaSuccess; ++s)
             e = launch_subround(h, r, s, h->all_eligible && rr == 0, row);
+        if (e == cudaSuccess) e = phase_begin(h);
         if (e == cudaSuccess) {
             k_round_end<<<1, 32, 0, st>>>(d, row);
+            h->launches++;
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = phase_end(h, PH_END, 1);
     }
+    if (e == cudaSuccess) e = collect_profile(h);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -765,6 +1098,7 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
                 stats[rr].approved = row[ST_APPR];
                 stats[rr].eligible = row[ST_ELIG];
                 stats[rr].max_block_weight = row[ST_MAXW];
+                stats[rr].moved_pins = row[ST_MOVED];
             }
         }
     }
@@ -799,6 +1133,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     if (e == cudaSuccess) e = cudaMemsetAsync(g_d, 0, sizeof(int64_t) * (size_t)d.n, st);
     if (e == cudaSuccess) {
         k_round_prep<<<d.n_tiles, kThreads, 0, st>>>(d, r, h->seed);
+        h->launches++;
         e = cudaGetLastError();
     }
     // the stats row written here is scratch: refine() clears the stats before use
@@ -808,6 +1143,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tot, 0, sizeof(int64_t) * 64, st);
     if (e == cudaSuccess) {
         k_expand_candidates<<<(d.n_ranges * 32 + 255) / 256, 256, 0, st>>>(d, t_d, g_d);
+        h->launches++;
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(target, t_d, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
@@ -823,3 +1159,36 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 }
 
 }  // namespace hgp
+
+extern "C" {
+
+int hgp_set_profiling(hgp_handle *h, int32_t enable)
+{
+    if (!h) return HGP_ERR_INVALID;
+    h->profiling = enable != 0;
+    h->events_used = 0;
+    for (int i = 0; i < HGP_PHASES; ++i) {
+        h->prof_ms[i] = 0.0;
+        h->prof_launches[i] = 0;
+    }
+    return HGP_OK;
+}
+
+int hgp_get_profile(hgp_handle *h, hgp_profile *out)
+{
+    if (!h || !out) return HGP_ERR_INVALID;
+    for (int i = 0; i < HGP_PHASES; ++i) {
+        out->ms[i] = h->prof_ms[i];
+        out->launches[i] = h->prof_launches[i];
+    }
+    return HGP_OK;
+}
+
+int hgp_get_launch_count(hgp_handle *h, int64_t *out)
+{
+    if (!h || !out) return HGP_ERR_INVALID;
+    *out = h->launches;
+    return HGP_OK;
+}
+
+}  // extern "C"

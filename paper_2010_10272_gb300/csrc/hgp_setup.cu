@@ -378,11 +378,11 @@ int init_state(hgp_handle *h)
     cudaStream_t st = h->stream;
     CK(cudaMemsetAsync(d.bw, 0, sizeof(int64_t) * d.k, st));
     CK(cudaMemsetAsync(d.obj, 0, sizeof(int64_t), st));
-    k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d);
+    k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
     CK(cudaGetLastError());
     const int g = grid_for((int64_t)d.m * 32, kThreads, 152 * 16);
-    if (d.k <= 32) k_init_nets<Rec16><<<g, kThreads, 0, st>>>(d);
-    else k_init_nets<Rec32><<<g, kThreads, 0, st>>>(d);
+    if (d.k <= 32) { k_init_nets<Rec16><<<g, kThreads, 0, st>>>(d); h->launches++; }
+    else { k_init_nets<Rec32><<<g, kThreads, 0, st>>>(d); h->launches++; }
     CK(cudaGetLastError());
     h->next_round = 0;
     h->all_eligible = true;
@@ -487,16 +487,16 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.nw = nw_d;
 
     // ---- validation
-    k_check_offsets<<<grid_for((int64_t)m + 1, 256), 256, 0, st>>>(off64, net_off, m, P, d.err);
-    k_check_vertices<<<grid_for(n, 256), 256, 0, st>>>(vw_d, part_in, n, k, d.err);
-    if (nw_d) k_check_nets<<<grid_for(m, 256), 256, 0, st>>>(nw_d, m, d.err);
+    k_check_offsets<<<grid_for((int64_t)m + 1, 256), 256, 0, st>>>(off64, net_off, m, P, d.err); h->launches++;
+    k_check_vertices<<<grid_for(n, 256), 256, 0, st>>>(vw_d, part_in, n, k, d.err); h->launches++;
+    if (nw_d) { k_check_nets<<<grid_for(m, 256), 256, 0, st>>>(nw_d, m, d.err); h->launches++; }
     CKF(cudaGetLastError());
     int32_t host_err[2] = {0, 0};
     CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CKF(cudaStreamSynchronize(st));
     if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     if (m > 0) {
-        k_check_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d);
+        k_check_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
         CKF(cudaGetLastError());
     }
     CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -518,9 +518,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     auto scan = [&](const int32_t *in, int32_t *outp, int64_t count) -> cudaError_t {
         const int64_t blocks = (count + kScanChunk - 1) / kScanChunk;
         const int64_t bl = blocks < 1 ? 1 : blocks;
-        k_scan_reduce<<<(unsigned)bl, kScanThreads, 0, st>>>(in, count, block_sums);
-        k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, bl);
-        k_scan_final<<<(unsigned)bl, kScanThreads, 0, st>>>(in, outp, count, block_sums);
+        k_scan_reduce<<<(unsigned)bl, kScanThreads, 0, st>>>(in, count, block_sums); h->launches++;
+        k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, bl); h->launches++;
+        k_scan_final<<<(unsigned)bl, kScanThreads, 0, st>>>(in, outp, count, block_sums); h->launches++;
         return cudaGetLastError();
     };
 
@@ -529,7 +529,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     if (max_size > narrow_max) {
         int32_t *widx = nullptr;
         CKF(dalloc(h, &widx, (int64_t)m + 1));
-        k_wide_flags<<<grid_for(m, 256), 256, 0, st>>>(net_off, m, narrow_max, tmp);
+        k_wide_flags<<<grid_for(m, 256), 256, 0, st>>>(net_off, m, narrow_max, tmp); h->launches++;
         CKF(scan(tmp, widx, m));
         int32_t nwide = 0;
         CKF(cudaMemcpyAsync(&nwide, widx + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -547,17 +547,17 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(dalloc(h, &vtx_off, (int64_t)n + 1));
     CKF(dalloc(h, &inc, P));
     CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
-    if (P) k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp);
+    if (P) { k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp); h->launches++; }
     CKF(scan(tmp, vtx_off, n));
     CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (m > 0) k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, tmp, inc);
+    if (m > 0) { k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, tmp, inc); h->launches++; }
     CKF(cudaGetLastError());
     d.vtx_off = vtx_off;
     d.inc = inc;
 
     unsigned long long *maxw_d = reinterpret_cast<unsigned long long *>(misc32 + 2);
     CKF(cudaMemsetAsync(maxw_d, 0, sizeof(unsigned long long), st));
-    k_vertex_netweight<<<grid_for(n, 256), 256, 0, st>>>(vtx_off, inc, nw_d, n, d.err, maxw_d);
+    k_vertex_netweight<<<grid_for(n, 256), 256, 0, st>>>(vtx_off, inc, nw_d, n, d.err, maxw_d); h->launches++;
     CKF(cudaGetLastError());
     unsigned long long maxw = 0;
     CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -569,7 +569,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     // ---- state
     uint8_t *part = nullptr;
     CKF(dalloc(h, &part, n));
-    k_copy_part<<<grid_for(n, 256), 256, 0, st>>>(part_in, part, n);
+    k_copy_part<<<grid_for(n, 256), 256, 0, st>>>(part_in, part, n); h->launches++;
     d.part = part;
     const int64_t entries = (int64_t)m * k;
     const int64_t words = (entries * w + 3) / 4;
@@ -689,6 +689,10 @@ void hgp_destroy(hgp_handle *h)
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (int i = 0; i < h->n_allocs; ++i)
         if (h->allocs[i]) cudaFree(h->allocs[i]);
+    for (int32_t i = 0; i < h->n_events; ++i) cudaEventDestroy(h->events[i]);
+    delete[] h->events;
+    delete[] h->event_phase;
+    delete[] h->event_count;
     if (h->d.stats) cudaFree(h->d.stats);
     if (h->h_stats) cudaFreeHost(h->h_stats);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -709,13 +713,13 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) {
-        k_check_vertices<<<grid_for(d.n, 256), 256, 0, st>>>(nullptr, tmp, d.n, d.k, d.err);
+        k_check_vertices<<<grid_for(d.n, 256), 256, 0, st>>>(nullptr, tmp, d.n, d.k, d.err); h->launches++;
         e = cudaMemcpyAsync(&err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && (err & ERR_INVALID)) rc = HGP_ERR_INVALID;
     if (e == cudaSuccess && rc == HGP_OK) {
-        k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n);
+        k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n); h->launches++;
         e = cudaGetLastError();
     }
     cudaFreeAsync(tmp, st);
@@ -754,14 +758,14 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     if (on_device) {
-        k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, part, d.n);
+        k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, part, d.n); h->launches++;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
         return HGP_OK;
     }
     int32_t *tmp = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
-    k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, tmp, d.n);
+    k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, tmp, d.n); h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(part, tmp, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(tmp, st);
@@ -786,7 +790,7 @@ int hgp_get_phi(hgp_handle *h, int32_t *phi)
     if (total == 0) return HGP_OK;
     int32_t *tmp = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)total, h->stream));
-    k_widen_phi<<<grid_for(total, 256), 256, 0, h->stream>>>(d, tmp);
+    k_widen_phi<<<grid_for(total, 256), 256, 0, h->stream>>>(d, tmp); h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(phi, tmp, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
@@ -802,8 +806,8 @@ int hgp_get_lambda(hgp_handle *h, uint64_t *lam)
     if (d.m == 0) return HGP_OK;
     uint64_t *tmp = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint64_t) * (size_t)d.m, h->stream));
-    if (d.k <= 32) k_get_lambda<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp);
-    else k_get_lambda<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp);
+    if (d.k <= 32) { k_get_lambda<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp); h->launches++; }
+    else { k_get_lambda<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp); h->launches++; }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, tmp, sizeof(uint64_t) * (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
@@ -847,7 +851,7 @@ cudaError_t objective_from_phi(hgp_handle *h, int64_t *d_out)
 {
     cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(int64_t), h->stream);
     if (e != cudaSuccess) return e;
-    k_obj_from_phi<<<grid_for(h->d.m, 256), 256, 0, h->stream>>>(h->d, reinterpret_cast<unsigned long long *>(d_out));
+    k_obj_from_phi<<<grid_for(h->d.m, 256), 256, 0, h->stream>>>(h->d, reinterpret_cast<unsigned long long *>(d_out)); h->launches++;
     return cudaGetLastError();
 }
 

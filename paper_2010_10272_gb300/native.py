@@ -17,7 +17,8 @@ _LIB_PATH = os.path.join(_HERE, "libhgp.so")
 _lock = threading.Lock()
 _lib = None
 
-STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight")
+STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight", "moved_pins")
+PHASES = ("sublists", "gain", "approval", "apply", "round_end")
 
 HGP_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "CUDA", 5: "TIMEOUT",
@@ -38,6 +39,10 @@ class Options(ctypes.Structure):
 
 class RoundStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in STAT_FIELDS]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("launches", ctypes.c_int64 * len(PHASES))]
 
 
 def library_path() -> str:
@@ -73,9 +78,13 @@ def load_library():
         lib.hgp_get_lambda.argtypes = [P, P]
         lib.hgp_get_info.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
+        lib.hgp_set_profiling.argtypes = [P, i32]
+        lib.hgp_get_profile.argtypes = [P, P]
+        lib.hgp_get_launch_count.argtypes = [P, P]
         for name in ("hgp_refine", "hgp_set_partition", "hgp_objective", "hgp_objective_from_phi",
                      "hgp_get_partition", "hgp_get_block_weights", "hgp_get_phi", "hgp_get_lambda",
-                     "hgp_get_info", "hgp_debug_candidates"):
+                     "hgp_get_info", "hgp_debug_candidates", "hgp_set_profiling",
+                     "hgp_get_profile", "hgp_get_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
         lib.hgp_destroy.argtypes = [P]
         lib.hgp_destroy.restype = None
@@ -178,7 +187,7 @@ class HGP:
 
     # -- refinement
     def refine(self, rounds: int, stats: bool = True):
-        """Runs `rounds` LP rounds; returns int64 [rounds x 5] statistics (or None)."""
+        """Runs `rounds` LP rounds; returns int64 [rounds x 6] statistics (STAT_FIELDS) or None."""
         if stats:
             buf = (RoundStats * max(1, rounds))()
             _check(self._lib.hgp_refine(self._h, int(rounds), buf), "hgp_refine")
@@ -241,3 +250,17 @@ class HGP:
         _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
                "hgp_debug_candidates")
         return t, g
+
+    # -- measurement
+    def set_profiling(self, enable: bool = True):
+        _check(self._lib.hgp_set_profiling(self._h, 1 if enable else 0), "hgp_set_profiling")
+
+    def profile(self) -> dict:
+        p = Profile()
+        _check(self._lib.hgp_get_profile(self._h, ctypes.byref(p)), "hgp_get_profile")
+        return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(PHASES)}
+
+    def launch_count(self) -> int:
+        out = ctypes.c_int64()
+        _check(self._lib.hgp_get_launch_count(self._h, ctypes.byref(out)), "hgp_get_launch_count")
+        return out.value

@@ -38,7 +38,7 @@ def test_golden(g):
             subrounds=g.subrounds, seed=g.seed)
     assert h.info()["lmax"] == g.lmax
     assert h.objective() == g.objective
-    stats = h.refine(len(g.rounds))
+    stats = h.refine(len(g.rounds))[:, :5]
     assert [tuple(r) for r in stats.tolist()] == list(g.rounds)
     np.testing.assert_array_equal(h.partition(), g.final)
 
@@ -198,7 +198,7 @@ def test_set_partition_equals_fresh_create():
     h.set_partition(hg.part)
     o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
     compare_state(h, o)
-    np.testing.assert_array_equal(h.refine(3), o.refine(3)[0])
+    np.testing.assert_array_equal(h.refine(3)[:, :5], o.refine(3)[0])
     compare_state(h, o)
 
 
@@ -210,7 +210,7 @@ def test_device_inputs_and_stream():
     h = HGP(hg.n, hg.m, t(hg.net_off), t(hg.pins), hg.k, hg.eps, t(hg.part), t(hg.vertex_w),
             t(hg.net_w), subrounds=4, device=True, stream=s)
     o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
-    np.testing.assert_array_equal(h.refine(3), o.refine(3)[0])
+    np.testing.assert_array_equal(h.refine(3)[:, :5], o.refine(3)[0])
     out = torch.empty(hg.n, dtype=torch.int32, device=dev)
     h.partition(out_device=out)
     np.testing.assert_array_equal(out.cpu().numpy(), o.partition())
@@ -259,3 +259,24 @@ def test_error_codes():
     assert _err(mk(net_w=np.array([1 << 30, 1 << 30], np.int32),
                    pins=np.array([0, 1, 1, 2], np.int32),
                    net_off=np.array([0, 2, 4], np.int64))) == 3
+
+
+def test_moved_pins_and_profile():
+    """moved_pins = sum of degrees of the vertices the oracle moved; profiling accounts for
+    every kernel the rounds launch."""
+    hg = synth.random_small(35, 20000, 18000, 8, max_size=9, weighted=True, rounds=3)
+    h = HGP.from_hypergraph(hg, subrounds=4)
+    h.set_profiling(True)
+    l0 = h.launch_count()
+    st = h.refine(3)
+    launched = h.launch_count() - l0
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    _, moves = o.refine(3, log_moves=True)
+    deg = np.bincount(hg.pins, minlength=hg.n)
+    for r in range(3):
+        sel = moves[(moves[:, 0] // 4) == r]
+        assert st[r, 5] == deg[sel[:, 1]].sum()
+    prof = h.profile()
+    assert sum(v[1] for v in prof.values()) == launched
+    assert prof["gain"][1] == 3 * 4 and prof["apply"][1] == 3 * 4
+    assert all(v[0] > 0 for v in prof.values())
