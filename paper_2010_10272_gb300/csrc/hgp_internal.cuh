@@ -2,7 +2,7 @@
 //
 // HBM layout of one handle (n vertices, m nets, P pins, k blocks):
 //   net_off[m+1], pins[P]        net -> pins CSR, int32 (Sec. 2 / Sec. 3.2 adjacency arrays)
-//   vtx_off[n+1], inc[P]         vertex -> incident nets CSR I(v), int32
+//   vtx_off[n+1], inc[P]         vertex -> incident nets CSR I(v), int32 (bit 31: wide net)
 //   vw[n]                        vertex weights c(v) (absent for unit weights)
 //   part[n]                      Pi as uint8 (k <= 64)
 //   phi                          Phi(e, i), row-major [m][k], entries of 1, 2 or 4 bytes packed
@@ -28,6 +28,9 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kBins = 4096;              // approval histogram bins (gains 1..4094 exact)
 constexpr int kNever = -2;               // move-stamp round meaning "never moved"
 constexpr uint32_t kWideFlag = 0x80000000u;
+// inc[] entries carry the net id in bits 0..30 and, in bit 31, whether the net's Phi row lives
+// in the wide table (so the apply step knows it without reading the net's record first)
+constexpr int32_t kNetMask = 0x7fffffff;
 
 // Per-net record for k <= 32, 16 bytes (two per 32-byte sector).
 struct __align__(16) Rec16 {

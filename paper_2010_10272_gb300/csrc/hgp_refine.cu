@@ -199,7 +199,7 @@ __device__ __forceinline__ void bitsliced_best(const GainWarp<Lam> &g, const Rec
             lam = g.lamc[i];
             w = g.wc[i];
         } else {
-            RecIO<Rec>::load_b(recs + __ldg(&inc[jb + (i - off)]), lam, w);
+            RecIO<Rec>::load_b(recs + (__ldg(&inc[jb + (i - off)]) & kNetMask), lam, w);
             w &= 0x7fffffff;
         }
         const Lam x = lam & T;
@@ -329,11 +329,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(Dev d, int32_t r, int32_t 
                 int v1 = 0, v2 = 0, e1 = 0, e2 = 0;
                 if (i1 < total) {
                     v1 = slot_of(g.off, i1);
-                    e1 = __ldg(&d.inc[g.jb[v1] + (i1 - g.off[v1])]);
+                    e1 = __ldg(&d.inc[g.jb[v1] + (i1 - g.off[v1])]) & kNetMask;
                 }
                 if (i2 < total) {
                     v2 = slot_of(g.off, i2);
-                    e2 = __ldg(&d.inc[g.jb[v2] + (i2 - g.off[v2])]);
+                    e2 = __ldg(&d.inc[g.jb[v2] + (i2 - g.off[v2])]) & kNetMask;
                 }
                 Lam s11 = 0, lam1 = 0, s12 = 0, lam2 = 0;
                 int32_t w1 = 0, mv1 = 0, w2 = 0, mv2 = 0;
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(Dev d, int32_t r, int32_t 
                     Lam lam = 0;
                     int32_t w = 0;
                     if (j < hje) {
-                        RecIO<Rec>::load_b(recs + __ldg(&d.inc[j]), lam, w);
+                        RecIO<Rec>::load_b(recs + (__ldg(&d.inc[j]) & kNetMask), lam, w);
                         w &= 0x7fffffff;
                     }
                     const int nn = min(32, hje - j0);
@@ -712,42 +712,90 @@ __global__ void __launch_bounds__(1024) k_tie_scan(Dev d)
 }
 
 // ------------------------------------------------------------------ apply
+struct alignas(16) ApplyWarp {
+    int32_t off[33];
+    int32_t jb[32];
+    int32_t a[32];
+    int32_t t[32];
+};
+
+// Applies up to kPins moved pins per lane (vertex moved a -> t, incident net e): Phi(e,a)--,
+// Phi(e,t)++, and from the old values the Lambda / S1 bit flips and the objective change
+// (Sec. 2: a pin count that steps 1 -> 0 removes the block from Lambda(e), 0 -> 1 adds it,
+// each changing (lambda-1) by one; a step into or out of the value 1 flips the S1 bit), then
+// stamps e as moved in round r.  Every load and atomic of the kPins pins is issued before any
+// result is used, so their latencies overlap.
+constexpr int kPins = 4;
+
 template <typename Rec>
-__device__ __forceinline__ void apply_pin(const Dev &d, Rec *rc, int32_t w, bool wide, int32_t oa,
-                                          int32_t ot, typename RecIO<Rec>::Lam ba,
-                                          typename RecIO<Rec>::Lam bt, int32_t r, long long &dobj)
+__device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const ApplyWarp &w_,
+                                                int32_t i0, int32_t total, int32_t r)
 {
     typedef typename RecIO<Rec>::Lam Lam;
-    (void)d;
-    (void)wide;
-    // a step of a pin count 1->0 or 0->1 flips its Lambda bit and changes the objective by
-    // omega(e); a step into or out of the value 1 flips its S1 bit
-    const Lam lx = (oa == 1 ? ba : (Lam)0) | (ot == 0 ? bt : (Lam)0);
-    const Lam sx = ((oa == 1 || oa == 2) ? ba : (Lam)0) | ((ot == 0 || ot == 1) ? bt : (Lam)0);
-    if (sizeof(Lam) == 8) {
-        if (lx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->lam), (unsigned long long)lx);
-        if (sx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->s1), (unsigned long long)sx);
-    } else {
-        if (lx) atomicXor(reinterpret_cast<unsigned int *>(&rc->lam), (unsigned int)lx);
-        if (sx) atomicXor(reinterpret_cast<unsigned int *>(&rc->s1), (unsigned int)sx);
+    int32_t e[kPins], a[kPins], t[kPins], oa[kPins], ot[kPins], w[kPins], mv[kPins];
+    bool ok[kPins];
+#pragma unroll
+    for (int q = 0; q < kPins; ++q) {
+        const int32_t i = i0 + q * 32;
+        ok[q] = i < total;
+        e[q] = 0; a[q] = 0; t[q] = 0;
+        if (ok[q]) {
+            const int v = slot_of(w_.off, i);
+            a[q] = w_.a[v];
+            t[q] = w_.t[v];
+            e[q] = d.inc[w_.jb[v] + (i - w_.off[v])];
+        }
     }
-    dobj += (ot == 0 ? w : 0) - (oa == 1 ? w : 0);
-    stamp_moved(&rc->mv, r);
+#pragma unroll
+    for (int q = 0; q < kPins; ++q) {
+        if (!ok[q]) continue;
+        const bool wide = e[q] < 0;
+        const int32_t ee = e[q] & kNetMask;
+        const int32_t wrow = wide ? d.widx[ee] : 0;
+        Rec *rc = recs + ee;
+        mv[q] = __ldcg(&rc->mv);
+        w[q] = __ldg(&rc->w) & 0x7fffffff;
+        oa[q] = phi_add(d, ee, a[q], -1, wide, wrow);
+        ot[q] = phi_add(d, ee, t[q], +1, wide, wrow);
+    }
+    long long dobj = 0;
+#pragma unroll
+    for (int q = 0; q < kPins; ++q) {
+        if (!ok[q]) continue;
+        Rec *rc = recs + (e[q] & kNetMask);
+        const Lam ba = (Lam)1 << a[q], bt = (Lam)1 << t[q];
+        const Lam lx = (oa[q] == 1 ? ba : (Lam)0) | (ot[q] == 0 ? bt : (Lam)0);
+        const Lam sx = ((oa[q] == 1 || oa[q] == 2) ? ba : (Lam)0) | ((ot[q] == 0 || ot[q] == 1) ? bt : (Lam)0);
+        if (sizeof(Lam) == 8) {
+            if (lx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->lam), (unsigned long long)lx);
+            if (sx) atomicXor(reinterpret_cast<unsigned long long *>(&rc->s1), (unsigned long long)sx);
+        } else {
+            if (lx) atomicXor(reinterpret_cast<unsigned int *>(&rc->lam), (unsigned int)lx);
+            if (sx) atomicXor(reinterpret_cast<unsigned int *>(&rc->s1), (unsigned int)sx);
+        }
+        // stamp: every writer of round r derives the same value from the pre-round stamp,
+        // and one that already sees round r leaves it alone
+        const int32_t last = mv[q] >> 1;
+        if (last != r) rc->mv = (r << 1) | (last == r - 1 ? 1 : 0);
+        dobj += (long long)(ot[q] == 0 ? w[q] : 0) - (long long)(oa[q] == 1 ? w[q] : 0);
+    }
+    return dobj;
 }
 
-// Persistent: each warp walks warp ranges with a grid stride and applies the approved moves
-// of its range.  Ties at a block's threshold gain are approved in vertex-id order: the warp
+// Persistent: each warp walks warp ranges with a grid stride.  For each 32 candidates of a
+// range it decides approval (ties at a block's threshold gain in vertex-id order: the warp
 // starts from the tile's exclusive tie prefix and adds the ties of the earlier ranges of the
-// same tile itself, so warps never wait for each other.
+// same tile itself, so warps never wait for each other), then applies the approved moves
+// over their incidences flattened across the lanes, so all atomics are in flight at once.
 template <typename Rec>
-__global__ void __launch_bounds__(kThreads, 5) k_apply(Dev d, int32_t r, unsigned long long *st_row)
+__global__ void __launch_bounds__(kThreads, 4) k_apply(Dev d, int32_t r, unsigned long long *st_row)
 {
-    typedef typename RecIO<Rec>::Lam Lam;
     __shared__ int mode[64];
     __shared__ int32_t gthr[64];
     __shared__ long long rem[64];
     __shared__ unsigned long long run[kWarps][64];
     __shared__ unsigned long long bwd[64];
+    __shared__ ApplyWarp aw[kWarps];
     __shared__ unsigned long long objd, napp, mpins;
     __shared__ int any_thr;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -767,6 +815,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_apply(Dev d, int32_t r, unsigne
     }
     __syncthreads();
     Rec *recs = reinterpret_cast<Rec *>(d.rec);
+    ApplyWarp &w_ = aw[wid];
     long long dobj = 0;
     int32_t nappr = 0, npins = 0;
     for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
@@ -816,41 +865,34 @@ __global__ void __launch_bounds__(kThreads, 5) k_apply(Dev d, int32_t r, unsigne
                 }
                 __syncwarp();
             }
+            int32_t deg = 0, jb = 0, a = 0;
             if (appr) {
                 const int32_t u = range * kRange + ul;
-                const int a = d.part[u];
+                a = d.part[u];
                 d.part[u] = (uint8_t)t;
                 atomicAdd(&bwd[a], (unsigned long long)(-(long long)cw));
                 atomicAdd(&bwd[t], cw);
-                const Lam ba = (Lam)1 << a, bt = (Lam)1 << t;
-                const int32_t jb = d.vtx_off[u], je = d.vtx_off[u + 1];
-                int32_t j = jb;
-                for (; j + 1 < je; j += 2) {
-                    const int32_t e0 = d.inc[j], e1 = d.inc[j + 1];
-                    Rec *r0 = recs + e0, *r1 = recs + e1;
-                    const int32_t wf0 = r0->w, wf1 = r1->w;
-                    const bool wd0 = wf0 < 0, wd1 = wf1 < 0;
-                    const int32_t wr0 = wd0 ? d.widx[e0] : 0, wr1 = wd1 ? d.widx[e1] : 0;
-                    const int32_t oa0 = phi_add(d, e0, a, -1, wd0, wr0);
-                    const int32_t ot0 = phi_add(d, e0, t, +1, wd0, wr0);
-                    const int32_t oa1 = phi_add(d, e1, a, -1, wd1, wr1);
-                    const int32_t ot1 = phi_add(d, e1, t, +1, wd1, wr1);
-                    apply_pin<Rec>(d, r0, wf0 & 0x7fffffff, wd0, oa0, ot0, ba, bt, r, dobj);
-                    apply_pin<Rec>(d, r1, wf1 & 0x7fffffff, wd1, oa1, ot1, ba, bt, r, dobj);
-                }
-                if (j < je) {
-                    const int32_t e0 = d.inc[j];
-                    Rec *r0 = recs + e0;
-                    const int32_t wf0 = r0->w;
-                    const bool wd0 = wf0 < 0;
-                    const int32_t wr0 = wd0 ? d.widx[e0] : 0;
-                    const int32_t oa0 = phi_add(d, e0, a, -1, wd0, wr0);
-                    const int32_t ot0 = phi_add(d, e0, t, +1, wd0, wr0);
-                    apply_pin<Rec>(d, r0, wf0 & 0x7fffffff, wd0, oa0, ot0, ba, bt, r, dobj);
-                }
+                jb = d.vtx_off[u];
+                deg = d.vtx_off[u + 1] - jb;
                 ++nappr;
-                npins += je - jb;
+                npins += deg;
             }
+            int32_t incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t total = __shfl_sync(kFull, incl, 31);
+            w_.off[lane] = incl - deg;
+            w_.jb[lane] = jb;
+            w_.a[lane] = a;
+            w_.t[lane] = t;
+            if (lane == 31) w_.off[32] = total;
+            __syncwarp();
+            for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
+                dobj += apply_pins<Rec>(d, recs, w_, i0 + lane, total, r);
+            __syncwarp();
         }
     }
     for (int o = 16; o; o >>= 1) {

@@ -197,6 +197,16 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
     if ((threadIdx.x & 31) == 0) atomicMax(max_w, local);
 }
 
+// bit 31 of inc[j] marks incidences of nets whose Phi row lives in the wide table
+__global__ void k_flag_wide_inc(const int32_t *off, int32_t *inc, int64_t P, int32_t narrow_max)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = inc[j];
+        if (off[e + 1] - off[e] > narrow_max) inc[j] = e | (int32_t)kWideFlag;
+    }
+}
+
 __global__ void k_wide_flags(const int32_t *off, int32_t m, int32_t narrow_max, int32_t *flags)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
@@ -565,6 +575,10 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(cudaStreamSynchronize(st));
     if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
     h->max_vertex_netweight = (int64_t)maxw;
+    if (h->n_wide > 0 && P > 0) {
+        k_flag_wide_inc<<<grid_for(P, 256), 256, 0, st>>>(net_off, inc, P, narrow_max); h->launches++;
+        CKF(cudaGetLastError());
+    }
 
     // ---- state
     uint8_t *part = nullptr;
