@@ -178,6 +178,40 @@ int hgp_get_profile(hgp_handle *h, hgp_profile *out);
 /* Number of kernels the handle has launched since creation (all phases, setup included). */
 int hgp_get_launch_count(hgp_handle *h, int64_t *out);
 
+/*
+ * Allocation-free gain step.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they need the computation, for example
+ * code running while an application allocator owns the whole device, inside host callbacks
+ * where cudaMalloc is not allowed, or on latency-critical paths that must not block on the
+ * allocator.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Computes, for the partition `part`, the candidates of sub-round s (0 <= s < subrounds) of
+ * the first round (every vertex eligible), exactly as hgp_debug_candidates does on a handle
+ * freshly created from the same inputs and options: target[u] = best block or -1, gain[u] =
+ * its gain or 0.
+ *
+ *   All arrays are DEVICE pointers owned by the caller: net_offsets int32[m+1] and pins
+ *   int32[P] (net -> pins), vtx_offsets int32[n+1] and inc_nets int32[P] (vertex -> incident
+ *   nets, the transpose of the first CSR; the caller must pass a consistent pair), vertex_w
+ *   int32[n] / net_w int32[m] or NULL for unit weights, part int32[n]; outputs target
+ *   int32[n] and gain int64[n].  Work is queued on cuda_stream (NULL = default stream); the
+ *   call synchronises that stream once to validate the inputs, then returns with the
+ *   computation queued.
+ *   Limit: m <= 262144 nets (2^18); k <= 64; subrounds <= 64.  Larger m returns
+ *   HGP_ERR_UNSUPPORTED.  Out-of-range offsets, pins, incident nets, partition entries or
+ *   non-positive weights return HGP_ERR_INVALID before any other kernel runs.
+ *   Scratch: a fixed 8 MiB device array inside the library, held on every GPU that loads the
+ *   library until the process exits.  Its address is looked up on the first call made on
+ *   each device (with that device current), so that first call should come before any
+ *   stream capture.  All calls share the array and it keeps the last call's contents:
+ *   calls whose work overlaps on the GPU race and must be serialised by the caller.
+ */
+int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, const int32_t *pins,
+                           const int32_t *vtx_offsets, const int32_t *inc_nets,
+                           const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
+                           const int32_t *part, int32_t subrounds, uint64_t seed, int32_t s,
+                           int32_t *target, int64_t *gain, void *cuda_stream);
+
 /* Frees all device memory of the handle (NULL is allowed). */
 void hgp_destroy(hgp_handle *h);
 

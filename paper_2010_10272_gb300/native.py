@@ -86,6 +86,9 @@ def load_library():
                      "hgp_get_info", "hgp_debug_candidates", "hgp_set_profiling",
                      "hgp_get_profile", "hgp_get_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
+        lib.hgp_candidates_noalloc.argtypes = [i32, i32, P, P, P, P, P, P, i32, f64, P, i32,
+                                               ctypes.c_uint64, i32, P, P, P]
+        lib.hgp_candidates_noalloc.restype = ctypes.c_int
         lib.hgp_destroy.argtypes = [P]
         lib.hgp_destroy.restype = None
         _lib = lib
@@ -264,3 +267,16 @@ class HGP:
         out = ctypes.c_int64()
         _check(self._lib.hgp_get_launch_count(self._h, ctypes.byref(out)), "hgp_get_launch_count")
         return out.value
+
+
+def candidates_noalloc(n, m, net_off, pins, vtx_off, inc, k, eps, part, target, gain,
+                       vertex_w=None, net_w=None, subrounds: int = 4, seed: int = 0, s: int = 0,
+                       stream=None):
+    """hgp_candidates_noalloc on torch CUDA tensors (int32 inputs, int32 target, int64 gain).
+    Returns the status code (0 = success)."""
+    lib = load_library()
+    sh = _stream_handle(stream)
+    return int(lib.hgp_candidates_noalloc(
+        int(n), int(m), _dptr(net_off), _dptr(pins), _dptr(vtx_off), _dptr(inc), _dptr(vertex_w),
+        _dptr(net_w), int(k), float(eps), _dptr(part), int(subrounds), int(seed), int(s),
+        _dptr(target), _dptr(gain), ctypes.c_void_p(sh) if sh else None))
