@@ -66,7 +66,9 @@ typedef struct {
     int32_t debug;       /* bit 0 (check mode): hgp_refine recomputes the objective from the
                             Phi table after the call and returns HGP_ERR_INTERNAL if it differs
                             from the incrementally maintained one [0] */
-    int32_t graph;       /* 1: replay refine() calls of the same round count as a CUDA graph [0] */
+    int32_t graph;       /* 1: hgp_refine captures its launches as a CUDA graph on the first call
+                            with a given round count and replays it afterwards [0]; ignored
+                            while profiling is on */
     void *cuda_stream;   /* cudaStream_t to run on, or NULL for a library-owned stream */
 } hgp_options;
 
@@ -167,6 +169,42 @@ int hgp_get_info(hgp_handle *h, int32_t *n, int32_t *m, int32_t *k, int64_t *pin
  * block); gain: host int64[n] (0 where target is -1).
  */
 int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain);
+
+/*
+ * Batches: many handles (hypergraphs of uneven sizes, any k and Phi width) refined together.
+ * Every phase of a round is one kernel launch over the work items of all member handles
+ * (members with k <= 32 and k > 32 form two groups), and by default the launches of a
+ * hgp_batch_refine call are captured once as a CUDA graph and replayed.  The arithmetic of
+ * each member is unchanged: refining a handle inside a batch gives exactly the result of
+ * refining it alone.  The batch does not own the handles; they must outlive it, must not be
+ * used elsewhere while a batch call runs, and their round numbering advances with the batch.
+ */
+typedef struct {
+    int32_t graph;              /* 1: capture/replay a CUDA graph per round count [1] */
+    int32_t gain_ctas_per_sm;   /* persistent grid of the gain kernel, CTAs per SM; 0 = occupancy */
+    int32_t apply_ctas_per_sm;  /* persistent grid of the apply kernel, CTAs per SM; 0 = occupancy */
+    int32_t reserved;
+    void *cuda_stream;          /* stream the batch runs on, or NULL for a library-owned stream */
+} hgp_batch_options;
+
+void hgp_batch_default_options(hgp_batch_options *opt);
+
+/* handles: host array of `count` distinct handles on the current device. */
+int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_options *opt,
+                     hgp_batch **out);
+
+/* Runs `rounds` rounds on every member.  stats: NULL or host hgp_round_stats[count * rounds],
+ * member-major (member i's rounds at [i * rounds, (i + 1) * rounds)); filled on return, and the
+ * call then synchronises.  Without stats the call returns with the work queued. */
+int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
+
+/* Waits for the batch's queued work. */
+int hgp_batch_synchronize(hgp_batch *b);
+
+/* Kernel launches issued by the batch so far (graph replays count their kernels). */
+int hgp_batch_get_launch_count(hgp_batch *b, int64_t *out);
+
+void hgp_batch_destroy(hgp_batch *b);
 
 /* Turns per-phase event timing on (enable != 0) or off, and clears the accumulated profile.
  * While on, hgp_refine synchronises the handle's stream before returning. */

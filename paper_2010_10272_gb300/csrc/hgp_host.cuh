@@ -27,7 +27,10 @@ struct hgp_handle {
     // CUDA-graph cache: one refine() of `graph_rounds` rounds
     cudaGraphExec_t graph_exec = nullptr;
     int32_t graph_rounds = 0;
-    int32_t *d_round = nullptr;   // device copy of the round counter (graph mode)
+    int32_t *d_round = nullptr;   // device round state (Dev::rs)
+    hgp::Dev *d_dev = nullptr;    // device copy of d, read by the kernels
+    bool dev_dirty = true;        // d changed since the last upload
+    int64_t graph_launches = 0;   // kernels in one replay of graph_exec
     // kernel launches since creation, and per-phase event timing
     int64_t launches = 0;
     int grid_gain = 0;            // persistent grid sizes (CTAs), set at first launch

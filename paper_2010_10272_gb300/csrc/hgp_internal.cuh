@@ -95,6 +95,9 @@ struct Dev {
     int64_t *tie;           // [k * n_tiles]
     int64_t *stats;         // [rounds * ST_N]
     int32_t *err;
+    uint64_t seed;          // sub-round hash seed
+    int32_t *rs;            // round state on the device: rs[0] = next round r, rs[1] = 0 while
+                            // every vertex is eligible (first round), 1 afterwards
 };
 
 __device__ __forceinline__ int lam_bits_ctz(uint32_t x) { return __ffs(x) - 1; }

@@ -23,13 +23,19 @@
 //                  Phi(e,t)++ with integer atomics, and Lambda(e), S1(e) and the objective
 //                  from the atomics' old values (each step of a pin count across 0/1/2 toggles
 //                  the matching bit, so the final bits are right whatever the order).
-//   k_round_end    per-round objective and heaviest block.
+//   k_round_end    per-round objective and heaviest block; advances the device round state.
+//
+// Every kernel takes the instance state as `const Dev *devs` in device memory and a list of
+// work items.  A single-handle launch passes items == nullptr: item i is the handle's own
+// range / tile / block i.  A batch launch passes (instance, local index) pairs covering many
+// handles at once, so one launch per phase refines a whole batch.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "hgp_host.cuh"
 
@@ -46,14 +52,37 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// instance and local index of work item i
+__device__ __forceinline__ const Dev &item_of(const Dev *devs, const int2 *items, int32_t i, int32_t &local)
+{
+    if (items) {
+        const int2 it = items[i];
+        local = it.y;
+        return devs[it.x];
+    }
+    local = i;
+    return devs[0];
+}
+
+__device__ __forceinline__ int32_t item_count(const Dev *devs, const int2 *items, int32_t n_items, int kind)
+{
+    if (items) return n_items;
+    return kind == 0 ? devs[0].n_ranges : (kind == 1 ? devs[0].n_tiles : devs[0].k);
+}
+
 // ------------------------------------------------------------------ round preparation
-__global__ void __launch_bounds__(kThreads) k_round_prep(Dev d, int32_t r, uint64_t seed)
+// warp per range item
+__global__ void __launch_bounds__(kThreads) k_round_prep(const Dev *devs, const int2 *items, int32_t n_items)
 {
     __shared__ uint8_t subs[kWarps][kRange];
     __shared__ int32_t cnt[kWarps][65];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t range = blockIdx.x * kWarps + wid;
-    if (range >= d.n_ranges) return;
+    const int32_t item = blockIdx.x * kWarps + wid;
+    if (item >= item_count(devs, items, n_items, 0)) return;
+    int32_t range;
+    const Dev d = item_of(devs, items, item, range);
+    const int32_t r = d.rs[0];
+    const uint64_t seed = d.seed;
     const int32_t base = range * kRange;
     const int32_t nv = min(kRange, d.n - base);
     const int32_t S = d.S;
@@ -249,51 +278,38 @@ __device__ __forceinline__ void best_by_planes(int np, const GainWarp<Lam> &g, c
 
 constexpr int32_t kPlaneMaxW = 2047;   // W(u) up to this uses bit planes (NP <= 11)
 
-// Persistent: each warp walks warp ranges with a grid stride and takes the vertices of
-// sub-round s of a range 32 at a time (one slot per lane).
-//   pass A  flattened over the chunk's incidences (every record gather issued at once): W,
-//           b(u) (Sec. 5), eligibility (Sec. 6) and T = union of Lambda(e) over the nets with
-//           Phi(e,a) = 1, minus a and the blocks without room for c(u); (Lambda, omega) of each
-//           incidence is kept in shared memory.  Only blocks in T can have a positive gain,
-//           since g_t <= omega({e : Phi(e,a) = 1, t in Lambda(e)}).
-//   pass B  per vertex, conn_t = omega({e in I(u) : t in Lambda(e)}) for all t in T at once in
-//           bit planes, and the arg-max of g_t = b(u) - W + conn_t.
-// A vertex whose incident net weights exceed kPlaneMaxW uses a warp-cooperative pass instead.
+// Per-warp state of the gain step that depends on the instance.
+template <typename Lam>
+struct GainInst {
+    Lam feas1;           // blocks with room for a unit-weight vertex
+    int32_t r;           // round number
+    int32_t all_elig;    // first round: every vertex eligible
+};
+
+// One range item of the gain step (see k_gain); returns the number of candidates written.
 template <typename Rec>
-__global__ void __launch_bounds__(kThreads, 4) k_gain(Dev d, int32_t r, int32_t s, int32_t all_elig,
-                                                      unsigned long long *st_row)
+__device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32_t s, GainWarp<typename RecIO<Rec>::Lam> &g,
+                                              const long long *slack, unsigned long long *tot,
+                                              const GainInst<typename RecIO<Rec>::Lam> &gi, int32_t &nel)
 {
     typedef typename RecIO<Rec>::Lam Lam;
     constexpr bool kWide = sizeof(Lam) == 8;
-    __shared__ GainWarp<Lam> ws[kWarps];
-    __shared__ long long slack[64];
-    __shared__ unsigned long long tot_s[64];
-    __shared__ unsigned long long cnt_s[2];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid < 64) {
-        tot_s[tid] = 0;
-        slack[tid] = tid < d.k ? d.lmax - d.bw[tid] : -1;
-    }
-    if (tid < 2) cnt_s[tid] = 0;
-    __syncthreads();
-    Lam feas1;
-    {
-        const unsigned lo = __ballot_sync(kFull, slack[lane] >= 1);
-        const unsigned hi = __ballot_sync(kFull, slack[lane + 32] >= 1);
-        if (kWide) feas1 = (Lam)((uint64_t)lo | ((uint64_t)hi << 32));
-        else feas1 = (Lam)lo;
-    }
-    GainWarp<Lam> &g = ws[wid];
-    const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
-    const bool unit = d.nw == nullptr;
-    int32_t nelig = 0, ncand = 0;
-    for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
+    const int lane = threadIdx.x & 31;
+    const Lam feas1 = gi.feas1;
+    const int32_t r = gi.r, all_elig = gi.all_elig;
+        const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
+        const bool unit = d.nw == nullptr;
         const int32_t rbase = range * kRange;
-        const uint16_t *ss = d.sub_start + (int64_t)range * (d.S + 1);
-        const int32_t beg = ss[s], cnt = (int32_t)ss[s + 1] - beg;
+        int32_t beg = 0, cnt = 0;
+        if (s < d.S) {
+            const uint16_t *ss = d.sub_start + (int64_t)range * (d.S + 1);
+            beg = ss[s];
+            cnt = (int32_t)ss[s + 1] - beg;
+        }
         const uint8_t *list = d.sub_list + (int64_t)range * kRange + beg;
         uint64_t *out = d.cand + (int64_t)range * kRange;
         int32_t nout = 0;
+        nel = 0;
         for (int32_t c0 = 0; c0 < cnt; c0 += 32) {
             const int32_t idx = c0 + lane;
             const bool valid = idx < cnt;
@@ -445,28 +461,130 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(Dev d, int32_t r, int32_t 
                     g_best = (int32_t)(key >> 8);
                 }
             }
-            nelig += __popc(__ballot_sync(kFull, elig));
+            nel += __popc(__ballot_sync(kFull, elig));
             const unsigned cm = __ballot_sync(kFull, t_best >= 0);
             if (t_best >= 0) {
                 const int pos = nout + __popc(cm & lanemask_lt());
                 out[pos] = ((uint64_t)(uint32_t)g_best << 32) | ((uint32_t)ul << 8) | (uint32_t)t_best;
-                atomicAdd(&tot_s[t_best], (unsigned long long)cu);
+                atomicAdd(&tot[t_best], (unsigned long long)cu);
             }
             nout += __popc(cm);
             __syncwarp();
         }
-        if (lane == 0) d.cand_cnt[range] = nout;
-        ncand += nout;
+        return nout;
+}
+
+template <typename Rec>
+__device__ __forceinline__ void gain_refresh(const Dev &d, long long *slack, GainInst<typename RecIO<Rec>::Lam> &gi)
+{
+    typedef typename RecIO<Rec>::Lam Lam;
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < 64; t += 32) slack[t] = t < d.k ? d.lmax - d.bw[t] : -1;
+    __syncwarp();
+    const unsigned lo = __ballot_sync(kFull, slack[lane] >= 1);
+    const unsigned hi = __ballot_sync(kFull, slack[lane + 32] >= 1);
+    if (sizeof(Lam) == 8) gi.feas1 = (Lam)((uint64_t)lo | ((uint64_t)hi << 32));
+    else gi.feas1 = (Lam)lo;
+    gi.r = d.rs[0];
+    gi.all_elig = d.rs[1] == 0;
+}
+
+// copies devs[inst] into a warp's shared slot
+__device__ __forceinline__ void load_dev(Dev &dst, const Dev *src)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t *a = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *b = reinterpret_cast<uint32_t *>(&dst);
+    for (int i = lane; i < (int)(sizeof(Dev) / 4); i += 32) b[i] = a[i];
+    __syncwarp();
+}
+
+// Persistent: each warp walks range items with a grid stride and takes the vertices of
+// sub-round s of a range 32 at a time (one slot per lane).
+//   pass A  flattened over the chunk's incidences (every record gather issued at once): W,
+//           b(u) (Sec. 5), eligibility (Sec. 6) and T = union of Lambda(e) over the nets with
+//           Phi(e,a) = 1, minus a and the blocks without room for c(u); (Lambda, omega) of each
+//           incidence is kept in shared memory.  Only blocks in T can have a positive gain,
+//           since g_t <= omega({e : Phi(e,a) = 1, t in Lambda(e)}).
+//   pass B  per vertex, conn_t = omega({e in I(u) : t in Lambda(e)}) for all t in T at once in
+//           bit planes, and the arg-max of g_t = b(u) - W + conn_t.
+// A vertex whose incident net weights exceed kPlaneMaxW uses a warp-cooperative pass instead.
+// B = false: one instance, d0 (parameter space), items are its ranges; B = true: a batch,
+// items name (instance, range) and each warp copies its item's instance into shared memory.
+template <typename Rec, bool B>
+__global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *devs, const int2 *items,
+                                                      int32_t n_items, int32_t s, int32_t rr)
+{
+    typedef typename RecIO<Rec>::Lam Lam;
+    __shared__ GainWarp<Lam> ws[kWarps];
+    __shared__ long long slack_w[kWarps][64];
+    __shared__ unsigned long long tot_w[kWarps][64];
+    __shared__ Dev dsm[B ? kWarps : 1];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    tot_w[wid][lane] = 0;
+    tot_w[wid][lane + 32] = 0;
+    GainInst<Lam> gi;
+    int32_t nelig = 0, ncand = 0;
+    int inst_prev = -1;
+    const int32_t n_it = B ? n_items : d0.n_ranges;
+    for (int32_t item = blockIdx.x * kWarps + wid; item < n_it; item += gridDim.x * kWarps) {
+        if (B) {
+            const int2 it = items[item];
+            if (it.x != inst_prev) {
+                load_dev(dsm[wid], devs + it.x);
+                gain_refresh<Rec>(dsm[wid], slack_w[wid], gi);
+                inst_prev = it.x;
+            }
+            const Dev &d = dsm[wid];
+            int32_t nel = 0;
+            const int32_t nout = gain_range<Rec>(d, it.y, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel);
+            if (lane == 0) d.cand_cnt[it.y] = nout;
+            // flush this item's totals into its own instance
+            unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
+            for (int t = lane; t < 64; t += 32) {
+                const unsigned long long v = tot_w[wid][t];
+                if (v) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&d.tot[t]), v);
+                    tot_w[wid][t] = 0;
+                }
+            }
+            if (lane == 0) {
+                if (nel) atomicAdd(row + ST_ELIG, (unsigned long long)nel);
+                if (nout) atomicAdd(row + ST_CAND, (unsigned long long)nout);
+            }
+            __syncwarp();
+        } else {
+            if (inst_prev < 0) {
+                gain_refresh<Rec>(d0, slack_w[wid], gi);
+                inst_prev = 0;
+            }
+            int32_t nel = 0;
+            const int32_t nout = gain_range<Rec>(d0, item, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel);
+            if (lane == 0) d0.cand_cnt[item] = nout;
+            nelig += nel;
+            ncand += nout;
+        }
     }
-    if (lane == 0) {
-        if (nelig) atomicAdd(&cnt_s[0], (unsigned long long)nelig);
-        if (ncand) atomicAdd(&cnt_s[1], (unsigned long long)ncand);
-    }
-    __syncthreads();
-    if (tid < d.k && tot_s[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&d.tot[tid]), tot_s[tid]);
-    if (tid == 0) {
-        if (cnt_s[0]) atomicAdd(st_row + ST_ELIG, cnt_s[0]);
-        if (cnt_s[1]) atomicAdd(st_row + ST_CAND, cnt_s[1]);
+    if (!B) {
+        // one instance: combine the warps of the CTA, then one atomic per block
+        __shared__ unsigned long long cnt_s[2];
+        if (tid < 2) cnt_s[tid] = 0;
+        __syncthreads();
+        if (lane == 0) {
+            if (nelig) atomicAdd(&cnt_s[0], (unsigned long long)nelig);
+            if (ncand) atomicAdd(&cnt_s[1], (unsigned long long)ncand);
+        }
+        __syncthreads();
+        if (tid < 64 && tid < d0.k) {
+            unsigned long long v = 0;
+            for (int w = 0; w < kWarps; ++w) v += tot_w[w][tid];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.tot[tid]), v);
+        }
+        if (tid == 0) {
+            unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
+            if (cnt_s[0]) atomicAdd(row + ST_ELIG, cnt_s[0]);
+            if (cnt_s[1]) atomicAdd(row + ST_CAND, cnt_s[1]);
+        }
     }
 }
 
@@ -488,39 +606,40 @@ __device__ __forceinline__ int refine_digit(int32_t v, int level, int64_t prefix
     return v & 1023;
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(Dev d, int level)
+// warp per range item: histogram of candidate weight by gain for saturated target blocks
+__global__ void __launch_bounds__(kThreads) k_hist(const Dev *devs, const int2 *items, int32_t n_items, int level)
 {
-    __shared__ int active[64];
-    __shared__ long long prefix[64];
-    __shared__ int any;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) any = 0;
-    __syncthreads();
-    if (tid < 64) {
+    __shared__ int active[kWarps][64];
+    __shared__ long long prefix[kWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t item = blockIdx.x * kWarps + wid;
+    if (item >= item_count(devs, items, n_items, 0)) return;
+    int32_t range;
+    const Dev d = item_of(devs, items, item, range);
+    int a_any = 0;
+    for (int t = lane; t < 64; t += 32) {
         int a = 0;
-        if (tid < d.k) {
+        if (t < d.k) {
             if (level == 0) {
-                a = d.bw[tid] + d.tot[tid] > d.lmax;
+                a = d.bw[t] + d.tot[t] > d.lmax;
             } else {
-                const Sel sl = d.sel[tid];
+                const Sel sl = d.sel[t];
                 a = sl.mode == SEL_REFINE && sl.level == level;
-                prefix[tid] = sl.g;
+                prefix[wid][t] = sl.g;
             }
         }
-        active[tid] = a;
-        if (a) any = 1;
+        active[wid][t] = a;
+        a_any |= a;
     }
-    __syncthreads();
-    if (!any) return;
-    const int32_t range = blockIdx.x * kWarps + wid;
-    if (range >= d.n_ranges) return;
+    if (!__any_sync(kFull, a_any)) return;
+    __syncwarp();
     const int32_t n = d.cand_cnt[range];
     const uint64_t *cand = d.cand + (int64_t)range * kRange;
     for (int i = lane; i < n; i += 32) {
         int t, ul;
         int32_t g;
         decode(cand[i], t, g, ul);
-        if (!active[t]) continue;
+        if (!active[wid][t]) continue;
         const unsigned long long c = d.vw ? (unsigned long long)d.vw[range * kRange + ul] : 1ull;
         int bin;
         if (level == 0) {
@@ -528,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Dev d, int level)
         } else {
             if (g < kBins - 1) continue;
             bool match;
-            bin = refine_digit(g - (kBins - 1), level, prefix[t], match);
+            bin = refine_digit(g - (kBins - 1), level, prefix[wid][t], match);
             if (!match) continue;
         }
         atomicAdd(&d.hist[(int64_t)t * kBins + bin], c);
@@ -563,13 +682,16 @@ __device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long 
     return r;
 }
 
-// one CTA per block t: threshold of the (gain desc, id asc) prefix that fits
-__global__ void __launch_bounds__(kThreads) k_select(Dev d, int level)
+// one CTA per block item (instance, t): threshold of the (gain desc, id asc) prefix that fits
+__global__ void __launch_bounds__(kThreads) k_select(const Dev *devs, const int2 *items, int32_t n_items, int level)
 {
     __shared__ unsigned long long wt[32];
     __shared__ int found_bin;
     __shared__ long long found_before;
-    const int t = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
+    if ((int32_t)blockIdx.x >= item_count(devs, items, n_items, 2)) return;
+    int32_t t;
+    const Dev d = item_of(devs, items, blockIdx.x, t);
     Sel sl = d.sel[t];
     long long cap;
     int nbins;
@@ -597,7 +719,7 @@ __global__ void __launch_bounds__(kThreads) k_select(Dev d, int level)
     const int hi = nbins - per * tid;
     unsigned long long sum = 0;
     for (int b = hi - 1; b >= hi - per; --b) sum += row[b];
-    if (tid == 0) found_bin = -1;
+    if (tid == 0) { found_bin = -1; found_before = 0; }
     const unsigned long long before = block_scan_u64(sum, wt);
     if ((long long)before <= cap && (long long)(before + sum) > cap) {
         unsigned long long c = before;
@@ -635,13 +757,18 @@ __global__ void __launch_bounds__(kThreads) k_select(Dev d, int level)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_tie_sum(Dev d)
+// one CTA per tile item (instance, tile of 8 ranges): weight of the candidates at their
+// block's threshold gain, per block
+__global__ void __launch_bounds__(kThreads) k_tie_sum(const Dev *devs, const int2 *items, int32_t n_items)
 {
     __shared__ int thr[64];
     __shared__ int32_t gthr[64];
     __shared__ unsigned long long ts[64];
     __shared__ int any;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if ((int32_t)blockIdx.x >= item_count(devs, items, n_items, 1)) return;
+    int32_t tile;
+    const Dev d = item_of(devs, items, blockIdx.x, tile);
     if (tid == 0) any = 0;
     __syncthreads();
     if (tid < 64) {
@@ -657,7 +784,7 @@ __global__ void __launch_bounds__(kThreads) k_tie_sum(Dev d)
     }
     __syncthreads();
     if (!any) return;
-    const int32_t range = blockIdx.x * kWarps + wid;
+    const int32_t range = tile * kWarps + wid;
     if (range < d.n_ranges) {
         const int32_t n = d.cand_cnt[range];
         const uint64_t *cand = d.cand + (int64_t)range * kRange;
@@ -670,14 +797,17 @@ __global__ void __launch_bounds__(kThreads) k_tie_sum(Dev d)
         }
     }
     __syncthreads();
-    if (tid < d.k && thr[tid]) d.tie[(int64_t)tid * d.n_tiles + blockIdx.x] = (int64_t)ts[tid];
+    if (tid < d.k && thr[tid]) d.tie[(int64_t)tid * d.n_tiles + tile] = (int64_t)ts[tid];
 }
 
-__global__ void __launch_bounds__(1024) k_tie_scan(Dev d)
+// one CTA per block item: exclusive prefix of the tie weights over the tiles, in tile order
+__global__ void __launch_bounds__(1024) k_tie_scan(const Dev *devs, const int2 *items, int32_t n_items)
 {
     __shared__ unsigned long long wt[32];
     __shared__ unsigned long long carry;
-    const int t = blockIdx.x;
+    if ((int32_t)blockIdx.x >= item_count(devs, items, n_items, 2)) return;
+    int32_t t;
+    const Dev d = item_of(devs, items, blockIdx.x, t);
     if (d.sel[t].mode != SEL_THRESH) return;
     int64_t *row = d.tie + (int64_t)t * d.n_tiles;
     if (threadIdx.x == 0) carry = 0;
@@ -782,150 +912,235 @@ __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const A
     return dobj;
 }
 
-// Persistent: each warp walks warp ranges with a grid stride.  For each 32 candidates of a
+// Per-warp approval state of one instance.
+struct ApplyInst {
+    int mode[64];
+    int32_t gthr[64];
+    long long rem[64];
+};
+
+__device__ __forceinline__ bool apply_refresh(const Dev &d, ApplyInst &ai, int32_t &r)
+{
+    const int lane = threadIdx.x & 31;
+    int thr_any = 0;
+    for (int t = lane; t < 64; t += 32) {
+        int md = SEL_ALL;
+        if (t < d.k) {
+            const Sel sl = d.sel[t];
+            md = sl.mode;
+            ai.gthr[t] = (int32_t)sl.g;
+            ai.rem[t] = sl.rem;
+        }
+        ai.mode[t] = md;
+        thr_any |= md == SEL_THRESH;
+    }
+    r = d.rs[0];
+    __syncwarp();
+    return __any_sync(kFull, thr_any) != 0;
+}
+
+// One range item of the apply step (see k_apply).
+template <typename Rec>
+__device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t r, bool any_thr,
+                                            const ApplyInst &ai, unsigned long long *run,
+                                            unsigned long long *bwd, ApplyWarp &w_, long long &idobj,
+                                            int32_t &iappr, int32_t &ipins)
+{
+    const int lane = threadIdx.x & 31;
+    const int *mode = ai.mode;
+    const int32_t *gthr = ai.gthr;
+    const long long *rem = ai.rem;
+    Rec *recs = reinterpret_cast<Rec *>(d.rec);
+    const int32_t ncand = d.cand_cnt[range];
+    if (ncand == 0) return;
+    const uint64_t *cand = d.cand + (int64_t)range * kRange;
+    if (any_thr) {
+        const int32_t tile = range / kWarps;
+        for (int t = lane; t < 64; t += 32)
+            run[t] = (t < d.k && mode[t] == SEL_THRESH)
+                         ? (unsigned long long)d.tie[(int64_t)t * d.n_tiles + tile] : 0ull;
+        __syncwarp();
+        for (int32_t pr = tile * kWarps; pr < range; ++pr) {
+            const int32_t n2 = d.cand_cnt[pr];
+            const uint64_t *c2 = d.cand + (int64_t)pr * kRange;
+            for (int i = lane; i < n2; i += 32) {
+                int t, ul;
+                int32_t g;
+                decode(c2[i], t, g, ul);
+                if (mode[t] == SEL_THRESH && g == gthr[t])
+                    atomicAdd(&run[t], d.vw ? (unsigned long long)d.vw[pr * kRange + ul] : 1ull);
+            }
+        }
+        __syncwarp();
+    }
+    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+        const int idx = c0 + lane;
+        int t = 0, ul = 0;
+        int32_t g = 0;
+        unsigned long long cw = 1;
+        bool appr = false, tie = false;
+        if (idx < ncand) {
+            decode(cand[idx], t, g, ul);
+            if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
+            const int md = mode[t];
+            if (md == SEL_ALL || g > gthr[t]) appr = true;
+            else if (g == gthr[t]) tie = true;
+        }
+        // ties in id order: exclusive prefix so far + own weight must fit the budget
+        unsigned tm = __ballot_sync(kFull, tie);
+        while (tm) {
+            const int l = __ffs(tm) - 1;
+            tm &= tm - 1;
+            if (lane == l) {
+                appr = (long long)(run[t] + cw) <= rem[t];
+                run[t] += cw;
+            }
+            __syncwarp();
+        }
+        int32_t deg = 0, jb = 0, a = 0;
+        if (appr) {
+            const int32_t u = range * kRange + ul;
+            a = d.part[u];
+            d.part[u] = (uint8_t)t;
+            atomicAdd(&bwd[a], (unsigned long long)(-(long long)cw));
+            atomicAdd(&bwd[t], cw);
+            jb = d.vtx_off[u];
+            deg = d.vtx_off[u + 1] - jb;
+            ++iappr;
+            ipins += deg;
+        }
+        int32_t incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t total = __shfl_sync(kFull, incl, 31);
+        w_.off[lane] = incl - deg;
+        w_.jb[lane] = jb;
+        w_.a[lane] = a;
+        w_.t[lane] = t;
+        if (lane == 31) w_.off[32] = total;
+        __syncwarp();
+        for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
+            idobj += apply_pins<Rec>(d, recs, w_, i0 + lane, total, r);
+        __syncwarp();
+    }
+}
+
+// Persistent: each warp walks range items with a grid stride.  For each 32 candidates of a
 // range it decides approval (ties at a block's threshold gain in vertex-id order: the warp
 // starts from the tile's exclusive tie prefix and adds the ties of the earlier ranges of the
 // same tile itself, so warps never wait for each other), then applies the approved moves
 // over their incidences flattened across the lanes, so all atomics are in flight at once.
-template <typename Rec>
-__global__ void __launch_bounds__(kThreads, 4) k_apply(Dev d, int32_t r, unsigned long long *st_row)
+// B as for k_gain.
+template <typename Rec, bool B>
+__global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *devs, const int2 *items,
+                                                       int32_t n_items, int32_t rr)
 {
-    __shared__ int mode[64];
-    __shared__ int32_t gthr[64];
-    __shared__ long long rem[64];
+    __shared__ ApplyInst ai_w[kWarps];
     __shared__ unsigned long long run[kWarps][64];
-    __shared__ unsigned long long bwd[64];
+    __shared__ unsigned long long bwd_w[kWarps][64];
     __shared__ ApplyWarp aw[kWarps];
-    __shared__ unsigned long long objd, napp, mpins;
-    __shared__ int any_thr;
+    __shared__ Dev dsm[B ? kWarps : 1];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) { objd = 0; napp = 0; mpins = 0; any_thr = 0; }
-    __syncthreads();
-    if (tid < 64) {
-        int md = SEL_ALL;
-        if (tid < d.k) {
-            const Sel sl = d.sel[tid];
-            md = sl.mode;
-            gthr[tid] = (int32_t)sl.g;
-            rem[tid] = sl.rem;
-        }
-        mode[tid] = md;
-        bwd[tid] = 0;
-        if (md == SEL_THRESH) any_thr = 1;
-    }
-    __syncthreads();
-    Rec *recs = reinterpret_cast<Rec *>(d.rec);
-    ApplyWarp &w_ = aw[wid];
+    bwd_w[wid][lane] = 0;
+    bwd_w[wid][lane + 32] = 0;
     long long dobj = 0;
-    int32_t nappr = 0, npins = 0;
-    for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
-        const int32_t ncand = d.cand_cnt[range];
-        if (ncand == 0) continue;
-        const uint64_t *cand = d.cand + (int64_t)range * kRange;
-        if (any_thr) {
-            const int32_t tile = range / kWarps;
-            for (int t = lane; t < 64; t += 32)
-                run[wid][t] = (t < d.k && mode[t] == SEL_THRESH)
-                                  ? (unsigned long long)d.tie[(int64_t)t * d.n_tiles + tile] : 0ull;
+    int32_t nappr = 0, npins = 0, r = 0;
+    int inst_prev = -1;
+    bool any_thr = false;
+    const int32_t n_it = B ? n_items : d0.n_ranges;
+    for (int32_t item = blockIdx.x * kWarps + wid; item < n_it; item += gridDim.x * kWarps) {
+        long long idobj = 0;
+        int32_t iappr = 0, ipins = 0;
+        if (B) {
+            const int2 it = items[item];
+            if (it.x != inst_prev) {
+                load_dev(dsm[wid], devs + it.x);
+                any_thr = apply_refresh(dsm[wid], ai_w[wid], r);
+                inst_prev = it.x;
+            }
+            const Dev &d = dsm[wid];
+            apply_range<Rec>(d, it.y, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            for (int o = 16; o; o >>= 1) {
+                idobj += __shfl_xor_sync(kFull, idobj, o);
+                iappr += __shfl_xor_sync(kFull, iappr, o);
+                ipins += __shfl_xor_sync(kFull, ipins, o);
+            }
             __syncwarp();
-            for (int32_t pr = tile * kWarps; pr < range; ++pr) {
-                const int32_t n2 = d.cand_cnt[pr];
-                const uint64_t *c2 = d.cand + (int64_t)pr * kRange;
-                for (int i = lane; i < n2; i += 32) {
-                    int t, ul;
-                    int32_t g;
-                    decode(c2[i], t, g, ul);
-                    if (mode[t] == SEL_THRESH && g == gthr[t])
-                        atomicAdd(&run[wid][t], d.vw ? (unsigned long long)d.vw[pr * kRange + ul] : 1ull);
+            for (int t = lane; t < 64; t += 32) {
+                const unsigned long long v = bwd_w[wid][t];
+                if (v) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[t]), v);
+                    bwd_w[wid][t] = 0;
                 }
             }
+            if (lane == 0) {
+                unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
+                if (idobj) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)idobj);
+                if (iappr) atomicAdd(row + ST_APPR, (unsigned long long)iappr);
+                if (ipins) atomicAdd(row + ST_MOVED, (unsigned long long)ipins);
+            }
             __syncwarp();
-        }
-        for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
-            const int idx = c0 + lane;
-            int t = 0, ul = 0;
-            int32_t g = 0;
-            unsigned long long cw = 1;
-            bool appr = false, tie = false;
-            if (idx < ncand) {
-                decode(cand[idx], t, g, ul);
-                if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
-                const int md = mode[t];
-                if (md == SEL_ALL || g > gthr[t]) appr = true;
-                else if (g == gthr[t]) tie = true;
+        } else {
+            if (inst_prev < 0) {
+                any_thr = apply_refresh(d0, ai_w[wid], r);
+                inst_prev = 0;
             }
-            // ties in id order: exclusive prefix so far + own weight must fit the budget
-            unsigned tm = __ballot_sync(kFull, tie);
-            while (tm) {
-                const int l = __ffs(tm) - 1;
-                tm &= tm - 1;
-                if (lane == l) {
-                    appr = (long long)(run[wid][t] + cw) <= rem[t];
-                    run[wid][t] += cw;
-                }
-                __syncwarp();
-            }
-            int32_t deg = 0, jb = 0, a = 0;
-            if (appr) {
-                const int32_t u = range * kRange + ul;
-                a = d.part[u];
-                d.part[u] = (uint8_t)t;
-                atomicAdd(&bwd[a], (unsigned long long)(-(long long)cw));
-                atomicAdd(&bwd[t], cw);
-                jb = d.vtx_off[u];
-                deg = d.vtx_off[u + 1] - jb;
-                ++nappr;
-                npins += deg;
-            }
-            int32_t incl = deg;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int32_t total = __shfl_sync(kFull, incl, 31);
-            w_.off[lane] = incl - deg;
-            w_.jb[lane] = jb;
-            w_.a[lane] = a;
-            w_.t[lane] = t;
-            if (lane == 31) w_.off[32] = total;
-            __syncwarp();
-            for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
-                dobj += apply_pins<Rec>(d, recs, w_, i0 + lane, total, r);
-            __syncwarp();
+            apply_range<Rec>(d0, item, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            dobj += idobj;
+            nappr += iappr;
+            npins += ipins;
         }
     }
-    for (int o = 16; o; o >>= 1) {
-        dobj += __shfl_xor_sync(kFull, dobj, o);
-        nappr += __shfl_xor_sync(kFull, nappr, o);
-        npins += __shfl_xor_sync(kFull, npins, o);
-    }
-    if (lane == 0) {
-        if (dobj) atomicAdd(&objd, (unsigned long long)dobj);
-        if (nappr) atomicAdd(&napp, (unsigned long long)nappr);
-        if (npins) atomicAdd(&mpins, (unsigned long long)npins);
-    }
-    __syncthreads();
-    if (tid < d.k && bwd[tid]) atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[tid]), bwd[tid]);
-    if (tid == 0) {
-        if (objd) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), objd);
-        if (napp) atomicAdd(st_row + ST_APPR, napp);
-        if (mpins) atomicAdd(st_row + ST_MOVED, mpins);
+    if (!B) {
+        __shared__ unsigned long long objd, napp, mpins;
+        for (int o = 16; o; o >>= 1) {
+            dobj += __shfl_xor_sync(kFull, dobj, o);
+            nappr += __shfl_xor_sync(kFull, nappr, o);
+            npins += __shfl_xor_sync(kFull, npins, o);
+        }
+        if (tid == 0) { objd = 0; napp = 0; mpins = 0; }
+        __syncthreads();
+        if (lane == 0) {
+            if (dobj) atomicAdd(&objd, (unsigned long long)dobj);
+            if (nappr) atomicAdd(&napp, (unsigned long long)nappr);
+            if (npins) atomicAdd(&mpins, (unsigned long long)npins);
+        }
+        __syncthreads();
+        if (tid < 64 && tid < d0.k) {
+            unsigned long long v = 0;
+            for (int w = 0; w < kWarps; ++w) v += bwd_w[w][tid];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.bw[tid]), v);
+        }
+        if (tid == 0) {
+            unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
+            if (objd) atomicAdd(reinterpret_cast<unsigned long long *>(d0.obj), objd);
+            if (napp) atomicAdd(row + ST_APPR, napp);
+            if (mpins) atomicAdd(row + ST_MOVED, mpins);
+        }
     }
 }
 
-__global__ void k_round_end(Dev d, unsigned long long *st_row)
+// thread per instance: per-round objective and heaviest block; advance the round state
+__global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr)
 {
-    if (threadIdx.x == 0) {
-        long long mx = 0;
-        for (int i = 0; i < d.k; ++i) mx = d.bw[i] > mx ? d.bw[i] : mx;
-        st_row[ST_OBJ] = (unsigned long long)*d.obj;
-        st_row[ST_MAXW] = (unsigned long long)mx;
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const Dev d = devs[i];
+    unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
+    long long mx = 0;
+    for (int t = 0; t < d.k; ++t) mx = d.bw[t] > mx ? d.bw[t] : mx;
+    row[ST_OBJ] = (unsigned long long)*d.obj;
+    row[ST_MAXW] = (unsigned long long)mx;
+    d.rs[0] += 1;
+    d.rs[1] = 1;
 }
 
-__global__ void k_expand_candidates(Dev d, int32_t *target, int64_t *gain)
+__global__ void k_expand_candidates(const Dev *devs, int32_t *target, int64_t *gain)
 {
+    const Dev d = devs[0];
     const int lane = threadIdx.x & 31;
     const int32_t range = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (range >= d.n_ranges) return;
@@ -939,37 +1154,46 @@ __global__ void k_expand_candidates(Dev d, int32_t *target, int64_t *gain)
     }
 }
 
-// ------------------------------------------------------------------ host side
-// Persistent grid: as many CTAs as fit on the device at once, never more than the work.
+// ------------------------------------------------------------------ launch plans (host)
+// A set of instances with one record type, launched together: one instance with its own
+// ranges (items == nullptr), or a batch group with explicit (instance, local index) items.
+struct Plan {
+    Dev d0{};                     // single instance: its state by value (kernel parameter)
+    const Dev *devs = nullptr;
+    const int2 *ranges = nullptr, *tiles = nullptr, *blocks = nullptr;
+    int32_t n_ranges = 0, n_tiles = 0, n_blocks = 0, n_inst = 0;
+    int32_t S_max = 0;
+    bool levels = false;   // some instance can have gains >= kBins - 1
+    bool rec32 = false;
+    int grid_gain = 0, grid_apply = 0;
+    cudaStream_t st = nullptr;
+    int64_t *launches = nullptr;
+    hgp_handle *prof = nullptr;   // per-phase event timing (single-instance launches only)
+};
+
 template <typename K>
-int persistent_grid(hgp_handle *h, K kernel)
+int persistent_grid(int device, K kernel, int32_t n_ranges)
 {
     int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
     (void)cudaGetLastError();
     int64_t g = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (h->d.n_ranges + kWarps - 1) / kWarps;
+    const int64_t need = (n_ranges + kWarps - 1) / kWarps;
     if (g > need) g = need;
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename Rec>
-cudaError_t launch_gain(hgp_handle *h, int32_t r, int32_t s, bool all_elig, unsigned long long *st_row)
+void set_grids(Plan &p, int device)
 {
-    if (!h->grid_gain) h->grid_gain = persistent_grid(h, k_gain<Rec>);
-    k_gain<Rec><<<h->grid_gain, kThreads, 0, h->stream>>>(h->d, r, s, all_elig ? 1 : 0, st_row);
-    h->launches++;
-    return cudaGetLastError();
-}
-
-template <typename Rec>
-cudaError_t launch_apply(hgp_handle *h, int32_t r, unsigned long long *st_row)
-{
-    if (!h->grid_apply) h->grid_apply = persistent_grid(h, k_apply<Rec>);
-    k_apply<Rec><<<h->grid_apply, kThreads, 0, h->stream>>>(h->d, r, st_row);
-    h->launches++;
-    return cudaGetLastError();
+    const bool b = p.ranges != nullptr;
+    if (p.rec32) {
+        p.grid_gain = persistent_grid(device, b ? k_gain<Rec32, true> : k_gain<Rec32, false>, p.n_ranges);
+        p.grid_apply = persistent_grid(device, b ? k_apply<Rec32, true> : k_apply<Rec32, false>, p.n_ranges);
+    } else {
+        p.grid_gain = persistent_grid(device, b ? k_gain<Rec16, true> : k_gain<Rec16, false>, p.n_ranges);
+        p.grid_apply = persistent_grid(device, b ? k_apply<Rec16, true> : k_apply<Rec16, false>, p.n_ranges);
+    }
 }
 
 // Per-phase event timing (profiling mode): a pair of events around each phase instance.
@@ -977,7 +1201,7 @@ enum { PH_PREP = 0, PH_GAIN = 1, PH_APPROVE = 2, PH_APPLY = 3, PH_END = 4 };
 
 cudaError_t phase_begin(hgp_handle *h)
 {
-    if (!h->profiling) return cudaSuccess;
+    if (!h || !h->profiling) return cudaSuccess;
     if (h->events_used + 2 > h->n_events) {
         // grow the pool (existing events stay valid; pending pairs are kept)
         const int32_t cap = h->n_events ? h->n_events * 2 : 256;
@@ -1007,7 +1231,7 @@ cudaError_t phase_begin(hgp_handle *h)
 
 cudaError_t phase_end(hgp_handle *h, int phase, int32_t launches)
 {
-    if (!h->profiling) return cudaSuccess;
+    if (!h || !h->profiling) return cudaSuccess;
     cudaError_t e = cudaEventRecord(h->events[h->events_used + 1], h->stream);
     h->event_phase[h->events_used / 2] = phase;
     h->event_count[h->events_used / 2] = launches;
@@ -1029,38 +1253,121 @@ cudaError_t collect_profile(hgp_handle *h)
     return e;
 }
 
-cudaError_t launch_subround(hgp_handle *h, int32_t r, int32_t s, bool all_elig, unsigned long long *st_row)
+unsigned warp_grid(int32_t n_items) { return (unsigned)((n_items + kWarps - 1) / kWarps); }
+
+cudaError_t launch_gain(const Plan &p, int32_t s, int32_t rr)
 {
-    Dev &d = h->d;
-    cudaStream_t st = h->stream;
-    cudaError_t e = phase_begin(h);
-    if (e == cudaSuccess)
-        e = d.k <= 32 ? launch_gain<Rec16>(h, r, s, all_elig, st_row) : launch_gain<Rec32>(h, r, s, all_elig, st_row);
-    if (e == cudaSuccess) e = phase_end(h, PH_GAIN, 1);
-    if (e != cudaSuccess) return e;
-    e = phase_begin(h);
-    if (e != cudaSuccess) return e;
-    int32_t n = 0;
-    k_hist<<<d.n_tiles, kThreads, 0, st>>>(d, 0);
-    k_select<<<d.k, kThreads, 0, st>>>(d, 0);
-    n += 2;
-    if (h->max_vertex_netweight >= kBins - 1) {
-        for (int level = 1; level <= 3; ++level) {
-            k_hist<<<d.n_tiles, kThreads, 0, st>>>(d, level);
-            k_select<<<d.k, kThreads, 0, st>>>(d, level);
-            n += 2;
+    const bool b = p.ranges != nullptr;
+    if (p.rec32 && b) k_gain<Rec32, true><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, rr);
+    else if (p.rec32) k_gain<Rec32, false><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, rr);
+    else if (b) k_gain<Rec16, true><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, rr);
+    else k_gain<Rec16, false><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, rr);
+    *p.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const Plan &p)
+{
+    k_round_prep<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges);
+    *p.launches += 1;
+    return cudaGetLastError();
+}
+
+// one round: sub-round lists, then per sub-round gain -> approval -> apply, then round end
+cudaError_t launch_round(const Plan &p, int32_t rr)
+{
+    cudaError_t e = phase_begin(p.prof);
+    if (e == cudaSuccess) e = launch_prep(p);
+    if (e == cudaSuccess) e = phase_end(p.prof, PH_PREP, 1);
+    for (int32_t s = 0; s < p.S_max && e == cudaSuccess; ++s) {
+        e = phase_begin(p.prof);
+        if (e == cudaSuccess) e = launch_gain(p, s, rr);
+        if (e == cudaSuccess) e = phase_end(p.prof, PH_GAIN, 1);
+        if (e == cudaSuccess) e = phase_begin(p.prof);
+        if (e != cudaSuccess) break;
+        int32_t n = 0;
+        k_hist<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, 0);
+        k_select<<<p.n_blocks, kThreads, 0, p.st>>>(p.devs, p.blocks, p.n_blocks, 0);
+        n += 2;
+        if (p.levels) {
+            for (int level = 1; level <= 3; ++level) {
+                k_hist<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, level);
+                k_select<<<p.n_blocks, kThreads, 0, p.st>>>(p.devs, p.blocks, p.n_blocks, level);
+                n += 2;
+            }
         }
+        k_tie_sum<<<p.n_tiles, kThreads, 0, p.st>>>(p.devs, p.tiles, p.n_tiles);
+        k_tie_scan<<<p.n_blocks, 1024, 0, p.st>>>(p.devs, p.blocks, p.n_blocks);
+        n += 2;
+        *p.launches += n;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPROVE, n);
+        if (e == cudaSuccess) e = phase_begin(p.prof);
+        if (e != cudaSuccess) break;
+        const bool b = p.ranges != nullptr;
+        if (p.rec32 && b) k_apply<Rec32, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
+        else if (p.rec32) k_apply<Rec32, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
+        else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
+        else k_apply<Rec16, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
+        *p.launches += 1;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, 1);
     }
-    k_tie_sum<<<d.n_tiles, kThreads, 0, st>>>(d);
-    k_tie_scan<<<d.k, 1024, 0, st>>>(d);
-    n += 2;
-    h->launches += n;
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = phase_end(h, PH_APPROVE, n);
-    if (e == cudaSuccess) e = phase_begin(h);
-    if (e != cudaSuccess) return e;
-    e = d.k <= 32 ? launch_apply<Rec16>(h, r, st_row) : launch_apply<Rec32>(h, r, st_row);
-    if (e == cudaSuccess) e = phase_end(h, PH_APPLY, 1);
+    if (e == cudaSuccess) e = phase_begin(p.prof);
+    if (e == cudaSuccess) {
+        k_round_end<<<(p.n_inst + 127) / 128, 128, 0, p.st>>>(p.devs, p.n_inst, rr);
+        *p.launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = phase_end(p.prof, PH_END, 1);
+    return e;
+}
+
+// the handle's instance state as a device-resident Dev (re-uploaded when it changed)
+cudaError_t sync_dev(hgp_handle *h)
+{
+    if (!h->d_dev) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&h->d_dev), sizeof(Dev));
+        if (e != cudaSuccess) return e;
+        h->dev_dirty = true;
+    }
+    if (!h->dev_dirty) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(h->d_dev, &h->d, sizeof(Dev), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) h->dev_dirty = false;
+    return e;
+}
+
+Plan single_plan(hgp_handle *h)
+{
+    Plan p;
+    p.d0 = h->d;
+    p.devs = h->d_dev;
+    p.n_ranges = h->d.n_ranges;
+    p.n_tiles = h->d.n_tiles;
+    p.n_blocks = h->d.k;
+    p.n_inst = 1;
+    p.S_max = h->d.S;
+    p.levels = h->max_vertex_netweight >= kBins - 1;
+    p.rec32 = h->d.k > 32;
+    if (!h->grid_gain) {
+        Plan q = p;
+        set_grids(q, h->device);
+        h->grid_gain = q.grid_gain;
+        h->grid_apply = q.grid_apply;
+    }
+    p.grid_gain = h->grid_gain;
+    p.grid_apply = h->grid_apply;
+    p.st = h->stream;
+    p.launches = &h->launches;
+    p.prof = h->profiling ? h : nullptr;
+    return p;
+}
+
+cudaError_t enqueue_rounds(const Plan &p, int64_t *stats, int32_t rounds)
+{
+    cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * ST_N * (size_t)rounds, p.st);
+    for (int32_t rr = 0; rr < rounds && e == cudaSuccess; ++rr) e = launch_round(p, rr);
     return e;
 }
 
@@ -1087,6 +1394,35 @@ int ensure_stats(hgp_handle *h, int32_t rounds)
     h->d.stats = dev;
     h->h_stats = host;
     h->stats_cap = cap;
+    h->dev_dirty = true;
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_rounds = 0;
+    }
+    return HGP_OK;
+}
+
+static int copy_stats_out(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
+{
+    cudaError_t e = cudaMemcpyAsync(h->h_stats, h->d.stats, sizeof(int64_t) * ST_N * (size_t)rounds,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    if (stats) {
+        for (int32_t rr = 0; rr < rounds; ++rr) {
+            const int64_t *row = h->h_stats + (int64_t)rr * ST_N;
+            stats[rr].objective = row[ST_OBJ];
+            stats[rr].candidates = row[ST_CAND];
+            stats[rr].approved = row[ST_APPR];
+            stats[rr].eligible = row[ST_ELIG];
+            stats[rr].max_block_weight = row[ST_MAXW];
+            stats[rr].moved_pins = row[ST_MOVED];
+        }
+    }
     return HGP_OK;
 }
 
@@ -1096,29 +1432,43 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
     if (h->next_round + rounds >= ((int64_t)1 << 30)) return HGP_ERR_UNSUPPORTED;
     int rc = ensure_stats(h, rounds);
     if (rc != HGP_OK) return rc;
-    Dev &d = h->d;
-    cudaStream_t st = h->stream;
-    cudaError_t e = cudaMemsetAsync(d.stats, 0, sizeof(int64_t) * ST_N * (size_t)rounds, st);
-    for (int32_t rr = 0; rr < rounds && e == cudaSuccess; ++rr) {
-        const int32_t r = (int32_t)(h->next_round + rr);
-        unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
-        e = phase_begin(h);
-        if (e != cudaSuccess) break;
-        k_round_prep<<<d.n_tiles, kThreads, 0, st>>>(d, r, h->seed);
-        h->launches++;
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = phase_end(h, PH_PREP, 1);
-        for (int32_t s = 0; s < d.S && e == cudaSuccess; ++s)
-            e = launch_subround(h, r, s, h->all_eligible && rr == 0, row);
-        if (e == cudaSuccess) e = phase_begin(h);
-        if (e == cudaSuccess) {
-            k_round_end<<<1, 32, 0, st>>>(d, row);
-            h->launches++;
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = phase_end(h, PH_END, 1);
+    cudaError_t e = sync_dev(h);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
     }
-    if (e == cudaSuccess) e = collect_profile(h);
+    Plan p = single_plan(h);
+    const bool use_graph = h->graph && !h->profiling;
+    if (use_graph) {
+        if (!h->graph_exec || h->graph_rounds != rounds) {
+            if (h->graph_exec) {
+                cudaGraphExecDestroy(h->graph_exec);
+                h->graph_exec = nullptr;
+            }
+            // the captured launches are counted at replay, not at capture
+            int64_t scratch = 0;
+            Plan q = p;
+            q.launches = &scratch;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e2 = enqueue_rounds(q, h->d.stats, rounds);
+                e = cudaStreamEndCapture(h->stream, &graph);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e == cudaSuccess) {
+                h->graph_rounds = rounds;
+                h->graph_launches = scratch;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(h->graph_exec, h->stream);
+        if (e == cudaSuccess) h->launches += h->graph_launches;
+    } else {
+        e = enqueue_rounds(p, h->d.stats, rounds);
+        if (e == cudaSuccess) e = collect_profile(h);
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -1126,33 +1476,18 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
     h->next_round += rounds;
     h->all_eligible = false;
     if (stats || (h->debug & 1)) {
-        e = cudaMemcpyAsync(h->h_stats, d.stats, sizeof(int64_t) * ST_N * (size_t)rounds, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return status_of(e);
-        }
-        if (stats) {
-            for (int32_t rr = 0; rr < rounds; ++rr) {
-                const int64_t *row = h->h_stats + (int64_t)rr * ST_N;
-                stats[rr].objective = row[ST_OBJ];
-                stats[rr].candidates = row[ST_CAND];
-                stats[rr].approved = row[ST_APPR];
-                stats[rr].eligible = row[ST_ELIG];
-                stats[rr].max_block_weight = row[ST_MAXW];
-                stats[rr].moved_pins = row[ST_MOVED];
-            }
-        }
+        rc = copy_stats_out(h, rounds, stats);
+        if (rc != HGP_OK) return rc;
     }
     if (h->debug & 1) {
         int64_t *tmp = nullptr;
         int64_t from_phi = 0, maintained = 0;
-        e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int64_t), st);
+        e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int64_t), h->stream);
         if (e == cudaSuccess) e = objective_from_phi(h, tmp);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&from_phi, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&maintained, d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (tmp) cudaFreeAsync(tmp, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&from_phi, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&maintained, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+        if (tmp) cudaFreeAsync(tmp, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
@@ -1166,25 +1501,24 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 {
     Dev &d = h->d;
     cudaStream_t st = h->stream;
-    const int32_t r = (int32_t)h->next_round;
+    cudaError_t e = sync_dev(h);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    Plan p = single_plan(h);
     int32_t *t_d = nullptr;
     int64_t *g_d = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&t_d), sizeof(int32_t) * (size_t)d.n, st);
+    e = cudaMallocAsync(reinterpret_cast<void **>(&t_d), sizeof(int32_t) * (size_t)d.n, st);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&g_d), sizeof(int64_t) * (size_t)d.n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(t_d, 0xFF, sizeof(int32_t) * (size_t)d.n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g_d, 0, sizeof(int64_t) * (size_t)d.n, st);
-    if (e == cudaSuccess) {
-        k_round_prep<<<d.n_tiles, kThreads, 0, st>>>(d, r, h->seed);
-        h->launches++;
-        e = cudaGetLastError();
-    }
     // the stats row written here is scratch: refine() clears the stats before use
-    unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats);
-    if (e == cudaSuccess)
-        e = d.k <= 32 ? launch_gain<Rec16>(h, r, s, h->all_eligible, row) : launch_gain<Rec32>(h, r, s, h->all_eligible, row);
+    if (e == cudaSuccess) e = launch_prep(p);
+    if (e == cudaSuccess) e = launch_gain(p, s, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tot, 0, sizeof(int64_t) * 64, st);
     if (e == cudaSuccess) {
-        k_expand_candidates<<<(d.n_ranges * 32 + 255) / 256, 256, 0, st>>>(d, t_d, g_d);
+        k_expand_candidates<<<(d.n_ranges * 32 + 255) / 256, 256, 0, st>>>(h->d_dev, t_d, g_d);
         h->launches++;
         e = cudaGetLastError();
     }
@@ -1202,7 +1536,300 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 
 }  // namespace hgp
 
+// ================================================================== batch of handles
+struct hgp_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int32_t use_graph = 1;
+    int32_t gain_ctas = 0, apply_ctas = 0;     // per-SM CTA overrides (0 = occupancy)
+    std::vector<hgp_handle *> hs;
+    struct Group {
+        Plan plan;
+        std::vector<int32_t> members;           // indices into hs
+        Dev *d_devs = nullptr;
+        int2 *d_items = nullptr;                // ranges, then tiles, then blocks
+    } g[2];
+    int64_t *d_stats = nullptr;
+    int64_t *h_stats = nullptr;
+    int32_t stats_cap = 0;
+    cudaGraphExec_t exec = nullptr;
+    int32_t graph_rounds = 0;
+    int64_t graph_launches = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void free_groups(hgp_batch *b)
+{
+    for (auto &gr : b->g) {
+        if (gr.d_devs) cudaFree(gr.d_devs);
+        if (gr.d_items) cudaFree(gr.d_items);
+        gr.d_devs = nullptr;
+        gr.d_items = nullptr;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_rounds = 0;
+}
+
+int grid_override(int device, int ctas_per_sm, int fallback, int32_t n_ranges)
+{
+    if (ctas_per_sm <= 0) return fallback;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int64_t g = (int64_t)sms * ctas_per_sm;
+    const int64_t need = (n_ranges + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// (re)builds the per-group device arrays for a stats capacity of `cap` rounds
+int build_groups(hgp_batch *b, int32_t cap)
+{
+    free_groups(b);
+    const int32_t count = (int32_t)b->hs.size();
+    if (b->d_stats) cudaFree(b->d_stats);
+    if (b->h_stats) cudaFreeHost(b->h_stats);
+    b->d_stats = nullptr;
+    b->h_stats = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_stats), sizeof(int64_t) * ST_N * (size_t)cap * count);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&b->h_stats), sizeof(int64_t) * ST_N * (size_t)cap * count);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    b->stats_cap = cap;
+    for (int gi = 0; gi < 2; ++gi) {
+        auto &gr = b->g[gi];
+        gr.members.clear();
+        for (int32_t i = 0; i < count; ++i)
+            if ((b->hs[i]->d.k > 32) == (gi == 1)) gr.members.push_back(i);
+        gr.plan = Plan();
+        if (gr.members.empty()) continue;
+        std::vector<Dev> devs;
+        std::vector<int2> ranges, tiles, blocks;
+        int32_t S_max = 0;
+        bool levels = false;
+        for (size_t j = 0; j < gr.members.size(); ++j) {
+            const hgp_handle *h = b->hs[gr.members[j]];
+            Dev d = h->d;
+            d.stats = b->d_stats + (int64_t)gr.members[j] * cap * ST_N;
+            devs.push_back(d);
+            for (int32_t r = 0; r < d.n_ranges; ++r) ranges.push_back(make_int2((int)j, r));
+            for (int32_t t = 0; t < d.n_tiles; ++t) tiles.push_back(make_int2((int)j, t));
+            for (int32_t t = 0; t < d.k; ++t) blocks.push_back(make_int2((int)j, t));
+            S_max = d.S > S_max ? d.S : S_max;
+            levels = levels || h->max_vertex_netweight >= kBins - 1;
+        }
+        const size_t n_items = ranges.size() + tiles.size() + blocks.size();
+        e = cudaMalloc(reinterpret_cast<void **>(&gr.d_devs), sizeof(Dev) * devs.size());
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&gr.d_items), sizeof(int2) * n_items);
+        std::vector<int2> all;
+        all.reserve(n_items);
+        all.insert(all.end(), ranges.begin(), ranges.end());
+        all.insert(all.end(), tiles.begin(), tiles.end());
+        all.insert(all.end(), blocks.begin(), blocks.end());
+        if (e == cudaSuccess) e = cudaMemcpy(gr.d_devs, devs.data(), sizeof(Dev) * devs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(gr.d_items, all.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return status_of(e);
+        }
+        Plan &p = gr.plan;
+        p.devs = gr.d_devs;
+        p.ranges = gr.d_items;
+        p.tiles = gr.d_items + ranges.size();
+        p.blocks = gr.d_items + ranges.size() + tiles.size();
+        p.n_ranges = (int32_t)ranges.size();
+        p.n_tiles = (int32_t)tiles.size();
+        p.n_blocks = (int32_t)blocks.size();
+        p.n_inst = (int32_t)devs.size();
+        p.S_max = S_max;
+        p.levels = levels;
+        p.rec32 = gi == 1;
+        set_grids(p, b->device);
+        p.grid_gain = grid_override(b->device, b->gain_ctas, p.grid_gain, p.n_ranges);
+        p.grid_apply = grid_override(b->device, b->apply_ctas, p.grid_apply, p.n_ranges);
+        p.st = b->stream;
+        p.launches = &b->launches;
+    }
+    return HGP_OK;
+}
+
+cudaError_t enqueue_batch(hgp_batch *b, int32_t rounds, int64_t *launch_counter)
+{
+    const int32_t count = (int32_t)b->hs.size();
+    cudaError_t e = cudaMemsetAsync(b->d_stats, 0, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count, b->stream);
+    for (int32_t rr = 0; rr < rounds && e == cudaSuccess; ++rr)
+        for (auto &gr : b->g) {
+            if (gr.members.empty() || e != cudaSuccess) continue;
+            Plan p = gr.plan;
+            p.launches = launch_counter;
+            e = launch_round(p, rr);
+        }
+    return e;
+}
+
+}  // namespace
+
 extern "C" {
+
+void hgp_batch_default_options(hgp_batch_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->graph = 1;
+}
+
+int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_options *opt, hgp_batch **out)
+{
+    if (!out) return HGP_ERR_INVALID;
+    *out = nullptr;
+    if (!handles || count < 1) return HGP_ERR_INVALID;
+    hgp_batch_options o;
+    hgp_batch_default_options(&o);
+    if (opt) o = *opt;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int32_t i = 0; i < count; ++i) {
+        if (!handles[i] || handles[i]->device != dev) return HGP_ERR_INVALID;
+        for (int32_t j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return HGP_ERR_INVALID;
+    }
+    hgp_batch *b = new (std::nothrow) hgp_batch();
+    if (!b) return HGP_ERR_OOM;
+    b->device = dev;
+    b->use_graph = o.graph;
+    b->gain_ctas = o.gain_ctas_per_sm;
+    b->apply_ctas = o.apply_ctas_per_sm;
+    b->hs.assign(handles, handles + count);
+    if (o.cuda_stream) {
+        b->stream = (cudaStream_t)o.cuda_stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete b;
+        return HGP_ERR_CUDA;
+    } else {
+        b->own_stream = true;
+    }
+    for (hgp_handle *h : b->hs) cudaStreamSynchronize(h->stream);
+    const int rc = build_groups(b, 8);
+    if (rc != HGP_OK) {
+        hgp_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return HGP_OK;
+}
+
+int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
+{
+    if (!b || rounds < 0) return HGP_ERR_INVALID;
+    if (rounds == 0) return HGP_OK;
+    for (hgp_handle *h : b->hs) {
+        if (h->next_round + rounds >= ((int64_t)1 << 30)) return HGP_ERR_UNSUPPORTED;
+        // the batch reads the handles' state from its own stream
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return HGP_ERR_CUDA;
+        }
+    }
+    if (rounds > b->stats_cap) {
+        int32_t cap = b->stats_cap;
+        while (cap < rounds) cap *= 2;
+        const int rc = build_groups(b, cap);
+        if (rc != HGP_OK) return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (b->use_graph) {
+        if (!b->exec || b->graph_rounds != rounds) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            int64_t scratch = 0;
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e2 = enqueue_batch(b, rounds, &scratch);
+                e = cudaStreamEndCapture(b->stream, &graph);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e == cudaSuccess) {
+                b->graph_rounds = rounds;
+                b->graph_launches = scratch;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) b->launches += b->graph_launches;
+    } else {
+        e = enqueue_batch(b, rounds, &b->launches);
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    for (hgp_handle *h : b->hs) {
+        h->next_round += rounds;
+        h->all_eligible = false;
+    }
+    const int32_t count = (int32_t)b->hs.size();
+    if (stats) {
+        e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
+                            cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return status_of(e);
+        }
+        for (int32_t i = 0; i < count; ++i)
+            for (int32_t rr = 0; rr < rounds; ++rr) {
+                const int64_t *row = b->h_stats + ((int64_t)i * b->stats_cap + rr) * ST_N;
+                hgp_round_stats &o = stats[(int64_t)i * rounds + rr];
+                o.objective = row[ST_OBJ];
+                o.candidates = row[ST_CAND];
+                o.approved = row[ST_APPR];
+                o.eligible = row[ST_ELIG];
+                o.max_block_weight = row[ST_MAXW];
+                o.moved_pins = row[ST_MOVED];
+            }
+    }
+    return HGP_OK;
+}
+
+int hgp_batch_synchronize(hgp_batch *b)
+{
+    if (!b) return HGP_ERR_INVALID;
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return HGP_OK;
+}
+
+int hgp_batch_get_launch_count(hgp_batch *b, int64_t *out)
+{
+    if (!b || !out) return HGP_ERR_INVALID;
+    *out = b->launches;
+    return HGP_OK;
+}
+
+void hgp_batch_destroy(hgp_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_groups(b);
+    if (b->d_stats) cudaFree(b->d_stats);
+    if (b->h_stats) cudaFreeHost(b->h_stats);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    (void)cudaGetLastError();
+    delete b;
+}
 
 int hgp_set_profiling(hgp_handle *h, int32_t enable)
 {

@@ -388,6 +388,8 @@ int init_state(hgp_handle *h)
     cudaStream_t st = h->stream;
     CK(cudaMemsetAsync(d.bw, 0, sizeof(int64_t) * d.k, st));
     CK(cudaMemsetAsync(d.obj, 0, sizeof(int64_t), st));
+    // round 0, every vertex eligible
+    CK(cudaMemsetAsync(d.rs, 0, 2 * sizeof(int32_t), st));
     k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
     CK(cudaGetLastError());
     const int g = grid_for((int64_t)d.m * 32, kThreads, 152 * 16);
@@ -627,6 +629,8 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.sel = sel;
     d.tie = tie;
     CKF(dalloc(h, &h->d_round, 4));
+    d.rs = h->d_round;
+    d.seed = o.seed;
 
     rc = init_state(h);
     if (rc != HGP_OK) return fail(rc);
@@ -708,6 +712,7 @@ void hgp_destroy(hgp_handle *h)
     delete[] h->event_phase;
     delete[] h->event_count;
     if (h->d.stats) cudaFree(h->d.stats);
+    if (h->d_dev) cudaFree(h->d_dev);
     if (h->h_stats) cudaFreeHost(h->h_stats);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     (void)cudaGetLastError();

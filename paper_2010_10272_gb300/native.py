@@ -37,6 +37,12 @@ class Options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p)]
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("gain_ctas_per_sm", ctypes.c_int32),
+                ("apply_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
 class RoundStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in STAT_FIELDS]
 
@@ -89,6 +95,17 @@ def load_library():
         lib.hgp_candidates_noalloc.argtypes = [i32, i32, P, P, P, P, P, P, i32, f64, P, i32,
                                                ctypes.c_uint64, i32, P, P, P]
         lib.hgp_candidates_noalloc.restype = ctypes.c_int
+        lib.hgp_batch_default_options.argtypes = [P]
+        lib.hgp_batch_default_options.restype = None
+        lib.hgp_batch_create.argtypes = [P, i32, P, P]
+        lib.hgp_batch_refine.argtypes = [P, i32, P]
+        lib.hgp_batch_synchronize.argtypes = [P]
+        lib.hgp_batch_get_launch_count.argtypes = [P, P]
+        for name in ("hgp_batch_create", "hgp_batch_refine", "hgp_batch_synchronize",
+                     "hgp_batch_get_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.hgp_batch_destroy.argtypes = [P]
+        lib.hgp_batch_destroy.restype = None
         lib.hgp_destroy.argtypes = [P]
         lib.hgp_destroy.restype = None
         _lib = lib
@@ -280,3 +297,53 @@ def candidates_noalloc(n, m, net_off, pins, vtx_off, inc, k, eps, part, target, 
         int(n), int(m), _dptr(net_off), _dptr(pins), _dptr(vtx_off), _dptr(inc), _dptr(vertex_w),
         _dptr(net_w), int(k), float(eps), _dptr(part), int(subrounds), int(seed), int(s),
         _dptr(target), _dptr(gain), ctypes.c_void_p(sh) if sh else None))
+
+
+class Batch:
+    """hgp_batch over existing HGP handles (which must stay alive while the batch is used)."""
+
+    def __init__(self, handles, graph: bool = True, gain_ctas_per_sm: int = 0,
+                 apply_ctas_per_sm: int = 0, stream=None):
+        self._lib = load_library()
+        self.handles = list(handles)
+        o = BatchOptions()
+        self._lib.hgp_batch_default_options(ctypes.byref(o))
+        o.graph = 1 if graph else 0
+        o.gain_ctas_per_sm, o.apply_ctas_per_sm = int(gain_ctas_per_sm), int(apply_ctas_per_sm)
+        sh = _stream_handle(stream)
+        o.cuda_stream = ctypes.c_void_p(sh) if sh else None
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        self._b = ctypes.c_void_p()
+        _check(self._lib.hgp_batch_create(arr, len(self.handles), ctypes.byref(o),
+                                          ctypes.byref(self._b)), "hgp_batch_create")
+
+    def refine(self, rounds: int, stats: bool = True):
+        """Runs `rounds` rounds on every member; returns int64 [count x rounds x 6] or None."""
+        n = len(self.handles)
+        if stats:
+            buf = (RoundStats * max(1, n * rounds))()
+            _check(self._lib.hgp_batch_refine(self._b, int(rounds), buf), "hgp_batch_refine")
+            out = np.array([[getattr(buf[i], f) for f in STAT_FIELDS] for i in range(n * rounds)],
+                           dtype=np.int64)
+            return out.reshape(n, rounds, len(STAT_FIELDS))
+        _check(self._lib.hgp_batch_refine(self._b, int(rounds), None), "hgp_batch_refine")
+        return None
+
+    def synchronize(self):
+        _check(self._lib.hgp_batch_synchronize(self._b), "hgp_batch_synchronize")
+
+    def launch_count(self) -> int:
+        out = ctypes.c_int64()
+        _check(self._lib.hgp_batch_get_launch_count(self._b, ctypes.byref(out)), "hgp_batch_get_launch_count")
+        return out.value
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._lib.hgp_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

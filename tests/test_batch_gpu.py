@@ -1,0 +1,71 @@
+"""Batched refinement: one launch per phase over many handles, replayed as a CUDA graph.
+
+Each member refined inside a batch must give exactly the result of refining it alone (and the
+oracle's), for uneven sizes, mixed k (both record layouts), mixed Phi widths, weights and
+sub-round counts, over several calls (graph capture, then replay with continuing rounds).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_10272_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _members():
+    out = []
+    specs = [(2, 3000, False, 4, 0), (4, 9000, True, 4, 0), (8, 20000, True, 3, 1), (16, 7000, True, 4, 2),
+             (33, 5000, False, 2, 0), (64, 12000, True, 4, 0), (5, 2049, False, 1, 4), (64, 1500, True, 7, 1)]
+    for i, (k, n, w, S, pw) in enumerate(specs):
+        hg = synth.random_small(4000 + i, n, int(n * 0.9), k, max_size=9, weighted=w, rounds=5)
+        out.append((hg, S, pw))
+    for hg in synth.config_batch(count=6, n_hi=30_000):
+        out.append((hg, 4, 0))
+    return out
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_equals_alone_and_oracle(graph):
+    from paper_2010_10272_gb300 import HGP, Batch
+    members = _members()
+    hs = [HGP.from_hypergraph(hg, subrounds=S, phi_width=pw, seed=3) for hg, S, pw in members]
+    b = Batch(hs, graph=graph)
+    got = [b.refine(2), b.refine(3), b.refine(3)]        # capture, new capture (rounds differ), replay
+    got = np.concatenate(got, axis=1)
+    for i, (hg, S, pw) in enumerate(members):
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=3)
+        want, _ = o.refine(8)
+        np.testing.assert_array_equal(got[i, :, :5], want)
+        np.testing.assert_array_equal(hs[i].partition(), o.partition())
+        np.testing.assert_array_equal(hs[i].block_weights(), o.block_weights())
+        assert hs[i].objective() == o.objective() == hs[i].objective_from_phi()
+        assert hs[i].info()["next_round"] == 8
+        # a handle refined alone after the batch continues the same sequence
+        alone = hs[i].refine(1)[:, :5]
+        np.testing.assert_array_equal(alone, o.refine(1)[0])
+    assert b.launch_count() > 0
+    b.close()
+
+
+def test_single_handle_graph_mode_replay():
+    from paper_2010_10272_gb300 import HGP
+    hg = synth.random_small(77, 30000, 28000, 64, max_size=10, weighted=True, rounds=6)
+    h = HGP.from_hypergraph(hg, subrounds=4, graph=1)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    for r in (2, 2, 2, 1):                 # capture, replay, replay, re-capture
+        np.testing.assert_array_equal(h.refine(r)[:, :5], o.refine(r)[0])
+    np.testing.assert_array_equal(h.partition(), o.partition())
+    h.set_partition(hg.part)              # reset also restarts the device round state
+    o2 = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    np.testing.assert_array_equal(h.refine(2)[:, :5], o2.refine(2)[0])
