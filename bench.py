@@ -251,6 +251,8 @@ def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
+    if args.workload == "batch":
+        args.workload = "small"
     value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -284,7 +286,10 @@ def run_gpu(args, world, rank, local):
     to_dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     d_off, d_pins, d_part = to_dev(hg.net_off), to_dev(hg.pins), to_dev(hg.part)
     d_vw, d_nw = to_dev(hg.vertex_w), to_dev(hg.net_w)
-    stream = torch.cuda.current_stream(dev)
+    # one explicit stream for the library and the timing events (a NULL stream handle would
+    # make the library create its own stream)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     h = HGP(hg.n, hg.m, d_off, d_pins, hg.k, hg.eps, d_part, d_vw, d_nw, subrounds=S, device=True,
             stream=stream)
     info = h.info()
@@ -398,13 +403,98 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------------------------------ batch workload
+def run_batch(args, world, rank, local):
+    """256 planted instances of uneven size refined together (one launch per phase, replayed as
+    a CUDA graph) against the same 256 instances refined one after another with plain
+    per-instance launches on the same stream.  value = the batched throughput."""
+    import torch
+    from paper_2010_10272_gb300 import HGP, Batch, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    insts = synth.config_batch(count=args.batch_count)
+    t_gen = time.perf_counter() - t0
+    R, S = insts[0].rounds, args.subrounds
+    P = sum(h.num_pins for h in insts)
+    to_dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    parts = [to_dev(h.part) for h in insts]
+    hs = [HGP(h.n, h.m, to_dev(h.net_off), to_dev(h.pins), h.k, h.eps, parts[i], to_dev(h.vertex_w),
+              to_dev(h.net_w), subrounds=S, device=True, stream=stream) for i, h in enumerate(insts)]
+    batch = Batch(hs, graph=True, stream=stream)
+
+    def reset():
+        for h, p in zip(hs, parts):
+            h.set_partition(p, device=True)
+        torch.cuda.synchronize()
+
+    def plain_step():
+        for h in hs:
+            h.refine(R, stats=False)
+
+    def batch_step():
+        batch.refine(R, stats=False)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            reset()
+            fn()
+            torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            reset()
+            barrier(world)
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return ms
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = batch.launch_count()
+    ms_b = timed(batch_step, args.steps, args.warmup)
+    launches = (batch.launch_count() - l0) // (args.steps + args.warmup) * args.steps
+    clocks = sampler.stop()
+    ms_p = timed(plain_step, max(2, args.steps // 2), 1)
+    total_b = max_over_ranks(sum(ms_b), world)
+    value = world * len(ms_b) * P * R / (total_b / 1e3)
+    plain = world * len(ms_p) * P * R / (max_over_ranks(sum(ms_p), world) / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_b / len(ms_b), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(insts)} planted hypergraphs, n log-uniform 1e3-2e5, "
+                               "|e|=min(2+Zipf(2.5),1000), k in {2,4,8,16}, c(v) in U{1..4}",
+                   "instances": len(insts), "pins": P, "rounds": R, "subrounds": S,
+                   "parallelism": f"replicas x{world}",
+                   "step": f"reset all partitions (untimed) + {R} rounds of every instance",
+                   "l2": "inputs larger than L2"},
+        "batched_vs_plain": {"batched_pins_per_s": value, "plain_pins_per_s": plain,
+                             "ratio": value / plain, "plain_ms_per_step": statistics.mean(ms_p),
+                             "batched_ms_per_step": statistics.mean(ms_b)},
+        "gpu_launches": launches, "clocks": clocks, "setup_s": {"generate": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="powerlaw")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch"], default="powerlaw")
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--subrounds", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -416,6 +506,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
+    elif args.workload == "batch":
+        rc = run_batch(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:
