@@ -251,7 +251,7 @@ def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    if args.workload == "batch":
+    if args.workload in ("batch", "serving"):
         args.workload = "small"
     value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup)
     line = {
@@ -487,13 +487,91 @@ def run_batch(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------------------------------ serving workload
+def run_serving(args, world, rank, local):
+    """Poisson arrivals of refinement requests (planted, pins log-uniform 1e4-5e6, k in
+    {2..32}, 3 rounds) served with continuous batching.  First a saturated run (every request
+    queued at t=0) measures the service capacity mu; then arrivals at 0.5 mu and 0.8 mu give
+    p50/p99 latency (arrival -> partition on the host).  value = saturated pin-rounds/s."""
+    import torch
+    from paper_2010_10272_gb300 import build
+    from paper_2010_10272_gb300.serve import Request, Server, latency_summary
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(torch.device("cuda", local))
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    pool = [synth.serving_request(np.random.SeedSequence(10_000 + i)) for i in range(args.serve_pool)]
+    t_gen = time.perf_counter() - t0
+
+    def make(count, base):
+        return [Request.from_hypergraph(base + i, pool[i % len(pool)]) for i in range(count)]
+
+    def run(reqs, arrivals):
+        srv = Server(stream=stream)
+        order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
+        t_start = time.perf_counter()
+        nxt, done = 0, []
+        while nxt < len(order) or not srv.idle():
+            now = time.perf_counter() - t_start
+            while nxt < len(order) and arrivals[order[nxt]] <= now:
+                srv.submit(reqs[order[nxt]], arrival=t_start + arrivals[order[nxt]])
+                nxt += 1
+            if srv.idle():
+                time.sleep(max(0.0, min(0.001, arrivals[order[nxt]] - now)))
+                continue
+            done.extend(srv.step())
+        t_total = time.perf_counter() - t_start
+        srv.close()
+        return done, t_total
+
+    # warm-up (not reported)
+    run(make(min(len(pool), 16), 0), [0.0] * min(len(pool), 16))
+    sampler = ClockSampler(local)
+    sampler.start()
+    sat_reqs = make(args.serve_requests, 100_000)
+    done, t_sat = run(sat_reqs, [0.0] * len(sat_reqs))
+    clocks = sampler.stop()
+    work = sum(r.num_pins * r.rounds for r in done)
+    mu = len(done) / t_sat
+    rng = np.random.default_rng(args.serve_seed)
+    rates = {}
+    for frac in (0.5, 0.8):
+        lam = frac * mu
+        reqs = make(args.serve_requests, int(1e6 * frac))
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs))).tolist()
+        d2, t2 = run(reqs, arr)
+        rates[f"{frac:g}mu"] = dict(latency_summary(d2), arrival_rate_per_s=lam,
+                                    pin_rounds_per_s=sum(r.num_pins * r.rounds for r in d2) / t2)
+    value = work / t_sat
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(done),
+        "warmup": 16, "ms_per_step": t_sat * 1e3 / len(done), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals of planted hypergraphs, pins log-uniform "
+                               "1e4-5e6, |e|=2+Poisson(4), k in {2,4,8,16,32}, 3 rounds each",
+                   "requests": len(done), "distinct_instances": len(pool),
+                   "step": "one request, arrival to partition on the host",
+                   "l2": "request state resident in HBM; saturated run", "parallelism": "replicas x1"},
+        "serving": {"service_capacity_req_per_s": mu, "saturated_pin_rounds_per_s": value,
+                    "saturated_latency": latency_summary(done), "poisson": rates},
+        "clocks": clocks, "setup_s": {"generate": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch"], default="powerlaw")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving"], default="powerlaw")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--serve-seed", type=int, default=1)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--subrounds", type=int, default=4)
@@ -508,6 +586,8 @@ def main():
         rc = run_reference(args, world, rank)
     elif args.workload == "batch":
         rc = run_batch(args, world, rank, local)
+    elif args.workload == "serving":
+        rc = run_serving(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

@@ -1,0 +1,79 @@
+"""Serving loop: each request's result is the same alone and in the mix (tolerance 0: the
+arithmetic is integer), with requests arriving while others are on the GPU, admission by a
+memory budget that forces queueing, and uneven sizes / k / round counts."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_10272_gb300 import build
+    build.build()
+
+
+def _requests():
+    from paper_2010_10272_gb300.serve import Request
+    reqs = []
+    for i in range(14):
+        hg = synth.serving_request(np.random.SeedSequence(500 + i), p_lo=10_000, p_hi=400_000)
+        reqs.append(Request.from_hypergraph(i, hg, rounds=1 + i % 4, subrounds=1 + i % 4, seed=i))
+    return reqs
+
+
+def _alone(req):
+    from paper_2010_10272_gb300 import HGP
+    h = HGP(req.n, req.m, req.net_off, req.pins, req.k, req.eps, req.part, req.vertex_w, req.net_w,
+            subrounds=req.subrounds, seed=req.seed)
+    st = h.refine(req.rounds)
+    out = (h.partition(), h.objective(), st[:, :5].copy())
+    h.close()
+    return out
+
+
+@pytest.mark.parametrize("budget", [None, 96 << 20])
+def test_mix_equals_alone(budget):
+    from paper_2010_10272_gb300.serve import Server
+    reqs = _requests()
+    s = torch.cuda.Stream()
+    srv = Server(stream=s, memory_budget=budget, reserve_bytes=0)
+    done = []
+    pending = list(reqs)
+    # arrivals in waves while earlier requests are still running
+    while pending or not srv.idle():
+        for _ in range(3):
+            if pending:
+                srv.submit(pending.pop(0))
+        done.extend(srv.step())
+    srv.close()
+    assert sorted(r.rid for r in done) == list(range(len(reqs)))
+    if budget is not None:
+        assert srv.ticks > max(r.rounds for r in reqs) + 2   # the budget forced queueing
+    for r in done:
+        part, obj, objs = _alone(r)
+        np.testing.assert_array_equal(r.result, part)
+        assert r.objective == obj
+        np.testing.assert_array_equal(r.stats[:, :5], objs)
+        assert r.finished >= r.admitted >= r.arrival
+
+
+def test_footprint_estimate_covers_creation():
+    from paper_2010_10272_gb300 import HGP
+    from paper_2010_10272_gb300.serve import Request
+    hg = synth.serving_request(np.random.SeedSequence(9), p_lo=2_000_000, p_hi=2_000_001)
+    req = Request.from_hypergraph(0, hg)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    h = HGP.from_hypergraph(hg)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    print("device bytes used by one request:", used, "estimate:", req.footprint())
+    assert used <= req.footprint()
+    h.close()
