@@ -139,6 +139,20 @@ int hgp_refine(hgp_handle *h, int32_t rounds, hgp_round_stats *stats);
  * vertex eligible, exactly as if the handle had been created with this partition. */
 int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device);
 
+/*
+ * Checkpoint / resume.  Everything later rounds depend on: the partition (int32[n]), which nets
+ * had a pin moved in the last completed round (uint8[m], 1 = moved; these decide eligibility in
+ * the next round, Sec. 6), the next round number (it selects the sub-rounds), and whether the
+ * next round is the first one after creation (every vertex eligible).  All arrays are host
+ * memory.  hgp_import_state on a handle created from the same hypergraph and options continues
+ * exactly where the exported handle stopped: refine(a); export; import; refine(b) equals
+ * refine(a + b).  moved_nets may be NULL on import only when first_round != 0.
+ */
+int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t *next_round,
+                     int32_t *first_round);
+int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_nets,
+                     int64_t next_round, int32_t first_round);
+
 /* (lambda-1)(Pi) as maintained incrementally (Sec. 2). */
 int hgp_objective(hgp_handle *h, int64_t *out);
 

@@ -341,6 +341,33 @@ __global__ void k_get_lambda(Dev d, uint64_t *out)
         out[e] = (uint64_t)reinterpret_cast<const Rec *>(d.rec)[e].lam;
 }
 
+// move stamps of the records
+template <typename Rec>
+__global__ void k_export_moved(Dev d, int32_t r, int32_t first, uint8_t *out)
+{
+    const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (!first && moved_in_prev_round(recs[e].mv, r)) ? 1 : 0;
+}
+
+template <typename Rec>
+__global__ void k_import_moved(Dev d, int32_t r, const uint8_t *flags)
+{
+    Rec *recs = reinterpret_cast<Rec *>(d.rec);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (flags[e]) recs[e].mv = (r - 1) * 2;   // last move in round r-1
+}
+
+__global__ void k_set_round_state(int32_t *rs, int32_t r, int32_t started)
+{
+    if (threadIdx.x == 0) {
+        rs[0] = r;
+        rs[1] = started;
+    }
+}
+
 __global__ void k_part_to_i32(const uint8_t *part, int32_t *out, int32_t n)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -748,6 +775,68 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
     }
     if (rc != HGP_OK) return rc;
     return init_state(h);
+}
+
+int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t *next_round,
+                     int32_t *first_round)
+{
+    if (!h) return HGP_ERR_INVALID;
+    if (part) {
+        const int rc = hgp_get_partition(h, part, 0);
+        if (rc != HGP_OK) return rc;
+    }
+    if (moved_nets && h->d.m > 0) {
+        Dev &d = h->d;
+        uint8_t *tmp = nullptr;
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
+        if (d.k <= 32)
+            k_export_moved<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, (int32_t)h->next_round,
+                                                                             h->all_eligible ? 1 : 0, tmp);
+        else
+            k_export_moved<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, (int32_t)h->next_round,
+                                                                             h->all_eligible ? 1 : 0, tmp);
+        h->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(moved_nets, tmp, (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
+        cudaFreeAsync(tmp, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        CK(e);
+    }
+    if (next_round) *next_round = h->next_round;
+    if (first_round) *first_round = h->all_eligible ? 1 : 0;
+    return HGP_OK;
+}
+
+int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_nets,
+                     int64_t next_round, int32_t first_round)
+{
+    if (!h || !part || next_round < 0 || next_round >= ((int64_t)1 << 30)) return HGP_ERR_INVALID;
+    if (!first_round && !moved_nets && h->d.m > 0) return HGP_ERR_INVALID;
+    int rc = hgp_set_partition(h, part, 0);
+    if (rc != HGP_OK) return rc;
+    Dev &d = h->d;
+    const int32_t r = (int32_t)next_round;
+    if (!first_round && d.m > 0) {
+        uint8_t *tmp = nullptr;
+        CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, moved_nets, (size_t)d.m, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) {
+            if (d.k <= 32) k_import_moved<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, r, tmp);
+            else k_import_moved<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, r, tmp);
+            h->launches++;
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(tmp, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        CK(e);
+    }
+    k_set_round_state<<<1, 32, 0, h->stream>>>(d.rs, r, first_round ? 0 : 1);
+    h->launches++;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    h->next_round = next_round;
+    h->all_eligible = first_round != 0;
+    return HGP_OK;
 }
 
 int hgp_objective(hgp_handle *h, int64_t *out)

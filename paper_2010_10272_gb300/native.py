@@ -84,6 +84,10 @@ def load_library():
         lib.hgp_get_lambda.argtypes = [P, P]
         lib.hgp_get_info.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
+        lib.hgp_export_state.argtypes = [P, P, P, P, P]
+        lib.hgp_import_state.argtypes = [P, P, P, i64, i32]
+        lib.hgp_export_state.restype = ctypes.c_int
+        lib.hgp_import_state.restype = ctypes.c_int
         lib.hgp_set_profiling.argtypes = [P, i32]
         lib.hgp_get_profile.argtypes = [P, P]
         lib.hgp_get_launch_count.argtypes = [P, P]
@@ -270,6 +274,23 @@ class HGP:
         _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
                "hgp_debug_candidates")
         return t, g
+
+    # -- checkpoint / resume
+    def export_state(self) -> dict:
+        part = np.empty(self.n, dtype=np.int32)
+        moved = np.empty(max(1, self.m), dtype=np.uint8)
+        r, first = ctypes.c_int64(), ctypes.c_int32()
+        _check(self._lib.hgp_export_state(self._h, _hptr(part), _hptr(moved), ctypes.byref(r),
+                                          ctypes.byref(first)), "hgp_export_state")
+        return {"partition": part, "moved_nets": moved[:self.m], "next_round": r.value,
+                "first_round": first.value}
+
+    def import_state(self, state: dict):
+        part = _host(state["partition"], np.int32)
+        moved = _host(state.get("moved_nets"), np.uint8)
+        _check(self._lib.hgp_import_state(self._h, _hptr(part), _hptr(moved),
+                                          int(state["next_round"]), int(state["first_round"])),
+               "hgp_import_state")
 
     # -- measurement
     def set_profiling(self, enable: bool = True):

@@ -280,3 +280,28 @@ def test_moved_pins_and_profile():
     assert sum(v[1] for v in prof.values()) == launched
     assert prof["gain"][1] == 3 * 4 and prof["apply"][1] == 3 * 4
     assert all(v[0] > 0 for v in prof.values())
+
+
+@pytest.mark.parametrize("k,graph", [(8, 0), (8, 1), (64, 0), (64, 1)])
+def test_checkpoint_resume(k, graph):
+    """refine(2); export; import into a fresh handle; refine(3) == refine(5) (and the oracle)."""
+    hg = synth.random_small(36 + k, 15000, 14000, k, max_size=9, weighted=True, rounds=5)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=3, seed=4)
+    want, _ = o.refine(5)
+    a = HGP.from_hypergraph(hg, subrounds=3, seed=4, graph=graph)
+    first = a.refine(2)[:, :5]
+    st = a.export_state()
+    assert st["next_round"] == 2 and st["first_round"] == 0
+    b = HGP.from_hypergraph(hg, subrounds=3, seed=4, graph=graph)
+    b.import_state(st)
+    rest = b.refine(3)[:, :5]
+    np.testing.assert_array_equal(np.concatenate([first, rest]), want)
+    np.testing.assert_array_equal(b.partition(), o.partition())
+    assert b.objective() == o.objective()
+    # a state exported before any round resumes as a fresh handle
+    c = HGP.from_hypergraph(hg, subrounds=3, seed=4)
+    s0 = c.export_state()
+    assert s0["first_round"] == 1 and not s0["moved_nets"].any()
+    d = HGP.from_hypergraph(hg, subrounds=3, seed=4)
+    d.import_state(s0)
+    np.testing.assert_array_equal(d.refine(5)[:, :5], want)
