@@ -342,6 +342,16 @@ def run_gpu(args, world, rank, local):
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": traffic, "algorithmic_bytes_per_launch": algo[kern],
                 "avg_launch_ms": avg_ms}
+    # second roofline: the gain step is bound by random record gathers (one per incidence of an
+    # active vertex), compared with the device's measured random 32-byte gather rate
+    from paper_2010_10272_gb300.native import probe_gather
+    g_ms, g_rate = probe_gather(1600 << 20, 86_000_000)
+    gain_ms = prof["gain"][0] / max(1, prof["gain"][1])
+    gathers_per_launch = info["pins"] / S
+    roofline["gather"] = {"kernel": "k_gain", "achieved_gathers_per_s": gathers_per_launch / (gain_ms / 1e3),
+                          "peak_gathers_per_s": g_rate,
+                          "frac": gathers_per_launch / (gain_ms / 1e3) / g_rate,
+                          "peak_kind": "measured random 32-byte gathers from a 1.6 GB array (hgp_probe_gather)"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items()}
     other = "apply" if kern == "gain" else "gain"

@@ -264,6 +264,15 @@ int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, con
                            const int32_t *part, int32_t subrounds, uint64_t seed, int32_t s,
                            int32_t *target, int64_t *gain, void *cuda_stream);
 
+/*
+ * Measurement helper (no counterpart in the paper): times n_gathers random 32-byte gathers from
+ * a freshly allocated array of array_bytes bytes on the current device (best of two timed runs
+ * after one warm-up) and returns the time and the rate.  The gain and apply steps are bound by
+ * such random accesses, so this rate is their ceiling when the per-net data exceeds L2.
+ * Allocates and frees its own buffers.
+ */
+int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *ms_out, double *gathers_per_s);
+
 /* Frees all device memory of the handle (NULL is allowed). */
 void hgp_destroy(hgp_handle *h);
 

@@ -566,24 +566,38 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
         }
     }
     if (!B) {
-        // one instance: combine the warps of the CTA, then one atomic per block
+        // one instance: the warps add their partial sums into warp 0's slots as they finish and
+        // the last warp of the CTA flushes them with one atomic per block (no barrier, so warps
+        // that finish early do not wait for the slowest one)
         __shared__ unsigned long long cnt_s[2];
-        if (tid < 2) cnt_s[tid] = 0;
+        __shared__ int warps_done;
+        if (tid == 0) { cnt_s[0] = 0; cnt_s[1] = 0; warps_done = 0; }
         __syncthreads();
+        if (wid != 0) {
+            for (int t = lane; t < 64; t += 32)
+                if (tot_w[wid][t]) atomicAdd(&tot_w[0][t], tot_w[wid][t]);
+        }
         if (lane == 0) {
             if (nelig) atomicAdd(&cnt_s[0], (unsigned long long)nelig);
             if (ncand) atomicAdd(&cnt_s[1], (unsigned long long)ncand);
         }
-        __syncthreads();
-        if (tid < 64 && tid < d0.k) {
-            unsigned long long v = 0;
-            for (int w = 0; w < kWarps; ++w) v += tot_w[w][tid];
-            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.tot[tid]), v);
-        }
-        if (tid == 0) {
-            unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
-            if (cnt_s[0]) atomicAdd(row + ST_ELIG, cnt_s[0]);
-            if (cnt_s[1]) atomicAdd(row + ST_CAND, cnt_s[1]);
+        __threadfence_block();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&warps_done, 1) == kWarps - 1;
+        last = __shfl_sync(kFull, last, 0);
+        if (last) {
+            __threadfence_block();
+            for (int t = lane; t < 64 && t < d0.k; t += 32) {
+                const unsigned long long v = atomicAdd(&tot_w[0][t], 0ull);
+                if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.tot[t]), v);
+            }
+            if (lane == 0) {
+                unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
+                const unsigned long long c0 = atomicAdd(&cnt_s[0], 0ull), c1 = atomicAdd(&cnt_s[1], 0ull);
+                if (c0) atomicAdd(row + ST_ELIG, c0);
+                if (c1) atomicAdd(row + ST_CAND, c1);
+            }
         }
     }
 }
@@ -954,7 +968,20 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
     const int32_t ncand = d.cand_cnt[range];
     if (ncand == 0) return;
     const uint64_t *cand = d.cand + (int64_t)range * kRange;
+    bool has_tie = false;
     if (any_thr) {
+        // the id-ordered tie prefix is only needed if this range holds a candidate at its
+        // block's threshold gain
+        bool tie = false;
+        for (int i = lane; i < ncand; i += 32) {
+            int t, ul;
+            int32_t g;
+            decode(cand[i], t, g, ul);
+            tie = tie || (mode[t] == SEL_THRESH && g == gthr[t]);
+        }
+        has_tie = __any_sync(kFull, tie) != 0;
+    }
+    if (has_tie) {
         const int32_t tile = range / kWarps;
         for (int t = lane; t < 64; t += 32)
             run[t] = (t < d.k && mode[t] == SEL_THRESH)
@@ -1095,30 +1122,44 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
         }
     }
     if (!B) {
+        // as in k_gain: partial sums into warp 0's slots, the last warp to finish flushes
         __shared__ unsigned long long objd, napp, mpins;
+        __shared__ int warps_done;
         for (int o = 16; o; o >>= 1) {
             dobj += __shfl_xor_sync(kFull, dobj, o);
             nappr += __shfl_xor_sync(kFull, nappr, o);
             npins += __shfl_xor_sync(kFull, npins, o);
         }
-        if (tid == 0) { objd = 0; napp = 0; mpins = 0; }
+        if (tid == 0) { objd = 0; napp = 0; mpins = 0; warps_done = 0; }
         __syncthreads();
+        if (wid != 0) {
+            for (int t = lane; t < 64; t += 32)
+                if (bwd_w[wid][t]) atomicAdd(&bwd_w[0][t], bwd_w[wid][t]);
+        }
         if (lane == 0) {
             if (dobj) atomicAdd(&objd, (unsigned long long)dobj);
             if (nappr) atomicAdd(&napp, (unsigned long long)nappr);
             if (npins) atomicAdd(&mpins, (unsigned long long)npins);
         }
-        __syncthreads();
-        if (tid < 64 && tid < d0.k) {
-            unsigned long long v = 0;
-            for (int w = 0; w < kWarps; ++w) v += bwd_w[w][tid];
-            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.bw[tid]), v);
-        }
-        if (tid == 0) {
-            unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
-            if (objd) atomicAdd(reinterpret_cast<unsigned long long *>(d0.obj), objd);
-            if (napp) atomicAdd(row + ST_APPR, napp);
-            if (mpins) atomicAdd(row + ST_MOVED, mpins);
+        __threadfence_block();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&warps_done, 1) == kWarps - 1;
+        last = __shfl_sync(kFull, last, 0);
+        if (last) {
+            __threadfence_block();
+            for (int t = lane; t < 64 && t < d0.k; t += 32) {
+                const unsigned long long v = atomicAdd(&bwd_w[0][t], 0ull);
+                if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&d0.bw[t]), v);
+            }
+            if (lane == 0) {
+                unsigned long long *row = reinterpret_cast<unsigned long long *>(d0.stats + (int64_t)rr * ST_N);
+                const unsigned long long o1 = atomicAdd(&objd, 0ull), a1 = atomicAdd(&napp, 0ull),
+                                         p1 = atomicAdd(&mpins, 0ull);
+                if (o1) atomicAdd(reinterpret_cast<unsigned long long *>(d0.obj), o1);
+                if (a1) atomicAdd(row + ST_APPR, a1);
+                if (p1) atomicAdd(row + ST_MOVED, p1);
+            }
         }
     }
 }

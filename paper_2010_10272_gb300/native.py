@@ -110,6 +110,8 @@ def load_library():
             getattr(lib, name).restype = ctypes.c_int
         lib.hgp_batch_destroy.argtypes = [P]
         lib.hgp_batch_destroy.restype = None
+        lib.hgp_probe_gather.argtypes = [i64, i64, P, P]
+        lib.hgp_probe_gather.restype = ctypes.c_int
         lib.hgp_destroy.argtypes = [P]
         lib.hgp_destroy.restype = None
         _lib = lib
@@ -368,3 +370,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_gather(array_bytes: int = 1600 << 20, n_gathers: int = 86_000_000):
+    """Random 32-byte gather rate of the current device: (ms, gathers per second)."""
+    lib = load_library()
+    ms, rate = ctypes.c_double(), ctypes.c_double()
+    _check(lib.hgp_probe_gather(int(array_bytes), int(n_gathers), ctypes.byref(ms), ctypes.byref(rate)),
+           "hgp_probe_gather")
+    return ms.value, rate.value
