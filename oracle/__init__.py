@@ -71,6 +71,8 @@ def _load():
         lib.oracle_subround_of.argtypes = [u64, i64, i32, i32]
         for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
             getattr(lib, name).argtypes = [P, P]
+        lib.oracle_exact_gains.restype = ctypes.c_int
+        lib.oracle_exact_gains.argtypes = [P, i32, P, P]
         lib.oracle_sample_candidates.restype = ctypes.c_int
         lib.oracle_sample_candidates.argtypes = [i32, i32, P, P, P, P, i32, f64, P, i32, u64,
                                                  i32, i32, P, P, P]
@@ -157,6 +159,14 @@ class Oracle:
         g = np.zeros(self.n, dtype=np.int64)
         self._lib.oracle_candidates(self._h, int(s), _ptr(t), _ptr(g))
         return t, g
+
+    def exact_gains(self, moves) -> np.ndarray:
+        """Gains of a move sequence [(u, from, to), ...] performed in order (state unchanged)."""
+        mv = np.ascontiguousarray(moves, dtype=np.int32).reshape(-1, 3)
+        g = np.zeros(mv.shape[0], dtype=np.int64)
+        if self._lib.oracle_exact_gains(self._h, int(mv.shape[0]), _ptr(mv), _ptr(g)) != 0:
+            raise ValueError("invalid move sequence")
+        return g
 
     def objective(self) -> int:
         return int(self._lib.oracle_objective(self._h))

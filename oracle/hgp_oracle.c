@@ -398,3 +398,39 @@ int oracle_sample_candidates(int32_t n, int32_t m, const int64_t *net_off, const
     free(bw); free(slot); free(phi_row); free(b); free(p);
     return 0;
 }
+
+/* Exact gains of a move sequence (Sec. 5.4): moves[3*j..3*j+2] = (u, from, to), performed in
+ * order j = 0..count-1; gain[j] = g_to(u) (Sec. 5) against the state after moves 0..j-1.
+ * The oracle's own state is not changed.  Returns -1 if a move is invalid (u out of range,
+ * from != Pi(u) at that point, to out of range or equal to from, a vertex moved twice). */
+int oracle_exact_gains(const oracle_t *o, int32_t count, const int32_t *moves, int64_t *gain)
+{
+    const int32_t n = o->n, m = o->m, k = o->k;
+    int64_t *phi = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m * k + 1));
+    int32_t *part = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint8_t *seen = (uint8_t *)calloc((size_t)n + 1, 1);
+    if (!phi || !part || !seen) { free(phi); free(part); free(seen); return -1; }
+    memcpy(phi, o->phi, sizeof(int64_t) * (size_t)m * k);
+    memcpy(part, o->part, sizeof(int32_t) * (size_t)n);
+    int rc = 0;
+    for (int32_t j = 0; j < count && rc == 0; ++j) {
+        const int32_t u = moves[3 * j], a = moves[3 * j + 1], b = moves[3 * j + 2];
+        if (u < 0 || u >= n || seen[u] || a != part[u] || b < 0 || b >= k || b == a) { rc = -1; break; }
+        seen[u] = 1;
+        int64_t bu = 0, pb = 0;
+        for (int64_t x = o->vtx_off[u]; x < o->vtx_off[u + 1]; ++x) {
+            const int32_t e = o->inc[x];
+            if (phi[(int64_t)e * k + a] == 1) bu += o->nw[e];
+            if (phi[(int64_t)e * k + b] == 0) pb += o->nw[e];
+        }
+        gain[j] = bu - pb;
+        for (int64_t x = o->vtx_off[u]; x < o->vtx_off[u + 1]; ++x) {
+            const int32_t e = o->inc[x];
+            phi[(int64_t)e * k + a]--;
+            phi[(int64_t)e * k + b]++;
+        }
+        part[u] = b;
+    }
+    free(phi); free(part); free(seen);
+    return rc;
+}
