@@ -265,6 +265,15 @@ int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, con
                            int32_t *target, int64_t *gain, void *cuda_stream);
 
 /*
+ * Exact gains of a move sequence (paper Sec. 5.4, Lemma 1), computed in parallel.
+ * moves: host int32[count][3] = (u, from, to) in sequence order, every vertex at most once,
+ * from = its current block, to != from.  gains: host int64[count], gains[j] = the gain (Sec. 5)
+ * of move j against the state after moves 0..j-1 were performed.  The handle's partition is
+ * not changed.  HGP_ERR_INVALID for an invalid move or sequence.
+ */
+int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *moves, int64_t *gains);
+
+/*
  * Measurement helper (no counterpart in the paper): times n_gathers random 32-byte gathers from
  * a freshly allocated array of array_bytes bytes on the current device (best of two timed runs
  * after one warm-up) and returns the time and the rate.  The gain and apply steps are bound by

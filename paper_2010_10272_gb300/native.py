@@ -84,6 +84,8 @@ def load_library():
         lib.hgp_get_lambda.argtypes = [P, P]
         lib.hgp_get_info.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
+        lib.hgp_exact_gains.argtypes = [P, i32, P, P]
+        lib.hgp_exact_gains.restype = ctypes.c_int
         lib.hgp_export_state.argtypes = [P, P, P, P, P]
         lib.hgp_import_state.argtypes = [P, P, P, i64, i32]
         lib.hgp_export_state.restype = ctypes.c_int
@@ -276,6 +278,13 @@ class HGP:
         _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
                "hgp_debug_candidates")
         return t, g
+
+    def exact_gains(self, moves) -> np.ndarray:
+        """Gains of a move sequence [(u, from, to), ...] performed in order (Lemma 1)."""
+        mv = np.ascontiguousarray(moves, dtype=np.int32).reshape(-1, 3)
+        g = np.empty(mv.shape[0], dtype=np.int64)
+        _check(self._lib.hgp_exact_gains(self._h, int(mv.shape[0]), _hptr(mv), _hptr(g)), "hgp_exact_gains")
+        return g
 
     # -- checkpoint / resume
     def export_state(self) -> dict:

@@ -305,3 +305,35 @@ def test_checkpoint_resume(k, graph):
     d = HGP.from_hypergraph(hg, subrounds=3, seed=4)
     d.import_state(s0)
     np.testing.assert_array_equal(d.refine(5)[:, :5], want)
+
+
+@pytest.mark.parametrize("k,weighted,frac", [(2, False, 0.3), (8, True, 0.5), (64, True, 0.2), (40, False, 1.0)])
+def test_exact_gains_match_oracle(k, weighted, frac):
+    """Lemma 1 on the GPU against the oracle's sequential replay, random move sequences."""
+    rng = np.random.default_rng(k)
+    hg = synth.random_small(70 + k, 20000, 18000, k, max_size=12, weighted=weighted)
+    h = HGP.from_hypergraph(hg)
+    o = oracle.Oracle.from_hypergraph(hg)
+    verts = rng.permutation(hg.n)[: int(frac * hg.n)]
+    to = rng.integers(0, k - 1, size=verts.size)
+    a = hg.part[verts]
+    to = np.where(to >= a, to + 1, to)
+    moves = np.stack([verts, a, to], axis=1).astype(np.int32)
+    np.testing.assert_array_equal(h.exact_gains(moves), o.exact_gains(moves))
+    np.testing.assert_array_equal(h.partition(), hg.part)      # state unchanged
+    from paper_2010_10272_gb300 import HGPError
+    bad = moves[:2].copy()
+    bad[1, 0] = bad[0, 0]                                        # vertex twice
+    with pytest.raises(HGPError):
+        h.exact_gains(bad)
+
+
+def test_exact_gains_of_lp_moves_sum_to_objective_change():
+    hg = synth.random_small(99, 30000, 30000, 16, max_size=8, weighted=True, rounds=1)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=1)
+    _, log = o.refine(1, log_moves=True)
+    h = HGP.from_hypergraph(hg, subrounds=1)
+    g = h.exact_gains(log[:, 1:].astype(np.int32))
+    st = h.refine(1)
+    o0 = oracle.Oracle.from_hypergraph(hg, subrounds=1)
+    assert o0.objective() - st[0, 0] == g.sum()
