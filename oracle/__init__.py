@@ -71,6 +71,7 @@ def _load():
         lib.oracle_subround_of.argtypes = [u64, i64, i32, i32]
         for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
             getattr(lib, name).argtypes = [P, P]
+        lib.oracle_set_variant.argtypes = [P, i32, i32]
         lib.oracle_exact_gains.restype = ctypes.c_int
         lib.oracle_exact_gains.argtypes = [P, i32, P, P]
         lib.oracle_sample_candidates.restype = ctypes.c_int
@@ -104,7 +105,8 @@ class Oracle:
     """Sequential oracle state for one hypergraph and partition."""
 
     def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None,
-                 subrounds: int = 4, seed: int = 0):
+                 subrounds: int = 4, seed: int = 0, balance_moves: bool = False,
+                 revert_negative: bool = False):
         lib = _load()
         self._lib = lib
         self.n, self.m, self.k = int(n), int(m), int(k)
@@ -117,11 +119,13 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle_create rejected the input")
         self._keep = None
+        lib.oracle_set_variant(self._h, int(bool(balance_moves)), int(bool(revert_negative)))
 
     @classmethod
-    def from_hypergraph(cls, hg, subrounds: int = 4, seed: int = 0, part=None):
+    def from_hypergraph(cls, hg, subrounds: int = 4, seed: int = 0, part=None, **variant):
         return cls(hg.n, hg.m, hg.net_off, hg.pins, hg.k, hg.eps,
-                   hg.part if part is None else part, hg.vertex_w, hg.net_w, subrounds, seed)
+                   hg.part if part is None else part, hg.vertex_w, hg.net_w, subrounds, seed,
+                   **variant)
 
     def close(self):
         if self._h:

@@ -56,6 +56,8 @@ typedef struct {
     int64_t *phi;          /* [m*k] Phi(e,i) */
     int64_t *bw;           /* [k]  block weights c(V_i) */
     int64_t round;         /* global round counter */
+    int32_t balance_moves; /* variant: zero-gain moves that improve the balance (Sec. 6) */
+    int32_t revert_negative; /* variant: undo moves whose exact gain is negative (Sec. 6) */
     int all_eligible;      /* 1 until the first round has run */
     uint8_t *moved_prev;   /* [m]  net had a pin moved in the previous round */
     uint8_t *moved_cur;    /* [m]  net had a pin moved in the current round */
@@ -201,7 +203,10 @@ static int eligible(const oracle_t *o, int32_t u)
 }
 
 /* Best feasible positive-gain target of u against the frozen state (Sec. 6): the block
- * with the highest gain, smallest id on ties; -1 if no block has positive gain and room. */
+ * with the highest gain, smallest id on ties; -1 if no block has positive gain and room.
+ * With the balance-move variant, a vertex without such a block may instead take a zero-gain
+ * move that improves the balance (Sec. 6): to a block t with room and w(t) + c(u) < w(a), the
+ * lightest such block (smallest id among equally light ones). */
 static void best_move(const oracle_t *o, int32_t u, int32_t *t_out, int64_t *g_out)
 {
     int32_t a = o->part[u];
@@ -212,8 +217,22 @@ static void best_move(const oracle_t *o, int32_t u, int32_t *t_out, int64_t *g_o
         int64_t g = oracle_gain(o, u, i);
         if (g > best_g && o->bw[i] + o->vw[u] <= o->lmax) { best_t = i; best_g = g; }
     }
+    if (best_t < 0 && o->balance_moves) {
+        for (int32_t i = 0; i < o->k; ++i) {
+            if (i == a) continue;
+            const int64_t wi = o->bw[i] + o->vw[u];
+            if (wi > o->lmax || wi >= o->bw[a] || oracle_gain(o, u, i) != 0) continue;
+            if (best_t < 0 || o->bw[i] < o->bw[best_t]) best_t = i;
+        }
+    }
     *t_out = best_t;
     *g_out = best_g;
+}
+
+void oracle_set_variant(oracle_t *o, int32_t balance_moves, int32_t revert_negative)
+{
+    o->balance_moves = balance_moves;
+    o->revert_negative = revert_negative;
 }
 
 static const oracle_t *g_sort_ctx;

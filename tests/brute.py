@@ -99,7 +99,7 @@ class Tiny:
 
 
 def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round: int = 0,
-              moved_prev: Optional[set] = None):
+              moved_prev: Optional[set] = None, balance_moves: bool = False):
     """Synchronous LP rounds with definitional gains.  Returns (part, per-round stats,
     move log [(global sub-round, u, from, to)], moved set of the last round).
 
@@ -134,6 +134,12 @@ def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round
                     g = t.gain(part, u, i)
                     if g > 0 and w[i] + t.vw[u] <= lmax and (best is None or g > best[1]):
                         best = (i, g)
+                if best is None and balance_moves:
+                    # a zero-gain move to a block it leaves more balanced than a: lightest first
+                    zs = [i for i in range(t.k) if i != part[u] and t.gain(part, u, i) == 0
+                          and w[i] + t.vw[u] <= lmax and w[i] + t.vw[u] < w[part[u]]]
+                    if zs:
+                        best = (min(zs, key=lambda i: (w[i], i)), 0)
                 if best is not None:
                     cands[u] = best
             n_cand += len(cands)

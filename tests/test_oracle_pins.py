@@ -263,3 +263,46 @@ def test_rejects_bad_partition():
     off, pins = t.csr()
     with pytest.raises(ValueError):
         oracle.Oracle(3, 1, off, pins, 2, 0.1, np.array([0, 2, 1], np.int32))
+
+
+# --- variant: zero-gain balance moves (Sec. 6) ----------------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_balance_moves_match_bruteforce(seed):
+    rng = np.random.default_rng(900 + seed)
+    k = int(rng.integers(2, 5))
+    S = int(rng.integers(1, 4))
+    t = random_tiny(rng, 14, 12, k, max_size=4, weighted=seed % 2 == 0, eps=0.5)
+    part = rng.integers(0, k, size=t.n)
+    part[: t.n // 2] = 0                                  # unbalanced: balance moves matter
+    off, pins = t.csr()
+    vw = None if all(x == 1 for x in t.vw) else np.array(t.vw, dtype=np.int32)
+    nw = None if all(x == 1 for x in t.nw) else np.array(t.nw, dtype=np.int32)
+    o = oracle.Oracle(t.n, t.m, off, pins, k, t.eps, part.astype(np.int32), vw, nw, S, seed,
+                      balance_moves=True)
+    stats, moves = o.refine(4, log_moves=True)
+    want_part, want_stats, want_log, _ = lp_rounds(t, part, 4, S=S, seed=seed, balance_moves=True)
+    assert [tuple(r) for r in stats.tolist()] == want_stats
+    assert [tuple(m) for m in moves.tolist()] == want_log
+    np.testing.assert_array_equal(o.partition(), want_part)
+
+
+def test_balance_moves_hand_example():
+    # Nets {0,1} and {2,3}; all four vertices in block 0 (k=2, eps=0.5, L_max = 3 > w... no:
+    # c(V) = 4, ceil(4/2) = 2, L_max = floor(1.5 * 2) = 3).  Every move has gain -1 except none
+    # with positive gain; vertex 0 -> block 1 has gain -1 (net {0,1} becomes cut), so no
+    # zero-gain move exists and nothing moves even with the variant.
+    t = Tiny(4, [[0, 1], [2, 3]], 2, 0.5)
+    o = make_oracle(t, [0, 0, 0, 0], S=1)
+    o2 = oracle.Oracle(4, 2, *t.csr(), 2, 0.5, np.zeros(4, np.int32), None, None, 1, 0,
+                       balance_moves=True)
+    assert o2.refine(1)[0][0, 2] == 0
+    # An isolated vertex has gain 0 to every block: with the variant it leaves the overloaded
+    # block 0 (w0 = 4 > L_max = 3) for block 1, the only lighter block (0 + 1 < 4).
+    t2 = Tiny(5, [[0, 1], [2, 3]], 2, 0.5)            # vertex 4 has no nets; c(V) = 5, L_max = 4
+    o3 = oracle.Oracle(5, 2, *t2.csr(), 2, 0.5, np.zeros(5, np.int32), None, None, 1, 0,
+                       balance_moves=True)
+    st, mv = o3.refine(1, log_moves=True)
+    assert [tuple(x) for x in mv.tolist()] == [(0, 4, 0, 1)]
+    assert st[0, 0] == 0 and st[0, 2] == 1
+    del o
