@@ -70,6 +70,12 @@ typedef struct {
                             with a given round count and replays it afterwards [0]; ignored
                             while profiling is on */
     void *cuda_stream;   /* cudaStream_t to run on, or NULL for a library-owned stream */
+    int32_t balance_moves;   /* variant (Sec. 6): a vertex without a feasible positive-gain
+                                target may take a zero-gain move to a block t with room and
+                                w(t) + c(u) < w(Pi(u)), the lightest such block [0] */
+    int32_t revert_negative; /* variant (Sec. 6, attributed gains): after each sub-round, the
+                                applied moves' exact gains in vertex-id order (Sec. 5.4) are
+                                computed and every move with a negative one is undone [0] */
 } hgp_options;
 
 /* Per-round statistics written by hgp_refine. */

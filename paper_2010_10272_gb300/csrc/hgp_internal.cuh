@@ -96,6 +96,8 @@ struct Dev {
     int64_t *stats;         // [rounds * ST_N]
     int32_t *err;
     uint64_t seed;          // sub-round hash seed
+    int32_t variant;        // bit 0: zero-gain balance moves; bit 1: revert negative moves
+    int32_t pad0;
     int32_t *rs;            // round state on the device: rs[0] = next round r, rs[1] = 0 while
                             // every vertex is eligible (first round), 1 afterwards
 };

@@ -193,6 +193,7 @@ struct alignas(16) GainWarp {
     Lam lamc[kCache];            // Lambda(e) of the chunk's incidences, in flattened order
     int32_t wc[kCache];          // omega(e)
     unsigned long long T[32];
+    unsigned long long A2[32];   // AND of Lambda(e) over nets with Phi(e,a) >= 2 (balance moves)
     int32_t W[32], b[32], jb[32], a[32], elig[32];
     int32_t off[33];
 };
@@ -216,7 +217,8 @@ __device__ __forceinline__ int slot_of(const int32_t *off, int32_t i)
 template <typename Lam, typename Rec, int NP, bool UNIT>
 __device__ __forceinline__ void bitsliced_best(const GainWarp<Lam> &g, const Rec *recs, const int32_t *inc,
                                                int32_t i_begin, int32_t i_end, int32_t jb, int32_t off,
-                                               Lam T, int &t_out, int32_t &conn_out)
+                                               Lam T, int &t_out, int32_t &conn_out, int32_t eq_value,
+                                               Lam &eq_out)
 {
     Lam c[NP];
 #pragma unroll
@@ -263,17 +265,22 @@ __device__ __forceinline__ void bitsliced_best(const GainWarp<Lam> &g, const Rec
     for (int p = 0; p < NP; ++p) v |= (int32_t)((c[p] >> t) & 1) << p;
     t_out = t;
     conn_out = v;
+    // blocks of T whose conn equals eq_value (eq_value < 0: none)
+    Lam eq = eq_value >= 0 && (eq_value >> NP) == 0 ? T : (Lam)0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) eq &= ((eq_value >> p) & 1) ? c[p] : ~c[p];
+    eq_out = eq;
 }
 
 template <typename Lam, typename Rec, bool UNIT>
 __device__ __forceinline__ void best_by_planes(int np, const GainWarp<Lam> &g, const Rec *recs,
                                                const int32_t *inc, int32_t ib, int32_t ie, int32_t jb,
-                                               int32_t off, Lam T, int &t, int32_t &conn)
+                                               int32_t off, Lam T, int &t, int32_t &conn, int32_t eqv, Lam &eq)
 {
-    if (np <= 4) bitsliced_best<Lam, Rec, 4, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
-    else if (np <= 6) bitsliced_best<Lam, Rec, 6, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
-    else if (np <= 8) bitsliced_best<Lam, Rec, 8, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
-    else bitsliced_best<Lam, Rec, 11, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn);
+    if (np <= 4) bitsliced_best<Lam, Rec, 4, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn, eqv, eq);
+    else if (np <= 6) bitsliced_best<Lam, Rec, 6, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn, eqv, eq);
+    else if (np <= 8) bitsliced_best<Lam, Rec, 8, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn, eqv, eq);
+    else bitsliced_best<Lam, Rec, 11, UNIT>(g, recs, inc, ib, ie, jb, off, T, t, conn, eqv, eq);
 }
 
 constexpr int32_t kPlaneMaxW = 2047;   // W(u) up to this uses bit planes (NP <= 11)
@@ -297,6 +304,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
     const int lane = threadIdx.x & 31;
     const Lam feas1 = gi.feas1;
     const int32_t r = gi.r, all_elig = gi.all_elig;
+    const bool balance = (d.variant & 1) != 0;
         const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
         const bool unit = d.nw == nullptr;
         const int32_t rbase = range * kRange;
@@ -327,6 +335,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
             g.W[lane] = 0;
             g.b[lane] = 0;
             g.T[lane] = 0;
+            g.A2[lane] = ~0ull;
             g.elig[lane] = all_elig;
             int32_t incl = deg;
 #pragma unroll
@@ -362,6 +371,8 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     if ((s11 >> g.a[v1]) & 1) {
                         atomicAdd(&g.b[v1], w1);
                         atomicOr(&g.T[v1], (unsigned long long)lam1);
+                    } else if (balance) {
+                        atomicAnd(&g.A2[v1], (unsigned long long)lam1);
                     }
                     if (moved_in_prev_round(mv1, r)) g.elig[v1] = 1;
                 }
@@ -372,6 +383,8 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     if ((s12 >> g.a[v2]) & 1) {
                         atomicAdd(&g.b[v2], w2);
                         atomicOr(&g.T[v2], (unsigned long long)lam2);
+                    } else if (balance) {
+                        atomicAnd(&g.A2[v2], (unsigned long long)lam2);
                     }
                     if (moved_in_prev_round(mv2, r)) g.elig[v2] = 1;
                 }
@@ -382,6 +395,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
             const bool elig = valid && g.elig[lane] != 0;
             Lam T = elig ? (Lam)g.T[lane] : (Lam)0;
             T &= ~((Lam)1 << a);
+            const Lam T_all = T;   // before the room filter (balance moves need it)
             if (d.vw) {
                 for (Lam x = T; x; x &= x - 1) {
                     const int t = lam_bits_ctz(x);
@@ -395,12 +409,14 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
             int32_t t_best = -1, g_best = 0;
             const int32_t bw_ = b - W;
             const unsigned wmax = __reduce_max_sync(kFull, plane_path ? (unsigned)W : 0u);
+            Lam zero_in = 0;   // blocks of T with gain exactly 0 (balance moves)
             if (plane_path) {
                 const int np = 32 - __clz((int)wmax);   // 2^np > wmax >= conn_t
                 int t;
                 int32_t conn;
-                if (unit) best_by_planes<Lam, Rec, true>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn);
-                else best_by_planes<Lam, Rec, false>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn);
+                const int32_t eqv = balance ? W - b : -1;
+                if (unit) best_by_planes<Lam, Rec, true>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn, eqv, zero_in);
+                else best_by_planes<Lam, Rec, false>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn, eqv, zero_in);
                 const int32_t gg = bw_ + conn;
                 if (gg > 0) {
                     t_best = t;
@@ -460,6 +476,31 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     t_best = 255 - (int)(key & 0xFF);
                     g_best = (int32_t)(key >> 8);
                 }
+                if (balance) {
+                    // zero-gain blocks of T among the ones this lane owns
+                    const unsigned zlo = __ballot_sync(kFull, ((Tlo >> lane) & 1) && hbw + acc0 == 0);
+                    const unsigned zhi = __ballot_sync(kFull, kWide && ((Thi >> lane) & 1) && hbw + acc1 == 0);
+                    if (lane == src) zero_in = kWide ? (Lam)((uint64_t)zlo | ((uint64_t)zhi << 32)) : (Lam)zlo;
+                }
+            }
+            if (balance && valid && elig && t_best < 0) {
+                // zero-gain moves that improve the balance (Sec. 6): blocks of T with gain 0, and
+                // blocks outside T that lie in every net where u is not alone (their gain is
+                // b - p_t = 0 exactly then); room and w(t) + c(u) < w(a); lightest block first
+                const Lam kmask = d.k >= (int)(8 * sizeof(Lam)) ? ~(Lam)0 : (((Lam)1 << d.k) - 1);
+                Lam z = (zero_in | ((Lam)g.A2[lane] & ~T_all & ~((Lam)1 << a))) & kmask;
+                const long long wa = d.lmax - slack[a];
+                long long best_w = 0;
+                for (Lam x = z; x; x &= x - 1) {
+                    const int t = lam_bits_ctz(x);
+                    const long long wt = d.lmax - slack[t];
+                    if (slack[t] < cu || wt + cu >= wa) continue;
+                    if (t_best < 0 || wt < best_w) {
+                        t_best = t;
+                        best_w = wt;
+                    }
+                }
+                g_best = 0;
             }
             nel += __popc(__ballot_sync(kFull, elig));
             const unsigned cm = __ballot_sync(kFull, t_best >= 0);

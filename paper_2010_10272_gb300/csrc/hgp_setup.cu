@@ -658,6 +658,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(dalloc(h, &h->d_round, 4));
     d.rs = h->d_round;
     d.seed = o.seed;
+    d.variant = (o.balance_moves ? 1 : 0) | (o.revert_negative ? 2 : 0);
 
     rc = init_state(h);
     if (rc != HGP_OK) return fail(rc);

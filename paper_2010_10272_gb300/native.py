@@ -34,7 +34,8 @@ class HGPError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("subrounds", ctypes.c_int32), ("phi_width", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("debug", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("balance_moves", ctypes.c_int32),
+                ("revert_negative", ctypes.c_int32)]
 
 
 class BatchOptions(ctypes.Structure):
@@ -168,12 +169,14 @@ class HGP:
 
     def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None, *,
                  subrounds: int = 4, seed: int = 0, phi_width: int = 0, debug: int = 0,
-                 graph: int = 0, stream=None, device: bool = False):
+                 graph: int = 0, stream=None, device: bool = False, balance_moves: bool = False,
+                 revert_negative: bool = False):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
         o = default_options()
         o.subrounds, o.phi_width, o.seed = int(subrounds), int(phi_width), int(seed)
         o.debug, o.graph = int(debug), int(graph)
+        o.balance_moves, o.revert_negative = int(bool(balance_moves)), int(bool(revert_negative))
         sh = _stream_handle(stream)
         o.cuda_stream = ctypes.c_void_p(sh) if sh else None
         self.n, self.m, self.k = int(n), int(m), int(k)

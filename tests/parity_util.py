@@ -24,12 +24,14 @@ def compare_state(h, o, check_phi=True):
         assert h.objective_from_phi() == o.objective()
 
 
-def run_both(hg, rounds=None, S=4, seed=0, phi_width=0, part=None, check_phi=True, chunks=None):
-    """Refine with both paths; `chunks` splits the rounds into several refine calls."""
+def run_both(hg, rounds=None, S=4, seed=0, phi_width=0, part=None, check_phi=True, chunks=None,
+             **variant):
+    """Refine with both paths; `chunks` splits the rounds into several refine calls;
+    `variant` (balance_moves, revert_negative) goes to both."""
     from paper_2010_10272_gb300 import HGP
     rounds = hg.rounds if rounds is None else rounds
-    h = HGP.from_hypergraph(hg, part=part, subrounds=S, seed=seed, phi_width=phi_width)
-    o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=seed, part=part)
+    h = HGP.from_hypergraph(hg, part=part, subrounds=S, seed=seed, phi_width=phi_width, **variant)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=seed, part=part, **variant)
     assert h.info()["lmax"] == o.lmax
     compare_state(h, o, check_phi)
     got, want = [], []

@@ -54,9 +54,10 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "hgp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(hgp_options), offsetof(hgp_options, phi_width),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hgp_options), offsetof(hgp_options, phi_width),
          offsetof(hgp_options, seed), offsetof(hgp_options, debug), offsetof(hgp_options, graph),
-         offsetof(hgp_options, cuda_stream), sizeof(hgp_round_stats));
+         offsetof(hgp_options, cuda_stream), offsetof(hgp_options, balance_moves),
+         offsetof(hgp_options, revert_negative), sizeof(hgp_round_stats));
   return 0;
 }
 '''
@@ -68,7 +69,7 @@ int main(void) {
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(Options), Options.phi_width.offset, Options.seed.offset,
             Options.debug.offset, Options.graph.offset, Options.cuda_stream.offset,
-            ctypes.sizeof(RoundStats)]
+            Options.balance_moves.offset, Options.revert_negative.offset, ctypes.sizeof(RoundStats)]
     assert vals == want
 
 
