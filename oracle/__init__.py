@@ -139,10 +139,13 @@ class Oracle:
             pass
 
     def refine(self, rounds: int, log_moves: bool = False, max_moves: int = 1 << 20):
-        """Runs `rounds` rounds. Returns (stats [rounds x 5] int64, moves or None).
+        """Runs `rounds` rounds. Returns (stats [rounds x 5] int64, moves or None); the
+        per-round count of reverted moves (revert variant) is left in `self.reverted`.
 
-        moves: int64 [count x 4] = (global sub-round index, u, from, to)."""
-        stats = np.zeros((rounds, len(STAT_FIELDS)), dtype=np.int64)
+        moves: int64 [count x 4] = (global sub-round index, u, from, to); a reverted move
+        appears a second time, from its target back to its source, after its sub-round's
+        moves."""
+        stats = np.zeros((rounds, len(STAT_FIELDS) + 1), dtype=np.int64)
         moves = np.zeros((max_moves, 4), dtype=np.int64) if log_moves else None
         cnt = ctypes.c_int64(0)
         rc = self._lib.oracle_refine(self._h, int(rounds), _ptr(stats), _ptr(moves),
@@ -153,7 +156,8 @@ class Oracle:
             if cnt.value > max_moves:
                 raise ValueError("move log truncated")
             moves = moves[:cnt.value].copy()
-        return stats, moves
+        self.reverted = stats[:, len(STAT_FIELDS)].copy()
+        return stats[:, :len(STAT_FIELDS)].copy(), moves
 
     def gain(self, u: int, i: int) -> int:
         return int(self._lib.oracle_gain(self._h, int(u), int(i)))

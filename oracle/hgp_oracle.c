@@ -30,6 +30,15 @@
  *   Candidates are then approved per target block in (gain desc, vertex id asc) order while
  *   the inclusive prefix of their weights fits into L_max - w(t).  All approved moves are
  *   applied, Phi and the block weights are updated, and the objective is recomputed.
+ * Variants (Sec. 6), both off by default:
+ *   balance moves: a vertex without a feasible positive-gain target may move with gain 0 to a
+ *   block t with room and w(t) + c(u) < w(Pi(u)) (the lightest such block, then the smaller id).
+ *   revert of negative attributed gains (Sec. 5.2, Sec. 6): the attributed gain of a move is
+ *   read as its gain when the sub-round's approved moves are performed one at a time in
+ *   ascending vertex id (each net then sees its moves in that order, and crediting +omega(e)
+ *   to the move that takes Phi(e, from) to 0 and -omega(e) to the one that takes Phi(e, to)
+ *   to 1 gives exactly this gain).  After the sub-round, every move whose attributed gain is
+ *   negative is undone.  A reverted move still counts as a move for eligibility.
  *
  * Build: gcc -O2 -shared -fPIC -o liboracle.so hgp_oracle.c
  */
@@ -66,11 +75,14 @@ typedef struct {
     int64_t *cand_g;       /* [n]  its gain */
     uint8_t *approved;     /* [n]  */
     int32_t *order;        /* [n]  */
+    int32_t *from;         /* [n]  block an approved vertex left */
+    int64_t *attr;         /* [n]  attributed gain of an approved move */
 } oracle_t;
 
 /* Per-round statistics, in this order: objective after the round, number of candidates,
- * number of approved moves, number of eligible vertices, heaviest block weight. */
-enum { ST_OBJ = 0, ST_CAND, ST_APPROVED, ST_ELIGIBLE, ST_MAXW, ST_COUNT };
+ * number of approved moves, number of eligible vertices, heaviest block weight, number of
+ * reverted moves. */
+enum { ST_OBJ = 0, ST_CAND, ST_APPROVED, ST_ELIGIBLE, ST_MAXW, ST_REVERTED, ST_COUNT };
 
 int64_t oracle_lmax(int64_t total_weight, int32_t k, double eps)
 {
@@ -112,6 +124,7 @@ void oracle_destroy(oracle_t *o)
     free(o->net_off); free(o->pins); free(o->vw); free(o->nw); free(o->vtx_off);
     free(o->inc); free(o->part); free(o->phi); free(o->bw); free(o->moved_prev);
     free(o->moved_cur); free(o->cand_t); free(o->cand_g); free(o->approved); free(o->order);
+    free(o->from); free(o->attr);
     free(o);
 }
 
@@ -141,9 +154,11 @@ oracle_t *oracle_create(int32_t n, int32_t m, const int64_t *net_off, const int3
     o->cand_g = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
     o->approved = (uint8_t *)calloc((size_t)n + 1, 1);
     o->order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    o->from = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    o->attr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
     if (!o->net_off || !o->pins || !o->vw || !o->nw || !o->vtx_off || !o->inc || !o->part ||
         !o->phi || !o->bw || !o->moved_prev || !o->moved_cur || !o->cand_t || !o->cand_g ||
-        !o->approved || !o->order) {
+        !o->approved || !o->order || !o->from || !o->attr) {
         oracle_destroy(o);
         return NULL;
     }
@@ -257,6 +272,21 @@ void oracle_candidates(const oracle_t *o, int32_t s, int32_t *target, int64_t *g
     }
 }
 
+/* Moves u from its block to t: partition, block weights, Phi, and the moved-net marks. */
+static void move_vertex(oracle_t *o, int32_t u, int32_t t)
+{
+    const int32_t a = o->part[u], k = o->k;
+    o->part[u] = t;
+    o->bw[a] -= o->vw[u];
+    o->bw[t] += o->vw[u];
+    for (int64_t j = o->vtx_off[u]; j < o->vtx_off[u + 1]; ++j) {
+        const int32_t e = o->inc[j];
+        o->phi[(int64_t)e * k + a]--;
+        o->phi[(int64_t)e * k + t]++;
+        o->moved_cur[e] = 1;
+    }
+}
+
 /* Runs `rounds` synchronous LP rounds.  stats: NULL or [rounds * ST_COUNT].
  * moves: NULL or [max_moves * 4] receiving (global sub-round index, u, from, to) for each
  * applied move in application order; *num_moves receives the count (may exceed max_moves,
@@ -268,7 +298,7 @@ int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
     int64_t logged = 0;
     for (int32_t rr = 0; rr < rounds; ++rr) {
         const int64_t r = o->round;
-        int64_t n_cand = 0, n_appr = 0, n_elig = 0;
+        int64_t n_cand = 0, n_appr = 0, n_elig = 0, n_rev = 0;
         memset(o->moved_cur, 0, (size_t)m);
         /* eligibility is fixed for the whole round: it depends only on the previous round */
         uint8_t *elig_copy = (uint8_t *)malloc((size_t)n + 1);
@@ -298,25 +328,36 @@ int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
                     if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;
                 }
             }
-            /* (3) apply every approved move (ascending vertex id) */
+            /* (3) apply every approved move (ascending vertex id); with the revert variant,
+             * the attributed gain of each is its gain just before it is performed */
             for (int32_t u = 0; u < n; ++u) {
                 if (!o->approved[u]) continue;
                 int32_t a = o->part[u], t = o->cand_t[u];
-                o->part[u] = t;
-                o->bw[a] -= o->vw[u];
-                o->bw[t] += o->vw[u];
-                for (int64_t j = o->vtx_off[u]; j < o->vtx_off[u + 1]; ++j) {
-                    int32_t e = o->inc[j];
-                    o->phi[(int64_t)e * k + a]--;
-                    o->phi[(int64_t)e * k + t]++;
-                    o->moved_cur[e] = 1;
+                if (o->revert_negative) {
+                    o->from[u] = a;
+                    o->attr[u] = oracle_gain(o, u, t);
                 }
+                move_vertex(o, u, t);
                 if (moves && logged < max_moves) {
                     int64_t *mv = moves + 4 * logged;
                     mv[0] = r * S + s; mv[1] = u; mv[2] = a; mv[3] = t;
                 }
                 logged++;
                 n_appr++;
+            }
+            /* (4) revert variant: undo every move with a negative attributed gain */
+            if (o->revert_negative) {
+                for (int32_t u = 0; u < n; ++u) {
+                    if (!o->approved[u] || o->attr[u] >= 0) continue;
+                    const int32_t t = o->part[u], a = o->from[u];
+                    move_vertex(o, u, a);
+                    if (moves && logged < max_moves) {
+                        int64_t *mv = moves + 4 * logged;
+                        mv[0] = r * S + s; mv[1] = u; mv[2] = t; mv[3] = a;
+                    }
+                    logged++;
+                    n_rev++;
+                }
             }
         }
         free(elig_copy);
@@ -332,6 +373,7 @@ int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
             st[ST_APPROVED] = n_appr;
             st[ST_ELIGIBLE] = n_elig;
             st[ST_MAXW] = maxw;
+            st[ST_REVERTED] = n_rev;
         }
     }
     if (num_moves) *num_moves = logged;

@@ -99,11 +99,15 @@ class Tiny:
 
 
 def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round: int = 0,
-              moved_prev: Optional[set] = None, balance_moves: bool = False):
+              moved_prev: Optional[set] = None, balance_moves: bool = False,
+              revert_negative: bool = False, reverted: Optional[list] = None):
     """Synchronous LP rounds with definitional gains.  Returns (part, per-round stats,
     move log [(global sub-round, u, from, to)], moved set of the last round).
 
-    Stats per round: (objective, candidates, approved, eligible, max block weight)."""
+    Stats per round: (objective, candidates, approved, eligible, max block weight).
+    revert_negative: each approved move is performed in ascending vertex id and its
+    attributed gain is the objective it removes at that moment; after the sub-round the moves
+    with a negative one go back (logged as reverse moves); per-round counts go to `reverted`."""
     part = [int(x) for x in part]
     lmax = t.lmax()
     stats, log = [], []
@@ -120,7 +124,7 @@ def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round
                 if t.inc[v]:
                     elig |= t.neighbours(v)
         moved_now = set()
-        n_cand = n_appr = 0
+        n_cand = n_appr = n_rev = 0
         for s in range(S):
             w = t.block_weights(part)
             cands: Dict[int, tuple] = {}
@@ -152,12 +156,22 @@ def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round
                     acc += t.vw[u]
                     if w[blk] + acc <= lmax:
                         approved.append(u)
+            attr = {}
             for u in sorted(approved):
                 log.append((r * S + s, u, part[u], cands[u][0]))
+                attr[u] = (t.gain(part, u, cands[u][0]), part[u])
                 part[u] = cands[u][0]
                 moved_now.add(u)
             n_appr += len(approved)
+            if revert_negative:
+                for u in sorted(approved):
+                    if attr[u][0] < 0:
+                        log.append((r * S + s, u, part[u], attr[u][1]))
+                        part[u] = attr[u][1]
+                        n_rev += 1
         stats.append((t.objective(part), n_cand, n_appr, len(elig), max(t.block_weights(part))))
+        if reverted is not None:
+            reverted.append(n_rev)
         moved_prev = moved_now
         all_elig = False
     return part, stats, log, moved_prev

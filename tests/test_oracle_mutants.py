@@ -33,8 +33,8 @@ MUTANTS = [
     ("approval id descending", "return (u > v) - (u < v);", "return (u < v) - (u > v);"),
     ("exclusive prefix", "acc += o->vw[u];\n                    if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;",
      "if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;\n                    acc += o->vw[u];"),
-    ("Phi update swapped", "o->phi[(int64_t)e * k + a]--;\n                    o->phi[(int64_t)e * k + t]++;",
-     "o->phi[(int64_t)e * k + a]++;\n                    o->phi[(int64_t)e * k + t]--;"),
+    ("Phi update swapped", "o->phi[(int64_t)e * k + a]--;\n        o->phi[(int64_t)e * k + t]++;",
+     "o->phi[(int64_t)e * k + a]++;\n        o->phi[(int64_t)e * k + t]--;"),
     ("block weight sign", "o->bw[a] -= o->vw[u];", "o->bw[a] += o->vw[u];"),
     ("always eligible", "if (o->all_eligible) return 1;", "return 1;"),
     ("never eligible after round 0", "if (o->moved_prev[o->inc[j]]) return 1;", "(void)j;"),
@@ -46,6 +46,13 @@ MUTANTS = [
     ("hash shift", "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;", "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;"),
     ("hash round/vertex swapped", "seed ^ (((uint64_t)round << 32) | (uint64_t)(uint32_t)u)",
      "seed ^ (((uint64_t)u << 32) | (uint64_t)(uint32_t)round)"),
+    ("balance move to the heaviest block", "if (best_t < 0 || o->bw[i] < o->bw[best_t]) best_t = i;",
+     "if (best_t < 0 || o->bw[i] > o->bw[best_t]) best_t = i;"),
+    ("balance move keeps equal weights", "wi >= o->bw[a]", "wi > o->bw[a]"),
+    ("balance move without room check", "if (wi > o->lmax || wi >= o->bw[a]", "if (wi >= o->bw[a]"),
+    ("attributed gain from the frozen state", "o->attr[u] = oracle_gain(o, u, t);", "o->attr[u] = o->cand_g[u];"),
+    ("revert of zero gains too", "if (!o->approved[u] || o->attr[u] >= 0) continue;",
+     "if (!o->approved[u] || o->attr[u] > 0) continue;"),
     ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
      "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
 ]

@@ -288,10 +288,9 @@ def test_balance_moves_match_bruteforce(seed):
 
 
 def test_balance_moves_hand_example():
-    # Nets {0,1} and {2,3}; all four vertices in block 0 (k=2, eps=0.5, L_max = 3 > w... no:
-    # c(V) = 4, ceil(4/2) = 2, L_max = floor(1.5 * 2) = 3).  Every move has gain -1 except none
-    # with positive gain; vertex 0 -> block 1 has gain -1 (net {0,1} becomes cut), so no
-    # zero-gain move exists and nothing moves even with the variant.
+    # Nets {0,1} and {2,3}, all four vertices in block 0 (k = 2, eps = 0.5, c(V) = 4,
+    # L_max = floor(1.5 * 2) = 3).  Every move cuts a net (gain -1), so there is neither a
+    # positive- nor a zero-gain move, and nothing moves even with the variant.
     t = Tiny(4, [[0, 1], [2, 3]], 2, 0.5)
     o = make_oracle(t, [0, 0, 0, 0], S=1)
     o2 = oracle.Oracle(4, 2, *t.csr(), 2, 0.5, np.zeros(4, np.int32), None, None, 1, 0,
@@ -305,4 +304,98 @@ def test_balance_moves_hand_example():
     st, mv = o3.refine(1, log_moves=True)
     assert [tuple(x) for x in mv.tolist()] == [(0, 4, 0, 1)]
     assert st[0, 0] == 0 and st[0, 2] == 1
-    del o
+
+
+def test_balance_moves_need_room():
+    # k = 3, eps = 0, c(V) = 9, L_max = 3; blocks 0 = {0..4} (w 5), 1 = {5,6,7} (w 3),
+    # 2 = {8} (w 1); one net {0, 1, 5}.  Vertices 0 and 1 have gain 0 to block 1 (Phi(e,0) = 2,
+    # Phi(e,1) = 1) and 1 + 3 < 5, but block 1 has no room, and their gain to block 2 is -1:
+    # no candidate.  Vertex 5 has gain +1 to the full block 0 and gain 0 to block 2 (1 + 1 < 3):
+    # a balance candidate, like the isolated 2, 3, 4 (block 0) and 6, 7 (block 1), all for
+    # block 2.  Block 2 has room for two: ids 2 and 3 (all gains 0).
+    t = Tiny(9, [[0, 1, 5]], 3, 0.0)
+    part = [0, 0, 0, 0, 0, 1, 1, 1, 2]
+    assert t.lmax() == 3
+    o = oracle.Oracle(9, 1, *t.csr(), 3, 0.0, np.array(part, np.int32), None, None, 1, 0,
+                      balance_moves=True)
+    st, mv = o.refine(1, log_moves=True)
+    assert st[0].tolist() == [1, 6, 2, 9, 3]
+    assert [tuple(x) for x in mv.tolist()] == [(0, 2, 0, 2), (0, 3, 0, 2)]
+    _, want_stats, want_log, _ = lp_rounds(t, part, 1, S=1, balance_moves=True)
+    assert want_stats == [(1, 6, 2, 9, 3)] and want_log == [(0, 2, 0, 2), (0, 3, 0, 2)]
+
+
+# --- variant: revert of negative attributed gains (Sec. 5.2, Sec. 6) -----------------------
+
+@pytest.mark.parametrize("seed", range(10))
+def test_revert_matches_bruteforce(seed):
+    rng = np.random.default_rng(950 + seed)
+    k = int(rng.integers(2, 5))
+    S = int(rng.integers(1, 3))
+    t = random_tiny(rng, 14, 14, k, max_size=4, weighted=seed % 2 == 0, eps=0.6)
+    part = rng.integers(0, k, size=t.n)
+    off, pins = t.csr()
+    vw = None if all(x == 1 for x in t.vw) else np.array(t.vw, dtype=np.int32)
+    nw = None if all(x == 1 for x in t.nw) else np.array(t.nw, dtype=np.int32)
+    balance = seed % 3 == 0
+    o = oracle.Oracle(t.n, t.m, off, pins, k, t.eps, part.astype(np.int32), vw, nw, S, seed,
+                      balance_moves=balance, revert_negative=True)
+    stats, moves = o.refine(4, log_moves=True)
+    rev = []
+    want_part, want_stats, want_log, _ = lp_rounds(t, part, 4, S=S, seed=seed, balance_moves=balance,
+                                                   revert_negative=True, reverted=rev)
+    assert [tuple(r) for r in stats.tolist()] == want_stats
+    assert [tuple(m) for m in moves.tolist()] == want_log
+    assert o.reverted.tolist() == rev
+    np.testing.assert_array_equal(o.partition(), want_part)
+
+
+def test_revert_happens_on_random_tiny():
+    # the brute-force comparison above must include sub-rounds with reverts
+    total = 0
+    for seed in range(40):
+        rng = np.random.default_rng(3000 + seed)
+        t = random_tiny(rng, 12, 12, 2, max_size=3, eps=0.6)
+        rev = []
+        lp_rounds(t, rng.integers(0, 2, size=t.n), 2, S=1, seed=seed, revert_negative=True, reverted=rev)
+        total += sum(rev)
+    assert total > 0
+
+
+def test_revert_hand_example_swap():
+    # Net {0,1} of weight 5 with vertex 0 in block 0 and vertex 1 in block 1; vertices 2 and
+    # 3 are isolated padding (c(V) = 4, L_max = floor(1.5 * 2) = 3).  Both 0 -> 1 and 1 -> 0
+    # have gain 5 against the frozen state and both fit, so both are approved (S = 1).  In id
+    # order, 0 -> 1 first removes the cut (+5); then 1 -> 0 cuts the net again (-5), so the
+    # move of vertex 1 is reverted: the net ends up uncut in block 1 (weight 3 = L_max).
+    t = Tiny(4, [[0, 1]], 2, 0.5, None, [5])
+    part = [0, 1, 0, 1]
+    plain = make_oracle(t, part, S=1)
+    st_plain, _ = plain.refine(1)
+    assert st_plain[0].tolist() == [5, 2, 2, 4, 2]             # the swap keeps the cut
+    o = oracle.Oracle(4, 1, *t.csr(), 2, 0.5, np.array(part, np.int32), None,
+                      np.array([5], np.int32), 1, 0, revert_negative=True)
+    st, mv = o.refine(1, log_moves=True)
+    assert st[0].tolist() == [0, 2, 2, 4, 3]
+    assert o.reverted.tolist() == [1]
+    assert [tuple(x) for x in mv.tolist()] == [(0, 0, 0, 1), (0, 1, 1, 0), (0, 1, 0, 1)]
+    assert o.partition().tolist() == [1, 1, 0, 1]
+    # eligibility: the reverted vertex counts as moved, so round 1 sees all vertices of the net
+    st1, _ = o.refine(1)
+    assert st1[0, 3] == 2
+
+
+def test_revert_attributed_gains_sum_to_objective_change():
+    # Sec. 5.2: the attributed gains of a sub-round's moves add up to the objective it removed;
+    # here the attributed gains are the exact gains of the id-ordered sequence (Sec. 5.4)
+    rng = np.random.default_rng(77)
+    for seed in range(6):
+        t = random_tiny(rng, 16, 14, 3, max_size=4, weighted=True, eps=0.6)
+        part = rng.integers(0, 3, size=t.n)
+        o = make_oracle(t, part, S=1)
+        before = o.objective()
+        _, log = o.refine(1, log_moves=True)
+        if len(log) == 0:
+            continue
+        gains = make_oracle(t, part, S=1).exact_gains(log[:, 1:4])
+        assert int(gains.sum()) == before - o.objective()
