@@ -73,9 +73,13 @@ typedef struct {
     int32_t balance_moves;   /* variant (Sec. 6): a vertex without a feasible positive-gain
                                 target may take a zero-gain move to a block t with room and
                                 w(t) + c(u) < w(Pi(u)), the lightest such block [0] */
-    int32_t revert_negative; /* variant (Sec. 6, attributed gains): after each sub-round, the
-                                applied moves' exact gains in vertex-id order (Sec. 5.4) are
-                                computed and every move with a negative one is undone [0] */
+    int32_t revert_negative; /* variant (Sec. 5.2, Sec. 6): the attributed gain of each applied
+                                move is its gain with every net seeing the sub-round's moves in
+                                ascending vertex id (computed by Lemma 1, Sec. 5.4); after the
+                                sub-round every move with a negative one is undone, and still
+                                counts as a move for eligibility.  Adds a table of 32 * 2^ceil(
+                                log2(2P)) bytes and n bytes.  Single handles only (a batch
+                                rejects it) [0] */
 } hgp_options;
 
 /* Per-round statistics written by hgp_refine. */
@@ -86,6 +90,7 @@ typedef struct {
     int64_t eligible;         /* eligible vertices in the round */
     int64_t max_block_weight; /* max_i c(V_i) after the round */
     int64_t moved_pins;       /* sum of d(u) over the vertices moved in the round */
+    int64_t reverted;         /* moves undone by the revert variant in the round */
 } hgp_round_stats;
 
 /* Device time per phase of the rounds, from CUDA events recorded on the handle's stream
@@ -209,7 +214,8 @@ typedef struct {
 
 void hgp_batch_default_options(hgp_batch_options *opt);
 
-/* handles: host array of `count` distinct handles on the current device. */
+/* handles: host array of `count` distinct handles on the current device.  Returns
+ * HGP_ERR_UNSUPPORTED for a handle created with the revert variant. */
 int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_options *opt,
                      hgp_batch **out);
 

@@ -23,6 +23,7 @@ namespace hgp {
 
 constexpr int kRange = 256;              // consecutive vertices handled by one warp
 constexpr int kWarps = 8;                // warps per tile CTA
+constexpr int kRvSlotBytes = 32;         // one slot of the revert variant's hash table
 constexpr int kTile = kRange * kWarps;   // vertices per tile (one CTA)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kBins = 4096;              // approval histogram bins (gains 1..4094 exact)
@@ -62,8 +63,8 @@ struct Sel {
 };
 
 enum { SEL_ALL = 0, SEL_THRESH = 1, SEL_REFINE = 2 };
-enum { ST_OBJ = 0, ST_CAND = 1, ST_APPR = 2, ST_ELIG = 3, ST_MAXW = 4, ST_MOVED = 5, ST_N = 6 };
-enum { ERR_INVALID = 1, ERR_UNSUPPORTED = 2 };
+enum { ST_OBJ = 0, ST_CAND = 1, ST_APPR = 2, ST_ELIG = 3, ST_MAXW = 4, ST_MOVED = 5, ST_REV = 6, ST_N = 7 };
+enum { ERR_INVALID = 1, ERR_UNSUPPORTED = 2, ERR_TABLE = 4 };
 
 struct Dev {
     int32_t n, m, k, P;
@@ -100,6 +101,12 @@ struct Dev {
     int32_t pad0;
     int32_t *rs;            // round state on the device: rs[0] = next round r, rs[1] = 0 while
                             // every vertex is eligible (first round), 1 afterwards
+    // revert variant only (nullptr otherwise)
+    uint8_t *rv_src;        // [n_ranges * kRange] per candidate slot: block an approved move left,
+                            // | 0x80 when it is to be undone; 0xFF when not approved
+    void *rv_tab;           // hash table of (net, block) order statistics of the sub-round's moves
+    int64_t rv_cap;         // its capacity in slots (a power of two >= 2 P)
+    unsigned long long *rv_cnt;  // [1] incidences of the vertices moved in the current sub-round
 };
 
 __device__ __forceinline__ int lam_bits_ctz(uint32_t x) { return __ffs(x) - 1; }

@@ -897,6 +897,8 @@ __global__ void __launch_bounds__(1024) k_tie_scan(const Dev *devs, const int2 *
 }
 
 // ------------------------------------------------------------------ apply
+constexpr uint8_t kRvNone = 0xFF, kRvBack = 0x80;   // revert variant: per candidate slot marks
+
 struct alignas(16) ApplyWarp {
     int32_t off[33];
     int32_t jb[32];
@@ -1077,6 +1079,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
             ++iappr;
             ipins += deg;
         }
+        if (d.rv_src && idx < ncand) d.rv_src[(int64_t)range * kRange + idx] = appr ? (uint8_t)a : kRvNone;
         int32_t incl = deg;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1149,6 +1152,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 if (idobj) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)idobj);
                 if (iappr) atomicAdd(row + ST_APPR, (unsigned long long)iappr);
                 if (ipins) atomicAdd(row + ST_MOVED, (unsigned long long)ipins);
+                if (ipins && d.rv_cnt) atomicAdd(d.rv_cnt, (unsigned long long)ipins);
             }
             __syncwarp();
         } else {
@@ -1200,8 +1204,231 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 if (o1) atomicAdd(reinterpret_cast<unsigned long long *>(d0.obj), o1);
                 if (a1) atomicAdd(row + ST_APPR, a1);
                 if (p1) atomicAdd(row + ST_MOVED, p1);
+                if (p1 && d0.rv_cnt) atomicAdd(d0.rv_cnt, p1);
             }
         }
+    }
+}
+
+// ------------------------------------------------------------------ revert variant
+// Attributed gains (Sec. 5.2) of a sub-round's approved moves, with every net seeing its moves
+// in ascending vertex id: the gain of u (a -> b) if the moves of smaller ids had been made
+// first.  Lemma 1 (Sec. 5.4) gives it from order statistics of the moves that touch (e, i),
+// with the vertex id as the position in the sequence:
+//     +omega(e)  iff  Psi(e, a) = 0, u = max out(e, a), min in(e, a) > u
+//     -omega(e)  iff  Psi(e, b) = 0, u = min in(e, b),  max out(e, b) < u
+// where Psi(e, i) is the number of pins of e that were in block i at the start of the sub-round
+// and stayed: Phi(e, i) after the moves minus |in(e, i)|.  Pass 1 records max out, min in and
+// |in| per touched (e, i) in an open-addressing table sized to the sub-round's moved
+// incidences; pass 2 sums the terms per move and marks the moves whose sum is negative; the
+// revert step moves those back (Sec. 6).  Balance holds after it: each block's approval was
+// checked against its weight at the start of the sub-round, without credit for departures.
+struct alignas(16) RvSlot {
+    unsigned long long key;   // e * 64 + i, kRvEmpty when free
+    int32_t max_out;          // largest id of a mover that left block i (a pin of e), -1 if none
+    int32_t min_in;           // smallest id of a mover that entered block i, INT32_MAX if none
+    int32_t n_in;             // number of movers that entered block i
+    int32_t pad[3];
+};
+static_assert(sizeof(RvSlot) == kRvSlotBytes, "revert table slot size");
+constexpr unsigned long long kRvEmpty = ~0ull;
+
+// slots in use this sub-round: a power of two >= 4 x moved incidences (>= 2 x keys), at most
+// the capacity (>= 2 P >= keys, so a free slot always exists)
+__device__ __forceinline__ uint64_t rv_slots(const Dev &d)
+{
+    const uint64_t need = 4ull * __ldcg(d.rv_cnt);
+    uint64_t c = 1024;
+    while (c < need && c < (uint64_t)d.rv_cap) c <<= 1;
+    return c;
+}
+
+// find (or insert) key by linear probing; at most `mask + 1` probes
+__device__ __forceinline__ RvSlot *rv_find(RvSlot *tab, uint64_t mask, unsigned long long key, bool insert)
+{
+    uint64_t p = splitmix64_output(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        RvSlot *sl = tab + p;
+        unsigned long long cur = __ldcg(&sl->key);
+        if (cur == key) return sl;
+        if (cur == kRvEmpty) {
+            if (!insert) return nullptr;
+            cur = atomicCAS(&sl->key, kRvEmpty, key);
+            if (cur == kRvEmpty || cur == key) return sl;
+        }
+        p = (p + 1) & mask;
+    }
+    return nullptr;
+}
+
+__global__ void k_rv_clear(const Dev d)
+{
+    const uint64_t n = rv_slots(d);
+    RvSlot *tab = reinterpret_cast<RvSlot *>(d.rv_tab);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        RvSlot sl;
+        sl.key = kRvEmpty;
+        sl.max_out = -1;
+        sl.min_in = 0x7fffffff;
+        sl.n_in = 0;
+        sl.pad[0] = sl.pad[1] = sl.pad[2] = 0;
+        tab[i] = sl;
+    }
+}
+
+struct alignas(16) RvWarp {
+    ApplyWarp w;
+    int32_t u[32];
+    int32_t g[32];
+};
+
+// Warp per range: the approved movers of each 32 candidates, their incidences flattened over
+// the lanes.  PASS 1 records the order statistics, PASS 2 sums each mover's attributed gain.
+template <typename Rec, int PASS>
+__global__ void __launch_bounds__(kThreads) k_rv_pass(const Dev d)
+{
+    __shared__ RvWarp rw_[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t range = blockIdx.x * kWarps + wid;
+    if (range >= d.n_ranges) return;
+    const int32_t ncand = d.cand_cnt[range];
+    if (ncand == 0) return;
+    RvWarp &rw = rw_[wid];
+    const uint64_t mask = rv_slots(d) - 1;
+    RvSlot *tab = reinterpret_cast<RvSlot *>(d.rv_tab);
+    const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
+    const uint64_t *cand = d.cand + (int64_t)range * kRange;
+    uint8_t *src = d.rv_src + (int64_t)range * kRange;
+    bool lost = false;
+    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+        const int idx = c0 + lane;
+        int32_t deg = 0, jb = 0, u = 0;
+        int t = 0, a = 0;
+        const uint8_t sa = idx < ncand ? src[idx] : kRvNone;
+        if (sa != kRvNone) {
+            int ul;
+            int32_t g;
+            decode(cand[idx], t, g, ul);
+            u = range * kRange + ul;
+            a = sa;
+            jb = d.vtx_off[u];
+            deg = d.vtx_off[u + 1] - jb;
+        }
+        int32_t incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t total = __shfl_sync(kFull, incl, 31);
+        rw.w.off[lane] = incl - deg;
+        rw.w.jb[lane] = jb;
+        rw.w.a[lane] = a;
+        rw.w.t[lane] = t;
+        rw.u[lane] = u;
+        rw.g[lane] = 0;
+        if (lane == 31) rw.w.off[32] = total;
+        __syncwarp();
+        for (int32_t i = lane; i < total; i += 32) {
+            const int v = slot_of(rw.w.off, i);
+            const int32_t e = d.inc[rw.w.jb[v] + (i - rw.w.off[v])];
+            const int32_t ee = e & kNetMask;
+            const int32_t av = rw.w.a[v], bv = rw.w.t[v], uv = rw.u[v];
+            const unsigned long long ka = (unsigned long long)ee * 64 + av, kb = (unsigned long long)ee * 64 + bv;
+            RvSlot *s_a = rv_find(tab, mask, ka, PASS == 1);
+            RvSlot *s_b = rv_find(tab, mask, kb, PASS == 1);
+            if (!s_a || !s_b) {
+                lost = true;
+                continue;
+            }
+            if (PASS == 1) {
+                atomicMax(&s_a->max_out, uv);
+                atomicMin(&s_b->min_in, uv);
+                atomicAdd(&s_b->n_in, 1);
+            } else {
+                const bool wide = e < 0;
+                const int32_t wrow = wide ? d.widx[ee] : 0;
+                const int32_t pa = phi_get(d, ee, av, wide, wrow), pb = phi_get(d, ee, bv, wide, wrow);
+                const int32_t w = __ldg(&recs[ee].w) & 0x7fffffff;
+                int32_t g = 0;
+                if (pa == s_a->n_in && s_a->max_out == uv && s_a->min_in > uv) g += w;
+                if (pb == s_b->n_in && s_b->min_in == uv && s_b->max_out < uv) g -= w;
+                if (g) atomicAdd(&rw.g[v], g);
+            }
+        }
+        __syncwarp();
+        if (PASS == 2 && sa != kRvNone && rw.g[lane] < 0) src[idx] = (uint8_t)(sa | kRvBack);
+        __syncwarp();
+    }
+    if (lost) atomicOr(d.err, ERR_TABLE);
+}
+
+// Warp per range: the marked moves go back to their source blocks (Phi, Lambda, S1, block
+// weights, objective as in the apply step; the nets keep their round-r stamps).  Resets the
+// sub-round's moved-incidence count for the next sub-round.
+template <typename Rec>
+__global__ void __launch_bounds__(kThreads) k_rv_revert(const Dev d, int32_t rr)
+{
+    __shared__ ApplyWarp aw[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t range = blockIdx.x * kWarps + wid;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d.rv_cnt = 0;
+    if (range >= d.n_ranges) return;
+    const int32_t ncand = d.cand_cnt[range];
+    if (ncand == 0) return;
+    const uint8_t *src = d.rv_src + (int64_t)range * kRange;
+    const uint64_t *cand = d.cand + (int64_t)range * kRange;
+    Rec *recs = reinterpret_cast<Rec *>(d.rec);
+    const int32_t r = d.rs[0];
+    long long dobj = 0;
+    int32_t nrev = 0;
+    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+        const int idx = c0 + lane;
+        const uint8_t sa = idx < ncand ? src[idx] : kRvNone;
+        const bool back = sa != kRvNone && (sa & kRvBack);
+        if (!__any_sync(kFull, back)) continue;
+        int32_t deg = 0, jb = 0;
+        int t = 0, a = 0;
+        if (back) {
+            int ul;
+            int32_t g;
+            decode(cand[idx], t, g, ul);
+            const int32_t u = range * kRange + ul;
+            a = sa & 0x3F;
+            d.part[u] = (uint8_t)a;
+            const long long cw = d.vw ? d.vw[u] : 1;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[t]), (unsigned long long)(-cw));
+            atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[a]), (unsigned long long)cw);
+            jb = d.vtx_off[u];
+            deg = d.vtx_off[u + 1] - jb;
+            ++nrev;
+        }
+        int32_t incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t total = __shfl_sync(kFull, incl, 31);
+        aw[wid].off[lane] = incl - deg;
+        aw[wid].jb[lane] = jb;
+        aw[wid].a[lane] = t;     // the move back leaves the target block ...
+        aw[wid].t[lane] = a;     // ... for the source block
+        if (lane == 31) aw[wid].off[32] = total;
+        __syncwarp();
+        for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
+            dobj += apply_pins<Rec>(d, recs, aw[wid], i0 + lane, total, r);
+        __syncwarp();
+    }
+    for (int o = 16; o; o >>= 1) {
+        dobj += __shfl_xor_sync(kFull, dobj, o);
+        nrev += __shfl_xor_sync(kFull, nrev, o);
+    }
+    if (lane == 0) {
+        if (dobj) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)dobj);
+        if (nrev) atomicAdd(reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N + ST_REV),
+                            (unsigned long long)nrev);
     }
 }
 
@@ -1247,6 +1474,7 @@ struct Plan {
     int32_t S_max = 0;
     bool levels = false;   // some instance can have gains >= kBins - 1
     bool rec32 = false;
+    bool revert = false;   // revert variant (single instance only)
     int grid_gain = 0, grid_apply = 0;
     cudaStream_t st = nullptr;
     int64_t *launches = nullptr;
@@ -1392,8 +1620,24 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
         else k_apply<Rec16, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
         *p.launches += 1;
+        int32_t n_apply = 1;
+        if (p.revert) {
+            const unsigned g = warp_grid(p.n_ranges);
+            k_rv_clear<<<p.grid_apply * 4, kThreads, 0, p.st>>>(p.d0);
+            if (p.rec32) {
+                k_rv_pass<Rec32, 1><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec32, 2><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_revert<Rec32><<<g, kThreads, 0, p.st>>>(p.d0, rr);
+            } else {
+                k_rv_pass<Rec16, 1><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec16, 2><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_revert<Rec16><<<g, kThreads, 0, p.st>>>(p.d0, rr);
+            }
+            *p.launches += 4;
+            n_apply += 4;
+        }
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, 1);
+        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, n_apply);
     }
     if (e == cudaSuccess) e = phase_begin(p.prof);
     if (e == cudaSuccess) {
@@ -1432,6 +1676,7 @@ Plan single_plan(hgp_handle *h)
     p.S_max = h->d.S;
     p.levels = h->max_vertex_netweight >= kBins - 1;
     p.rec32 = h->d.k > 32;
+    p.revert = h->d.rv_src != nullptr;
     if (!h->grid_gain) {
         Plan q = p;
         set_grids(q, h->device);
@@ -1503,6 +1748,7 @@ static int copy_stats_out(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
             stats[rr].eligible = row[ST_ELIG];
             stats[rr].max_block_weight = row[ST_MAXW];
             stats[rr].moved_pins = row[ST_MOVED];
+            stats[rr].reverted = row[ST_REV];
         }
     }
     return HGP_OK;
@@ -1777,6 +2023,7 @@ int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_
     cudaGetDevice(&dev);
     for (int32_t i = 0; i < count; ++i) {
         if (!handles[i] || handles[i]->device != dev) return HGP_ERR_INVALID;
+        if (handles[i]->d.rv_src) return HGP_ERR_UNSUPPORTED;   // revert variant: single instances only
         for (int32_t j = 0; j < i; ++j)
             if (handles[j] == handles[i]) return HGP_ERR_INVALID;
     }
@@ -1878,6 +2125,7 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
                 o.eligible = row[ST_ELIG];
                 o.max_block_weight = row[ST_MAXW];
                 o.moved_pins = row[ST_MOVED];
+                o.reverted = row[ST_REV];
             }
     }
     return HGP_OK;

@@ -655,6 +655,21 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.hist = hist;
     d.sel = sel;
     d.tie = tie;
+    if (o.revert_negative) {
+        // per candidate slot source blocks, and a table with room for the two (net, block)
+        // keys of every incidence of a sub-round's movers (at most 2 P keys)
+        uint8_t *rv_src = nullptr;
+        unsigned long long *rv_cnt = nullptr;
+        int64_t cap = 1024;
+        while (cap < 2 * (int64_t)P) cap <<= 1;
+        CKF(dalloc(h, &rv_src, (int64_t)d.n_ranges * kRange));
+        CKF(dalloc(h, &rv_cnt, 1));
+        CKF(dalloc(h, reinterpret_cast<uint4 **>(&d.rv_tab), cap * kRvSlotBytes / 16));
+        CKF(cudaMemsetAsync(rv_cnt, 0, sizeof(unsigned long long), st));
+        d.rv_src = rv_src;
+        d.rv_cnt = rv_cnt;
+        d.rv_cap = cap;
+    }
     CKF(dalloc(h, &h->d_round, 4));
     d.rs = h->d_round;
     d.seed = o.seed;

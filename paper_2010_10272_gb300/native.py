@@ -17,7 +17,8 @@ _LIB_PATH = os.path.join(_HERE, "libhgp.so")
 _lock = threading.Lock()
 _lib = None
 
-STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight", "moved_pins")
+STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight", "moved_pins",
+               "reverted")
 PHASES = ("sublists", "gain", "approval", "apply", "round_end")
 
 HGP_OK = 0
@@ -218,7 +219,7 @@ class HGP:
 
     # -- refinement
     def refine(self, rounds: int, stats: bool = True):
-        """Runs `rounds` LP rounds; returns int64 [rounds x 6] statistics (STAT_FIELDS) or None."""
+        """Runs `rounds` LP rounds; returns int64 [rounds x 7] statistics (STAT_FIELDS) or None."""
         if stats:
             buf = (RoundStats * max(1, rounds))()
             _check(self._lib.hgp_refine(self._h, int(rounds), buf), "hgp_refine")

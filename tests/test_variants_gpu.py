@@ -2,6 +2,8 @@
 
 * balance moves: a vertex without a feasible positive-gain target may take a zero-gain move
   to the lightest block t with room and w(t) + c(u) < w(Pi(u)).
+* revert: after each sub-round, the moves whose attributed gain (every net seeing the moves
+  in ascending vertex id, Sec. 5.2 / Lemma 1) is negative are undone.
 """
 import numpy as np
 import pytest
@@ -9,7 +11,7 @@ import pytest
 import oracle
 import synth
 from paper_2010_10272_gb300 import HGP
-from parity_util import run_both
+from parity_util import compare_state, run_both
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -84,3 +86,75 @@ def test_balance_moves_powerlaw_scaled():
     part = hg.part.copy()
     part[: hg.n // 4] = 0
     run_both(hg, rounds=3, S=4, part=part, check_phi=False, balance_moves=True)
+
+
+# ---------------------------------------------------------------- revert of negative moves
+REVERT_CASES = [
+    # (seed, n, m, k, max_size, weighted, S, phi_width, eps)
+    (1, 5000, 3000, 2, 4, False, 1, 0, 0.03),
+    (2, 7001, 5000, 3, 6, True, 1, 0, 0.05),
+    (3, 6143, 4000, 8, 5, False, 2, 0, 0.03),
+    (4, 9999, 8000, 16, 10, True, 4, 2, 0.1),
+    (5, 4097, 2000, 32, 4, False, 1, 4, 0.03),
+    (6, 6000, 5500, 33, 9, True, 4, 1, 0.03),
+    (7, 8191, 7000, 64, 12, True, 1, 0, 0.05),
+    (8, 2049, 2500, 5, 300, True, 1, 1, 0.03),    # wide tier
+]
+
+
+def _run_revert(hg, rounds, S, seed, phi_width=0, balance=False, graph=0, check_phi=True):
+    h = HGP.from_hypergraph(hg, subrounds=S, seed=seed, phi_width=phi_width, graph=graph,
+                            revert_negative=True, balance_moves=balance)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=seed, revert_negative=True,
+                                      balance_moves=balance)
+    got = h.refine(rounds)
+    want, _ = o.refine(rounds)
+    np.testing.assert_array_equal(got[:, :5], want)
+    np.testing.assert_array_equal(got[:, 6], o.reverted)
+    compare_state(h, o, check_phi)
+    return h, o, got
+
+
+@pytest.mark.parametrize("balance", [False, True])
+@pytest.mark.parametrize("case", REVERT_CASES, ids=[f"s{c[0]}-k{c[3]}-S{c[6]}" for c in REVERT_CASES])
+def test_revert_random(case, balance):
+    seed, n, m, k, max_size, weighted, S, w, eps = case
+    hg = synth.random_small(200 + seed, n, m, k, max_size=max_size, weighted=weighted, eps=eps, rounds=4)
+    _run_revert(hg, 4, S, seed, phi_width=w, balance=balance)
+
+
+def test_revert_happens_and_graph_replay():
+    hg = synth.random_small(204, 9999, 8000, 16, max_size=10, weighted=True, eps=0.1, rounds=4)
+    h, o, got = _run_revert(hg, 4, 4, 4, phi_width=2, graph=1)
+    assert got[:, 6].sum() > 100
+    # a second call replays the captured graph
+    got2 = h.refine(4)
+    want2, _ = o.refine(4)
+    np.testing.assert_array_equal(got2[:, :5], want2)
+    np.testing.assert_array_equal(got2[:, 6], o.reverted)
+    compare_state(h, o)
+
+
+def test_revert_hand_example_swap():
+    # net {0,1} (omega 5), vertex 0 in block 0, vertex 1 in block 1, isolated padding 2, 3: the
+    # swap is approved, and the move of vertex 1 (attributed gain -5 after 0 -> 1) is undone
+    h = HGP(4, 1, np.array([0, 2], np.int64), np.array([0, 1], np.int32), 2, 0.5,
+            np.array([0, 1, 0, 1], np.int32), None, np.array([5], np.int32), subrounds=1,
+            revert_negative=True)
+    st = h.refine(1)
+    assert st[0, :5].tolist() == [0, 2, 2, 4, 3] and st[0, 6] == 1
+    assert h.partition().tolist() == [1, 1, 0, 1]
+
+
+def test_revert_powerlaw_scaled():
+    hg = synth.config_powerlaw(scale=0.002)
+    _run_revert(hg, 3, 4, 0, check_phi=False)
+
+
+def test_revert_rejected_in_batch():
+    from paper_2010_10272_gb300 import Batch, HGPError
+    hg = synth.random_small(5, 3000, 2000, 4, rounds=2)
+    a = HGP.from_hypergraph(hg)
+    b = HGP.from_hypergraph(hg, revert_negative=True)
+    with pytest.raises(HGPError):
+        Batch([a, b])
