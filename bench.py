@@ -224,7 +224,11 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------------------------ oracle
-def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None):
+def variant_kwargs(name: str) -> dict:
+    return {"balance_moves": "balance" in name, "revert_negative": "revert" in name}
+
+
+def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None, variant="plain"):
     """Times the CPU oracle (single thread) on a bounded sample of the workload: the same
     recipe at a smaller scale, `rounds` rounds per step from the start partition."""
     import oracle
@@ -234,7 +238,7 @@ def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None):
     times = []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
-        o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=4, **variant_kwargs(variant))
         t1 = time.perf_counter()
         o.refine(rounds)
         t2 = time.perf_counter()
@@ -253,14 +257,15 @@ def run_reference(args, world, rank):
         return 0
     if args.workload in ("batch", "serving"):
         args.workload = "small"
-    value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup)
+    value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup,
+                                                variant=args.variant)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "sample": sample, "rounds": hg.rounds,
-                   "subrounds": 4},
+                   "subrounds": 4, "variant": args.variant},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -290,8 +295,9 @@ def run_gpu(args, world, rank, local):
     # make the library create its own stream)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
+    variant = variant_kwargs(args.variant)
     h = HGP(hg.n, hg.m, d_off, d_pins, hg.k, hg.eps, d_part, d_vw, d_nw, subrounds=S, device=True,
-            stream=stream)
+            stream=stream, **variant)
     info = h.info()
     del d_off, d_pins, d_vw, d_nw
 
@@ -366,7 +372,7 @@ def run_gpu(args, world, rank, local):
         pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         hp = [pin(hg.net_off), pin(hg.pins), pin(hg.part), pin(hg.vertex_w), pin(hg.net_w)]
         h2d = sum(a.nbytes for a in hp if a is not None)
-        d2h = hg.n * 4 + R * 8 * 6
+        d2h = hg.n * 4 + R * 8 * 7
         del h
         torch.cuda.empty_cache()
         times = []
@@ -375,7 +381,7 @@ def run_gpu(args, world, rank, local):
             barrier(world)
             t0 = time.perf_counter()
             h2 = HGP(hg.n, hg.m, hp[0], hp[1], hg.k, hg.eps, hp[2], hp[3], hp[4], subrounds=S,
-                     stream=stream)
+                     stream=stream, **variant)
             h2.refine(R)
             part_out = h2.partition()
             t1 = time.perf_counter()
@@ -389,7 +395,7 @@ def run_gpu(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, cstep, sample, _ = oracle_sample(args.workload, 1, 0)
+        cv, cstep, sample, _ = oracle_sample(args.workload, 1, 0, variant=args.variant)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     line = {
@@ -399,13 +405,14 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": WORKLOADS[args.workload][1], "n": hg.n, "m": hg.m, "pins": P,
                    "k": hg.k, "eps": hg.eps, "rounds": R, "subrounds": S,
                    "phi_width": info["phi_width"], "wide_nets": info["wide_nets"],
-                   "lmax": info["lmax"], "parallelism": f"replicas x{world}",
+                   "lmax": info["lmax"], "variant": args.variant, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (instance state ~10 GB resident in HBM)",
                    "step": f"reset start partition (untimed) + {R} LP rounds"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "phases": phases,
         "rounds_stats": {"objective": stats[:, 0].tolist(), "approved": stats[:, 2].tolist(),
-                         "eligible": stats[:, 3].tolist(), "moved_pins": stats[:, 5].tolist()},
+                         "eligible": stats[:, 3].tolist(), "moved_pins": stats[:, 5].tolist(),
+                         "reverted": stats[:, 6].tolist()},
         "setup_s": {"generate_or_load": t_gen},
     }
     if rank == 0:
@@ -585,6 +592,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--subrounds", type=int, default=4)
+    ap.add_argument("--variant", choices=["plain", "balance", "revert", "balance+revert"], default="plain",
+                    help="LP variant of Sec. 6: zero-gain balance moves and/or revert of negative "
+                         "attributed gains")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -95,8 +95,9 @@ typedef struct {
 
 /* Device time per phase of the rounds, from CUDA events recorded on the handle's stream
  * around each kernel while profiling is on (hgp_set_profiling).  Phases: 0 sub-round lists,
- * 1 gain and best target, 2 approval, 3 apply (Phi, Lambda, objective), 4 end of round. */
-#define HGP_PHASES 5
+ * 1 gain and best target, 2 approval, 3 apply (Phi, Lambda, objective), 4 end of round,
+ * 5 attributed gains and reverts (revert variant only). */
+#define HGP_PHASES 6
 typedef struct {
     double ms[HGP_PHASES];         /* accumulated milliseconds */
     int64_t launches[HGP_PHASES];  /* kernel launches accumulated into ms[] */

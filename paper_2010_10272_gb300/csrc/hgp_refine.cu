@@ -1507,7 +1507,7 @@ void set_grids(Plan &p, int device)
 }
 
 // Per-phase event timing (profiling mode): a pair of events around each phase instance.
-enum { PH_PREP = 0, PH_GAIN = 1, PH_APPROVE = 2, PH_APPLY = 3, PH_END = 4 };
+enum { PH_PREP = 0, PH_GAIN = 1, PH_APPROVE = 2, PH_APPLY = 3, PH_END = 4, PH_REVERT = 5 };
 
 cudaError_t phase_begin(hgp_handle *h)
 {
@@ -1620,8 +1620,10 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
         else k_apply<Rec16, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
         *p.launches += 1;
-        int32_t n_apply = 1;
-        if (p.revert) {
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, 1);
+        if (p.revert && e == cudaSuccess) e = phase_begin(p.prof);
+        if (e == cudaSuccess && p.revert) {
             const unsigned g = warp_grid(p.n_ranges);
             k_rv_clear<<<p.grid_apply * 4, kThreads, 0, p.st>>>(p.d0);
             if (p.rec32) {
@@ -1634,10 +1636,9 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
                 k_rv_revert<Rec16><<<g, kThreads, 0, p.st>>>(p.d0, rr);
             }
             *p.launches += 4;
-            n_apply += 4;
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = phase_end(p.prof, PH_REVERT, 4);
         }
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, n_apply);
     }
     if (e == cudaSuccess) e = phase_begin(p.prof);
     if (e == cudaSuccess) {

@@ -19,7 +19,7 @@ _lib = None
 
 STAT_FIELDS = ("objective", "candidates", "approved", "eligible", "max_block_weight", "moved_pins",
                "reverted")
-PHASES = ("sublists", "gain", "approval", "apply", "round_end")
+PHASES = ("sublists", "gain", "approval", "apply", "round_end", "revert")
 
 HGP_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "UNSUPPORTED", 4: "CUDA", 5: "TIMEOUT",

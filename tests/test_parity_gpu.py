@@ -279,7 +279,8 @@ def test_moved_pins_and_profile():
     prof = h.profile()
     assert sum(v[1] for v in prof.values()) == launched
     assert prof["gain"][1] == 3 * 4 and prof["apply"][1] == 3 * 4
-    assert all(v[0] > 0 for v in prof.values())
+    assert all(v[0] > 0 for name, v in prof.items() if name != "revert")
+    assert prof["revert"] == (0.0, 0)                 # revert variant off
 
 
 @pytest.mark.parametrize("k,graph", [(8, 0), (8, 1), (64, 0), (64, 1)])

@@ -158,3 +158,15 @@ def test_revert_rejected_in_batch():
     b = HGP.from_hypergraph(hg, revert_negative=True)
     with pytest.raises(HGPError):
         Batch([a, b])
+
+
+def test_revert_profile_phase():
+    hg = synth.random_small(36, 20000, 18000, 8, max_size=9, weighted=True, rounds=3)
+    h = HGP.from_hypergraph(hg, subrounds=4, revert_negative=True)
+    h.set_profiling(True)
+    l0 = h.launch_count()
+    h.refine(3)
+    launched = h.launch_count() - l0
+    prof = h.profile()
+    assert sum(v[1] for v in prof.values()) == launched
+    assert prof["revert"][1] == 3 * 4 * 4 and prof["revert"][0] > 0
