@@ -72,6 +72,8 @@ def _load():
         for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
             getattr(lib, name).argtypes = [P, P]
         lib.oracle_set_variant.argtypes = [P, i32, i32]
+        lib.oracle_rebalance.restype = ctypes.c_int
+        lib.oracle_rebalance.argtypes = [P, i32, P, P, P, P, i64, P]
         lib.oracle_exact_gains.restype = ctypes.c_int
         lib.oracle_exact_gains.argtypes = [P, i32, P, P]
         lib.oracle_sample_candidates.restype = ctypes.c_int
@@ -158,6 +160,26 @@ class Oracle:
             moves = moves[:cnt.value].copy()
         self.reverted = stats[:, len(STAT_FIELDS)].copy()
         return stats[:, :len(STAT_FIELDS)].copy(), moves
+
+    def rebalance(self, max_passes: int, log_moves: bool = False, max_moves: int = 1 << 20):
+        """Rebalancing passes (Sec. 8).  Returns (stats [passes x 5] int64, phases [passes]
+        int32, moves or None); moves as in refine, first field = pass * S + sub-round."""
+        stats = np.zeros((max(1, max_passes), len(STAT_FIELDS) + 1), dtype=np.int64)
+        phases = np.zeros(max(1, max_passes), dtype=np.int32)
+        moves = np.zeros((max_moves, 4), dtype=np.int64) if log_moves else None
+        npass = ctypes.c_int32(0)
+        cnt = ctypes.c_int64(0)
+        rc = self._lib.oracle_rebalance(self._h, int(max_passes), _ptr(stats), _ptr(phases),
+                                        ctypes.byref(npass), _ptr(moves),
+                                        int(max_moves if log_moves else 0), ctypes.byref(cnt))
+        if rc != 0:
+            raise MemoryError("oracle_rebalance failed")
+        p = npass.value
+        if log_moves:
+            if cnt.value > max_moves:
+                raise ValueError("move log truncated")
+            moves = moves[:cnt.value].copy()
+        return stats[:p, :len(STAT_FIELDS)].copy(), phases[:p].copy(), moves
 
     def gain(self, u: int, i: int) -> int:
         return int(self._lib.oracle_gain(self._h, int(u), int(i)))

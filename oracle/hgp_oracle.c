@@ -77,6 +77,7 @@ typedef struct {
     int32_t *order;        /* [n]  */
     int32_t *from;         /* [n]  block an approved vertex left */
     int64_t *attr;         /* [n]  attributed gain of an approved move */
+    uint8_t *selected;     /* [n]  rebalancing: passed the source-side selection */
 } oracle_t;
 
 /* Per-round statistics, in this order: objective after the round, number of candidates,
@@ -124,7 +125,7 @@ void oracle_destroy(oracle_t *o)
     free(o->net_off); free(o->pins); free(o->vw); free(o->nw); free(o->vtx_off);
     free(o->inc); free(o->part); free(o->phi); free(o->bw); free(o->moved_prev);
     free(o->moved_cur); free(o->cand_t); free(o->cand_g); free(o->approved); free(o->order);
-    free(o->from); free(o->attr);
+    free(o->from); free(o->attr); free(o->selected);
     free(o);
 }
 
@@ -156,9 +157,10 @@ oracle_t *oracle_create(int32_t n, int32_t m, const int64_t *net_off, const int3
     o->order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
     o->from = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
     o->attr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    o->selected = (uint8_t *)calloc((size_t)n + 1, 1);
     if (!o->net_off || !o->pins || !o->vw || !o->nw || !o->vtx_off || !o->inc || !o->part ||
         !o->phi || !o->bw || !o->moved_prev || !o->moved_cur || !o->cand_t || !o->cand_g ||
-        !o->approved || !o->order || !o->from || !o->attr) {
+        !o->approved || !o->order || !o->from || !o->attr || !o->selected) {
         oracle_destroy(o);
         return NULL;
     }
@@ -272,8 +274,9 @@ void oracle_candidates(const oracle_t *o, int32_t s, int32_t *target, int64_t *g
     }
 }
 
-/* Moves u from its block to t: partition, block weights, Phi, and the moved-net marks. */
-static void move_vertex(oracle_t *o, int32_t u, int32_t t)
+/* Moves u from its block to t: partition, block weights, Phi, and (mark != 0) the moved-net
+ * marks that decide the next LP round's eligibility. */
+static void move_vertex_marked(oracle_t *o, int32_t u, int32_t t, int mark)
 {
     const int32_t a = o->part[u], k = o->k;
     o->part[u] = t;
@@ -283,9 +286,11 @@ static void move_vertex(oracle_t *o, int32_t u, int32_t t)
         const int32_t e = o->inc[j];
         o->phi[(int64_t)e * k + a]--;
         o->phi[(int64_t)e * k + t]++;
-        o->moved_cur[e] = 1;
+        if (mark) o->moved_cur[e] = 1;
     }
 }
+
+static void move_vertex(oracle_t *o, int32_t u, int32_t t) { move_vertex_marked(o, u, t, 1); }
 
 /* Runs `rounds` synchronous LP rounds.  stats: NULL or [rounds * ST_COUNT].
  * moves: NULL or [max_moves * 4] receiving (global sub-round index, u, from, to) for each
@@ -376,6 +381,117 @@ int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
             st[ST_REVERTED] = n_rev;
         }
     }
+    if (num_moves) *num_moves = logged;
+    return 0;
+}
+
+static int64_t heaviest_block(const oracle_t *o)
+{
+    int64_t w = 0;
+    for (int32_t i = 0; i < o->k; ++i) if (o->bw[i] > w) w = o->bw[i];
+    return w;
+}
+
+/* Rebalancing (Sec. 8), in a synchronous form.  A pass splits the vertices into the S
+ * sub-rounds of the hash with round number 2^30 + pass (so it never coincides with an LP
+ * round).  In a sub-round, against the frozen state, a vertex u of an overloaded block a
+ * (w(a) > L_max) picks the block t != a with room (w(t) + c(u) <= L_max) of highest gain,
+ * smaller id on ties; in phase 1 only a gain >= 0 makes it a candidate (the paper's immediate
+ * non-negative moves), in phase 2 any gain does (the paper's second step, least connectivity
+ * increase first).  Candidates are ordered by (gain desc, id asc).  Source side: a candidate
+ * is selected while the weight that left its block before it, in that order, is still below
+ * w(a) - L_max (its block is still overloaded when it leaves).  Target side: selected
+ * candidates are approved while the inclusive prefix of their weights fits L_max - w(t).
+ * Approved moves are applied; they do not count as moves for LP eligibility.
+ * Passes run while a block is overloaded and at most max_passes times; phase 1 switches to
+ * phase 2 after a pass without moves, and a phase-2 pass without moves ends it.
+ * stats: NULL or [max_passes * ST_COUNT] per pass; phases: NULL or [max_passes].
+ * moves as in oracle_refine (first field = pass * S + sub-round).  Returns 0, -1 on failure. */
+int oracle_rebalance(oracle_t *o, int32_t max_passes, int64_t *stats, int32_t *phases,
+                     int32_t *num_passes, int64_t *moves, int64_t max_moves, int64_t *num_moves)
+{
+    const int32_t n = o->n, k = o->k, S = o->subrounds;
+    int32_t phase = 1, pass = 0;
+    int64_t logged = 0;
+    while (pass < max_passes && heaviest_block(o) > o->lmax) {
+        const int64_t rid = ((int64_t)1 << 30) + pass;
+        int64_t n_cand = 0, n_appr = 0, n_cons = 0;
+        for (int32_t s = 0; s < S; ++s) {
+            /* (1) candidates of overloaded blocks against the frozen state */
+            int32_t cnt = 0;
+            for (int32_t u = 0; u < n; ++u) {
+                o->cand_t[u] = -1;
+                o->cand_g[u] = 0;
+                o->selected[u] = 0;
+                o->approved[u] = 0;
+                const int32_t a = o->part[u];
+                if (oracle_subround_of(o->seed, rid, u, S) != s || o->bw[a] <= o->lmax) continue;
+                n_cons++;
+                int32_t best_t = -1;
+                int64_t best_g = 0;
+                for (int32_t i = 0; i < k; ++i) {
+                    if (i == a || o->bw[i] + o->vw[u] > o->lmax) continue;
+                    const int64_t g = oracle_gain(o, u, i);
+                    if (best_t < 0 || g > best_g) { best_t = i; best_g = g; }
+                }
+                if (best_t < 0 || (phase == 1 && best_g < 0)) continue;
+                o->cand_t[u] = best_t;
+                o->cand_g[u] = best_g;
+                o->order[cnt++] = u;
+                n_cand++;
+            }
+            g_sort_ctx = o;
+            qsort(o->order, (size_t)cnt, sizeof(int32_t), by_gain_desc_id_asc);
+            /* (2) source side: leave while the block is still overloaded */
+            for (int32_t a = 0; a < k; ++a) {
+                int64_t left = 0;
+                for (int32_t j = 0; j < cnt; ++j) {
+                    const int32_t u = o->order[j];
+                    if (o->part[u] != a) continue;
+                    if (left < o->bw[a] - o->lmax) o->selected[u] = 1;
+                    left += o->vw[u];
+                }
+            }
+            /* (3) target side: inclusive prefix of the selected candidates fits */
+            for (int32_t t = 0; t < k; ++t) {
+                int64_t acc = 0;
+                for (int32_t j = 0; j < cnt; ++j) {
+                    const int32_t u = o->order[j];
+                    if (!o->selected[u] || o->cand_t[u] != t) continue;
+                    acc += o->vw[u];
+                    if (o->bw[t] + acc <= o->lmax) o->approved[u] = 1;
+                }
+            }
+            /* (4) apply (ascending id), no eligibility marks */
+            for (int32_t u = 0; u < n; ++u) {
+                if (!o->approved[u]) continue;
+                const int32_t a = o->part[u], t = o->cand_t[u];
+                move_vertex_marked(o, u, t, 0);
+                if (moves && logged < max_moves) {
+                    int64_t *mv = moves + 4 * logged;
+                    mv[0] = (int64_t)pass * S + s; mv[1] = u; mv[2] = a; mv[3] = t;
+                }
+                logged++;
+                n_appr++;
+            }
+        }
+        if (stats) {
+            int64_t *st = stats + (int64_t)pass * ST_COUNT;
+            st[ST_OBJ] = objective_from_phi(o);
+            st[ST_CAND] = n_cand;
+            st[ST_APPROVED] = n_appr;
+            st[ST_ELIGIBLE] = n_cons;
+            st[ST_MAXW] = heaviest_block(o);
+            st[ST_REVERTED] = 0;
+        }
+        if (phases) phases[pass] = phase;
+        pass++;
+        if (n_appr == 0) {
+            if (phase == 2) break;
+            phase = 2;
+        }
+    }
+    if (num_passes) *num_passes = pass;
     if (num_moves) *num_moves = logged;
     return 0;
 }

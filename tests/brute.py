@@ -186,3 +186,62 @@ def random_tiny(rng: np.random.Generator, n: int, m: int, k: int, max_size: int 
     vw = rng.integers(1, 4, size=n).tolist() if weighted else None
     nw = rng.integers(1, 6, size=m).tolist() if weighted else None
     return Tiny(n, nets, k, eps, vw, nw)
+
+
+def rebalance(t: Tiny, part, max_passes: int, S: int = 4, seed: int = 0):
+    """Rebalancing passes (Sec. 8) with definitional gains (objective differences).
+    Returns (part, per-pass stats (objective, candidates, approved, considered, max block
+    weight), phases, move log [(pass * S + sub-round, u, from, to)])."""
+    part = [int(x) for x in part]
+    lmax = t.lmax()
+    stats, phases, log = [], [], []
+    phase, p = 1, 0
+    while p < max_passes and max(t.block_weights(part)) > lmax:
+        n_cand = n_appr = n_cons = 0
+        for s in range(S):
+            w = t.block_weights(part)
+            cands = {}
+            for u in range(t.n):
+                a = part[u]
+                if subround(seed, (1 << 30) + p, u, S) != s or w[a] <= lmax:
+                    continue
+                n_cons += 1
+                room = [i for i in range(t.k) if i != a and w[i] + t.vw[u] <= lmax]
+                if not room:
+                    continue
+                best = max(room, key=lambda i: (t.gain(part, u, i), -i))
+                g = t.gain(part, u, best)
+                if phase == 1 and g < 0:
+                    continue
+                cands[u] = (best, g)
+            n_cand += len(cands)
+            order = sorted(cands, key=lambda u: (-cands[u][1], u))
+            selected = set()
+            for a in range(t.k):
+                left = 0
+                for u in order:
+                    if part[u] != a:
+                        continue
+                    if left < w[a] - lmax:
+                        selected.add(u)
+                    left += t.vw[u]
+            approved = []
+            for blk in range(t.k):
+                acc = 0
+                for u in order:
+                    if u in selected and cands[u][0] == blk:
+                        acc += t.vw[u]
+                        if w[blk] + acc <= lmax:
+                            approved.append(u)
+            for u in sorted(approved):
+                log.append((p * S + s, u, part[u], cands[u][0]))
+                part[u] = cands[u][0]
+            n_appr += len(approved)
+        stats.append((t.objective(part), n_cand, n_appr, n_cons, max(t.block_weights(part))))
+        phases.append(phase)
+        p += 1
+        if n_appr == 0:
+            if phase == 2:
+                break
+            phase = 2
+    return part, stats, phases, log

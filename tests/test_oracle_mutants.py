@@ -2,7 +2,7 @@
 
 Each case copies the oracle source, plants one mistake (a dropped term, a wrong sign, a
 wrong index or comparison, a transposed operand), builds it, and runs the pin suite
-(tests/test_oracle_pins.py) against the broken copy.  The pin suite must fail for every
+(PIN_FILES below) against the broken copy.  The pin suite must fail for every
 mutant.  The committed oracle is never modified.
 """
 import concurrent.futures
@@ -16,6 +16,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hgp_oracle.c")
+
+# the pin suites run against each mutant
+PIN_FILES = ("test_oracle_pins.py", "test_oracle_rebalance.py", "test_oracle_exact_gains.py")
 
 # (name, exact text in the oracle source, replacement)
 MUTANTS = [
@@ -53,6 +56,15 @@ MUTANTS = [
     ("attributed gain from the frozen state", "o->attr[u] = oracle_gain(o, u, t);", "o->attr[u] = o->cand_g[u];"),
     ("revert of zero gains too", "if (!o->approved[u] || o->attr[u] >= 0) continue;",
      "if (!o->approved[u] || o->attr[u] > 0) continue;"),
+    ("rebalance source rule inclusive", "if (left < o->bw[a] - o->lmax) o->selected[u] = 1;\n                    left += o->vw[u];",
+     "left += o->vw[u];\n                    if (left < o->bw[a] - o->lmax) o->selected[u] = 1;"),
+    ("rebalance phase 1 takes negative gains", "if (best_t < 0 || (phase == 1 && best_g < 0)) continue;",
+     "if (best_t < 0) continue;"),
+    ("rebalance ignores room", "if (i == a || o->bw[i] + o->vw[u] > o->lmax) continue;", "if (i == a) continue;"),
+    ("rebalance moves make neighbours eligible", "move_vertex_marked(o, u, t, 0);",
+     "move_vertex_marked(o, u, t, 0); for (int64_t jj = o->vtx_off[u]; jj < o->vtx_off[u + 1]; ++jj) o->moved_prev[o->inc[jj]] = 1;"),
+    ("rebalance tie to larger block", "if (best_t < 0 || g > best_g) { best_t = i; best_g = g; }",
+     "if (best_t < 0 || g >= best_g) { best_t = i; best_g = g; }"),
     ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
      "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
 ]
@@ -68,8 +80,8 @@ def _run_mutant(name, old, new, workdir):
     open(c, "w").write(mutated)
     subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-o", so, c, "-lm"])
     env = dict(os.environ, HGP_ORACLE_LIB=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                       [os.path.join(ROOT, "tests", f) for f in PIN_FILES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
