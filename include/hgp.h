@@ -278,6 +278,26 @@ int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, con
                            int32_t *target, int64_t *gain, void *cuda_stream);
 
 /*
+ * Rebalancing (paper Sec. 8), in a synchronous form.  Runs passes while a block is heavier
+ * than L_max, at most max_passes.  A pass splits the vertices into the handle's S sub-rounds
+ * (hash round number 2^30 + pass index).  In a sub-round, against the state at its start,
+ * every vertex u of an overloaded block a picks the block t != a with room (w(t) + c(u) <=
+ * L_max) of highest gain (smaller id on ties).  Phase 1 keeps only gains >= 0 (the paper's
+ * immediate non-negative moves); after a phase-1 pass without moves, phase 2 keeps any gain
+ * (least connectivity increase first).  Candidates are ordered by (gain desc, id asc); per
+ * source block, a candidate passes while the weight that left before it is below
+ * w(a) - L_max; per target block, passing candidates are approved while their inclusive
+ * prefix fits L_max - w(t).  A phase-2 pass without moves ends the call.  Rebalancing moves
+ * do not count as moves for LP eligibility and do not advance the round number.
+ * stats: NULL or host hgp_round_stats[max_passes]; entry i describes pass i (eligible =
+ * vertices of overloaded blocks considered, reverted = 0).  phases: NULL or host
+ * int32[max_passes] (1 or 2).  num_passes: NULL or receives the number of passes run.
+ * HGP_ERR_UNSUPPORTED when twice the largest incident net weight of a vertex reaches 2^31.
+ */
+int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats *stats, int32_t *phases,
+                  int32_t *num_passes);
+
+/*
  * Exact gains of a move sequence (paper Sec. 5.4, Lemma 1), computed in parallel.
  * moves: host int32[count][3] = (u, from, to) in sequence order, every vertex at most once,
  * from = its current block, to != from.  gains: host int64[count], gains[j] = the gain (Sec. 5)

@@ -72,7 +72,9 @@ __device__ __forceinline__ int32_t item_count(const Dev *devs, const int2 *items
 
 // ------------------------------------------------------------------ round preparation
 // warp per range item
-__global__ void __launch_bounds__(kThreads) k_round_prep(const Dev *devs, const int2 *items, int32_t n_items)
+// r_ovr >= 0: hash with that round number instead of the device round state (rebalancing)
+__global__ void __launch_bounds__(kThreads) k_round_prep(const Dev *devs, const int2 *items, int32_t n_items,
+                                                         int32_t r_ovr = -1)
 {
     __shared__ uint8_t subs[kWarps][kRange];
     __shared__ int32_t cnt[kWarps][65];
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_round_prep(const Dev *devs, const 
     if (item >= item_count(devs, items, n_items, 0)) return;
     int32_t range;
     const Dev d = item_of(devs, items, item, range);
-    const int32_t r = d.rs[0];
+    const int32_t r = r_ovr >= 0 ? r_ovr : d.rs[0];
     const uint64_t seed = d.seed;
     const int32_t base = range * kRange;
     const int32_t nv = min(kRange, d.n - base);
@@ -293,18 +295,29 @@ struct GainInst {
     int32_t all_elig;    // first round: every vertex eligible
 };
 
+// Rebalancing pass settings (RB instances of the gain step).
+struct RbArgs {
+    int32_t r;       // round number of the sub-round hash for this pass
+    int32_t phase;   // 1: gain >= 0 only; 2: any gain
+    int32_t off;     // added to the gain to make the approval priority non-negative
+};
+
 // One range item of the gain step (see k_gain); returns the number of candidates written.
-template <typename Rec>
+// RB: a rebalancing pass (Sec. 8): only vertices of overloaded blocks take part, their target
+// is the block with room of highest gain (any sign), and the candidate records its source
+// block (bits 16..23) and the priority gain + off; the per-block totals are by source block.
+template <typename Rec, bool RB>
 __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32_t s, GainWarp<typename RecIO<Rec>::Lam> &g,
                                               const long long *slack, unsigned long long *tot,
-                                              const GainInst<typename RecIO<Rec>::Lam> &gi, int32_t &nel)
+                                              const GainInst<typename RecIO<Rec>::Lam> &gi, int32_t &nel,
+                                              const RbArgs &rb)
 {
     typedef typename RecIO<Rec>::Lam Lam;
     constexpr bool kWide = sizeof(Lam) == 8;
     const int lane = threadIdx.x & 31;
     const Lam feas1 = gi.feas1;
     const int32_t r = gi.r, all_elig = gi.all_elig;
-    const bool balance = (d.variant & 1) != 0;
+    const bool balance = !RB && (d.variant & 1) != 0;
         const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
         const bool unit = d.nw == nullptr;
         const int32_t rbase = range * kRange;
@@ -329,6 +342,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                 cu = d.vw ? d.vw[u] : 1;
                 jb = d.vtx_off[u];
                 deg = d.vtx_off[u + 1] - jb;
+                if (RB && slack[a] >= 0) deg = 0;   // not in an overloaded block: no work
             }
             g.a[lane] = a;
             g.jb[lane] = jb;
@@ -336,7 +350,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
             g.b[lane] = 0;
             g.T[lane] = 0;
             g.A2[lane] = ~0ull;
-            g.elig[lane] = all_elig;
+            g.elig[lane] = RB ? (valid && slack[a] < 0) : all_elig;
             int32_t incl = deg;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -374,7 +388,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     } else if (balance) {
                         atomicAnd(&g.A2[v1], (unsigned long long)lam1);
                     }
-                    if (moved_in_prev_round(mv1, r)) g.elig[v1] = 1;
+                    if (!RB && moved_in_prev_round(mv1, r)) g.elig[v1] = 1;
                 }
                 if (i2 < total) {
                     w2 &= 0x7fffffff;
@@ -386,14 +400,15 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     } else if (balance) {
                         atomicAnd(&g.A2[v2], (unsigned long long)lam2);
                     }
-                    if (moved_in_prev_round(mv2, r)) g.elig[v2] = 1;
+                    if (!RB && moved_in_prev_round(mv2, r)) g.elig[v2] = 1;
                 }
             }
             __syncwarp();
             // ---- per vertex: eligibility, candidate blocks, best block
             const int32_t W = g.W[lane], b = g.b[lane];
             const bool elig = valid && g.elig[lane] != 0;
-            Lam T = elig ? (Lam)g.T[lane] : (Lam)0;
+            const Lam kall = d.k >= (int)(8 * sizeof(Lam)) ? ~(Lam)0 : (((Lam)1 << d.k) - 1);
+            Lam T = elig ? (RB ? kall : (Lam)g.T[lane]) : (Lam)0;
             T &= ~((Lam)1 << a);
             const Lam T_all = T;   // before the room filter (balance moves need it)
             if (d.vw) {
@@ -418,7 +433,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                 if (unit) best_by_planes<Lam, Rec, true>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn, eqv, zero_in);
                 else best_by_planes<Lam, Rec, false>(np, g, recs, d.inc, my_off, my_off + deg, jb, my_off, T, t, conn, eqv, zero_in);
                 const int32_t gg = bw_ + conn;
-                if (gg > 0) {
+                if (RB ? (rb.phase == 2 || gg >= 0) : gg > 0) {
                     t_best = t;
                     g_best = gg;
                 }
@@ -454,16 +469,17 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     }
                 }
                 // key = gain << 8 | (255 - block): the larger key is the higher gain, then the
-                // smaller block
+                // smaller block (RB: the gain's sign bit flipped, so negative gains order too)
                 unsigned long long key = 0;
                 if ((Tlo >> lane) & 1) {
                     const int32_t gg = hbw + acc0;
-                    if (gg > 0) key = ((unsigned long long)(uint32_t)gg << 8) | (unsigned long long)(255 - lane);
+                    if (RB ? (rb.phase == 2 || gg >= 0) : gg > 0)
+                        key = ((unsigned long long)((uint32_t)gg ^ (RB ? 0x80000000u : 0u)) << 8) | (unsigned long long)(255 - lane);
                 }
                 if (kWide && ((Thi >> lane) & 1)) {
                     const int32_t gg = hbw + acc1;
-                    if (gg > 0) {
-                        const unsigned long long k2 = ((unsigned long long)(uint32_t)gg << 8) | (unsigned long long)(255 - (lane + 32));
+                    if (RB ? (rb.phase == 2 || gg >= 0) : gg > 0) {
+                        const unsigned long long k2 = ((unsigned long long)((uint32_t)gg ^ (RB ? 0x80000000u : 0u)) << 8) | (unsigned long long)(255 - (lane + 32));
                         key = k2 > key ? k2 : key;
                     }
                 }
@@ -474,7 +490,7 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                 }
                 if (lane == src && key) {
                     t_best = 255 - (int)(key & 0xFF);
-                    g_best = (int32_t)(key >> 8);
+                    g_best = (int32_t)((uint32_t)(key >> 8) ^ (RB ? 0x80000000u : 0u));
                 }
                 if (balance) {
                     // zero-gain blocks of T among the ones this lane owns
@@ -506,8 +522,14 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
             const unsigned cm = __ballot_sync(kFull, t_best >= 0);
             if (t_best >= 0) {
                 const int pos = nout + __popc(cm & lanemask_lt());
-                out[pos] = ((uint64_t)(uint32_t)g_best << 32) | ((uint32_t)ul << 8) | (uint32_t)t_best;
-                atomicAdd(&tot[t_best], (unsigned long long)cu);
+                if (RB) {
+                    out[pos] = ((uint64_t)(uint32_t)(g_best + rb.off) << 32) | ((uint32_t)a << 16) |
+                               ((uint32_t)ul << 8) | (uint32_t)t_best;
+                    atomicAdd(&tot[a], (unsigned long long)cu);
+                } else {
+                    out[pos] = ((uint64_t)(uint32_t)g_best << 32) | ((uint32_t)ul << 8) | (uint32_t)t_best;
+                    atomicAdd(&tot[t_best], (unsigned long long)cu);
+                }
             }
             nout += __popc(cm);
             __syncwarp();
@@ -552,9 +574,9 @@ __device__ __forceinline__ void load_dev(Dev &dst, const Dev *src)
 // A vertex whose incident net weights exceed kPlaneMaxW uses a warp-cooperative pass instead.
 // B = false: one instance, d0 (parameter space), items are its ranges; B = true: a batch,
 // items name (instance, range) and each warp copies its item's instance into shared memory.
-template <typename Rec, bool B>
+template <typename Rec, bool B, bool RB = false>
 __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *devs, const int2 *items,
-                                                      int32_t n_items, int32_t s, int32_t rr)
+                                                      int32_t n_items, int32_t s, int32_t rr, RbArgs rb = RbArgs{0, 0, 0})
 {
     typedef typename RecIO<Rec>::Lam Lam;
     __shared__ GainWarp<Lam> ws[kWarps];
@@ -578,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
             }
             const Dev &d = dsm[wid];
             int32_t nel = 0;
-            const int32_t nout = gain_range<Rec>(d, it.y, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel);
+            const int32_t nout = gain_range<Rec, false>(d, it.y, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel, rb);
             if (lane == 0) d.cand_cnt[it.y] = nout;
             // flush this item's totals into its own instance
             unsigned long long *row = reinterpret_cast<unsigned long long *>(d.stats + (int64_t)rr * ST_N);
@@ -597,10 +619,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
         } else {
             if (inst_prev < 0) {
                 gain_refresh<Rec>(d0, slack_w[wid], gi);
+                if (RB) gi.r = rb.r;
                 inst_prev = 0;
             }
             int32_t nel = 0;
-            const int32_t nout = gain_range<Rec>(d0, item, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel);
+            const int32_t nout = gain_range<Rec, RB>(d0, item, s, ws[wid], slack_w[wid], tot_w[wid], gi, nel, rb);
             if (lane == 0) d0.cand_cnt[item] = nout;
             nelig += nel;
             ncand += nout;
@@ -651,6 +674,30 @@ __device__ __forceinline__ void decode(uint64_t c, int &t, int32_t &g, int &ul)
     g = (int32_t)(c >> 32);
 }
 
+// Which block an approval stage groups a candidate by, and which candidates take part:
+//   KEY_T   LP: by target block, all candidates, inclusive prefix <= L_max - w(t);
+//   KEY_A   rebalancing, source side: by source block (bits 16..23), all candidates, a
+//           candidate passes while the weight before it is <= w(a) - L_max - 1 (exclusive);
+//   KEY_TS  rebalancing, target side: by target block, only candidates marked by KEY_A
+//           (bit 24), inclusive prefix <= L_max - w(t).
+enum { KEY_T = 0, KEY_A = 1, KEY_TS = 2 };
+constexpr uint64_t kSelBit = 1ull << 24;
+
+template <int KEY>
+__device__ __forceinline__ bool decode_key(uint64_t c, int &key, int &t, int32_t &g, int &ul)
+{
+    decode(c, t, g, ul);
+    key = KEY == KEY_A ? (int)((c >> 16) & 0xFF) : t;
+    return KEY != KEY_TS || (c & kSelBit) != 0;
+}
+
+// capacity of a key block for the stage (the weight its passing candidates may add up to)
+template <int KEY>
+__device__ __forceinline__ long long stage_cap(const Dev &d, int key)
+{
+    return KEY == KEY_A ? (long long)d.bw[key] - d.lmax - 1 : (long long)d.lmax - d.bw[key];
+}
+
 // digit of the overflow-bin refinement at `level` (1..3) for value v = g - (kBins - 1),
 // and whether v matches the prefix resolved so far
 __device__ __forceinline__ int refine_digit(int32_t v, int level, int64_t prefix, bool &match)
@@ -661,7 +708,8 @@ __device__ __forceinline__ int refine_digit(int32_t v, int level, int64_t prefix
     return v & 1023;
 }
 
-// warp per range item: histogram of candidate weight by gain for saturated target blocks
+// warp per range item: histogram of candidate weight by gain for saturated key blocks
+template <int KEY = KEY_T>
 __global__ void __launch_bounds__(kThreads) k_hist(const Dev *devs, const int2 *items, int32_t n_items, int level)
 {
     __shared__ int active[kWarps][64];
@@ -676,7 +724,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(const Dev *devs, const int2 *
         int a = 0;
         if (t < d.k) {
             if (level == 0) {
-                a = d.bw[t] + d.tot[t] > d.lmax;
+                a = d.tot[t] > 0 && d.tot[t] > stage_cap<KEY>(d, t);
             } else {
                 const Sel sl = d.sel[t];
                 a = sl.mode == SEL_REFINE && sl.level == level;
@@ -691,10 +739,10 @@ __global__ void __launch_bounds__(kThreads) k_hist(const Dev *devs, const int2 *
     const int32_t n = d.cand_cnt[range];
     const uint64_t *cand = d.cand + (int64_t)range * kRange;
     for (int i = lane; i < n; i += 32) {
-        int t, ul;
+        int t, ul, key;
         int32_t g;
-        decode(cand[i], t, g, ul);
-        if (!active[wid][t]) continue;
+        if (!decode_key<KEY>(cand[i], key, t, g, ul) || !active[wid][key]) continue;
+        t = key;
         const unsigned long long c = d.vw ? (unsigned long long)d.vw[range * kRange + ul] : 1ull;
         int bin;
         if (level == 0) {
@@ -738,6 +786,7 @@ __device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long 
 }
 
 // one CTA per block item (instance, t): threshold of the (gain desc, id asc) prefix that fits
+template <int KEY = KEY_T>
 __global__ void __launch_bounds__(kThreads) k_select(const Dev *devs, const int2 *items, int32_t n_items, int level)
 {
     __shared__ unsigned long long wt[32];
@@ -752,8 +801,8 @@ __global__ void __launch_bounds__(kThreads) k_select(const Dev *devs, const int2
     int nbins;
     if (level == 0) {
         const long long tot = d.tot[t];
-        cap = d.lmax - d.bw[t];
-        if (d.bw[t] + tot <= d.lmax) {
+        cap = stage_cap<KEY>(d, t);
+        if (tot == 0 || tot <= cap) {
             if (tid == 0) {
                 Sel o;
                 o.mode = SEL_ALL; o.level = 0; o.g = 0; o.rem = 0;
@@ -814,6 +863,7 @@ __global__ void __launch_bounds__(kThreads) k_select(const Dev *devs, const int2
 
 // one CTA per tile item (instance, tile of 8 ranges): weight of the candidates at their
 // block's threshold gain, per block
+template <int KEY = KEY_T>
 __global__ void __launch_bounds__(kThreads) k_tie_sum(const Dev *devs, const int2 *items, int32_t n_items)
 {
     __shared__ int thr[64];
@@ -844,11 +894,10 @@ __global__ void __launch_bounds__(kThreads) k_tie_sum(const Dev *devs, const int
         const int32_t n = d.cand_cnt[range];
         const uint64_t *cand = d.cand + (int64_t)range * kRange;
         for (int i = lane; i < n; i += 32) {
-            int t, ul;
+            int t, ul, key;
             int32_t g;
-            decode(cand[i], t, g, ul);
-            if (thr[t] && g == gthr[t])
-                atomicAdd(&ts[t], d.vw ? (unsigned long long)d.vw[range * kRange + ul] : 1ull);
+            if (decode_key<KEY>(cand[i], key, t, g, ul) && thr[key] && g == gthr[key])
+                atomicAdd(&ts[key], d.vw ? (unsigned long long)d.vw[range * kRange + ul] : 1ull);
         }
     }
     __syncthreads();
@@ -914,7 +963,7 @@ struct alignas(16) ApplyWarp {
 // result is used, so their latencies overlap.
 constexpr int kPins = 4;
 
-template <typename Rec>
+template <typename Rec, bool STAMP = true>
 __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const ApplyWarp &w_,
                                                 int32_t i0, int32_t total, int32_t r)
 {
@@ -940,7 +989,7 @@ __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const A
         const int32_t ee = e[q] & kNetMask;
         const int32_t wrow = wide ? d.widx[ee] : 0;
         Rec *rc = recs + ee;
-        mv[q] = __ldcg(&rc->mv);
+        mv[q] = STAMP ? __ldcg(&rc->mv) : 0;
         w[q] = __ldg(&rc->w) & 0x7fffffff;
         oa[q] = phi_add(d, ee, a[q], -1, wide, wrow);
         ot[q] = phi_add(d, ee, t[q], +1, wide, wrow);
@@ -962,8 +1011,10 @@ __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const A
         }
         // stamp: every writer of round r derives the same value from the pre-round stamp,
         // and one that already sees round r leaves it alone
-        const int32_t last = mv[q] >> 1;
-        if (last != r) rc->mv = (r << 1) | (last == r - 1 ? 1 : 0);
+        if (STAMP) {
+            const int32_t last = mv[q] >> 1;
+            if (last != r) rc->mv = (r << 1) | (last == r - 1 ? 1 : 0);
+        }
         dobj += (long long)(ot[q] == 0 ? w[q] : 0) - (long long)(oa[q] == 1 ? w[q] : 0);
     }
     return dobj;
@@ -996,31 +1047,25 @@ __device__ __forceinline__ bool apply_refresh(const Dev &d, ApplyInst &ai, int32
     return __any_sync(kFull, thr_any) != 0;
 }
 
-// One range item of the apply step (see k_apply).
-template <typename Rec>
-__device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t r, bool any_thr,
-                                            const ApplyInst &ai, unsigned long long *run,
-                                            unsigned long long *bwd, ApplyWarp &w_, long long &idobj,
-                                            int32_t &iappr, int32_t &ipins)
+// The id-ordered tie prefix of a range: per key block at its threshold gain, the weight of
+// the passing candidates at the threshold in the earlier ranges of the tile (the tile's
+// exclusive prefix plus the earlier ranges of the same tile).  Only needed, and only built,
+// when the range holds such a candidate; returns whether it does.
+template <int KEY>
+__device__ __forceinline__ bool range_tie_prefix(const Dev &d, int32_t range, bool any_thr, const ApplyInst &ai,
+                                                 unsigned long long *run, const uint64_t *cand, int32_t ncand)
 {
     const int lane = threadIdx.x & 31;
     const int *mode = ai.mode;
     const int32_t *gthr = ai.gthr;
-    const long long *rem = ai.rem;
-    Rec *recs = reinterpret_cast<Rec *>(d.rec);
-    const int32_t ncand = d.cand_cnt[range];
-    if (ncand == 0) return;
-    const uint64_t *cand = d.cand + (int64_t)range * kRange;
     bool has_tie = false;
     if (any_thr) {
-        // the id-ordered tie prefix is only needed if this range holds a candidate at its
-        // block's threshold gain
         bool tie = false;
         for (int i = lane; i < ncand; i += 32) {
-            int t, ul;
+            int t, ul, key;
             int32_t g;
-            decode(cand[i], t, g, ul);
-            tie = tie || (mode[t] == SEL_THRESH && g == gthr[t]);
+            const bool in = decode_key<KEY>(cand[i], key, t, g, ul);
+            tie = tie || (in && mode[key] == SEL_THRESH && g == gthr[key]);
         }
         has_tie = __any_sync(kFull, tie) != 0;
     }
@@ -1034,39 +1079,70 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
             const int32_t n2 = d.cand_cnt[pr];
             const uint64_t *c2 = d.cand + (int64_t)pr * kRange;
             for (int i = lane; i < n2; i += 32) {
-                int t, ul;
+                int t, ul, key;
                 int32_t g;
-                decode(c2[i], t, g, ul);
-                if (mode[t] == SEL_THRESH && g == gthr[t])
-                    atomicAdd(&run[t], d.vw ? (unsigned long long)d.vw[pr * kRange + ul] : 1ull);
+                if (decode_key<KEY>(c2[i], key, t, g, ul) && mode[key] == SEL_THRESH && g == gthr[key])
+                    atomicAdd(&run[key], d.vw ? (unsigned long long)d.vw[pr * kRange + ul] : 1ull);
             }
         }
         __syncwarp();
     }
+    return has_tie;
+}
+
+// Approval of the candidate in this lane's slot of a 32-candidate chunk: above its key
+// block's threshold gain, or at it and within the block's remainder in id order (KEY_A:
+// the weight before it; otherwise: including its own weight).
+template <int KEY>
+__device__ __forceinline__ bool approve_slot(const Dev &d, int32_t range, const uint64_t *cand, int32_t ncand,
+                                             int idx, const ApplyInst &ai, unsigned long long *run, int &t,
+                                             int &key, int32_t &g, int &ul, unsigned long long &cw)
+{
+    const int lane = threadIdx.x & 31;
+    bool appr = false, tie = false;
+    t = 0; key = 0; g = 0; ul = 0; cw = 1;
+    if (idx < ncand) {
+        const bool in = decode_key<KEY>(cand[idx], key, t, g, ul);
+        if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
+        const int md = ai.mode[key];
+        if (in) {
+            if (md == SEL_ALL || g > ai.gthr[key]) appr = true;
+            else if (g == ai.gthr[key]) tie = true;
+        }
+    }
+    unsigned tm = __ballot_sync(kFull, tie);
+    while (tm) {
+        const int l = __ffs(tm) - 1;
+        tm &= tm - 1;
+        if (lane == l) {
+            appr = (long long)(run[key] + (KEY == KEY_A ? 0ull : cw)) <= ai.rem[key];
+            run[key] += cw;
+        }
+        __syncwarp();
+    }
+    return appr;
+}
+
+// One range item of the apply step (see k_apply).  KEY_T: LP (stamps the nets, records the
+// revert variant's source blocks); KEY_TS: rebalancing (no stamps).
+template <typename Rec, int KEY>
+__device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t r, bool any_thr,
+                                            const ApplyInst &ai, unsigned long long *run,
+                                            unsigned long long *bwd, ApplyWarp &w_, long long &idobj,
+                                            int32_t &iappr, int32_t &ipins)
+{
+    const int lane = threadIdx.x & 31;
+    Rec *recs = reinterpret_cast<Rec *>(d.rec);
+    const int32_t ncand = d.cand_cnt[range];
+    if (ncand == 0) return;
+    const uint64_t *cand = d.cand + (int64_t)range * kRange;
+    range_tie_prefix<KEY>(d, range, any_thr, ai, run, cand, ncand);
     for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
         const int idx = c0 + lane;
-        int t = 0, ul = 0;
-        int32_t g = 0;
-        unsigned long long cw = 1;
-        bool appr = false, tie = false;
-        if (idx < ncand) {
-            decode(cand[idx], t, g, ul);
-            if (d.vw) cw = (unsigned long long)d.vw[range * kRange + ul];
-            const int md = mode[t];
-            if (md == SEL_ALL || g > gthr[t]) appr = true;
-            else if (g == gthr[t]) tie = true;
-        }
-        // ties in id order: exclusive prefix so far + own weight must fit the budget
-        unsigned tm = __ballot_sync(kFull, tie);
-        while (tm) {
-            const int l = __ffs(tm) - 1;
-            tm &= tm - 1;
-            if (lane == l) {
-                appr = (long long)(run[t] + cw) <= rem[t];
-                run[t] += cw;
-            }
-            __syncwarp();
-        }
+        int t, key, ul;
+        int32_t g;
+        unsigned long long cw;
+        const bool appr = approve_slot<KEY>(d, range, cand, ncand, idx, ai, run, t, key, g, ul, cw);
         int32_t deg = 0, jb = 0, a = 0;
         if (appr) {
             const int32_t u = range * kRange + ul;
@@ -1079,7 +1155,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
             ++iappr;
             ipins += deg;
         }
-        if (d.rv_src && idx < ncand) d.rv_src[(int64_t)range * kRange + idx] = appr ? (uint8_t)a : kRvNone;
+        if (KEY == KEY_T && d.rv_src && idx < ncand) d.rv_src[(int64_t)range * kRange + idx] = appr ? (uint8_t)a : kRvNone;
         int32_t incl = deg;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1094,7 +1170,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
         if (lane == 31) w_.off[32] = total;
         __syncwarp();
         for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
-            idobj += apply_pins<Rec>(d, recs, w_, i0 + lane, total, r);
+            idobj += apply_pins<Rec, KEY == KEY_T>(d, recs, w_, i0 + lane, total, r);
         __syncwarp();
     }
 }
@@ -1105,7 +1181,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
 // same tile itself, so warps never wait for each other), then applies the approved moves
 // over their incidences flattened across the lanes, so all atomics are in flight at once.
 // B as for k_gain.
-template <typename Rec, bool B>
+template <typename Rec, bool B, int KEY = KEY_T>
 __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *devs, const int2 *items,
                                                        int32_t n_items, int32_t rr)
 {
@@ -1133,7 +1209,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 inst_prev = it.x;
             }
             const Dev &d = dsm[wid];
-            apply_range<Rec>(d, it.y, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            apply_range<Rec, KEY>(d, it.y, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
             for (int o = 16; o; o >>= 1) {
                 idobj += __shfl_xor_sync(kFull, idobj, o);
                 iappr += __shfl_xor_sync(kFull, iappr, o);
@@ -1152,7 +1228,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 if (idobj) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)idobj);
                 if (iappr) atomicAdd(row + ST_APPR, (unsigned long long)iappr);
                 if (ipins) atomicAdd(row + ST_MOVED, (unsigned long long)ipins);
-                if (ipins && d.rv_cnt) atomicAdd(d.rv_cnt, (unsigned long long)ipins);
+                if (KEY == KEY_T && ipins && d.rv_cnt) atomicAdd(d.rv_cnt, (unsigned long long)ipins);
             }
             __syncwarp();
         } else {
@@ -1160,7 +1236,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 any_thr = apply_refresh(d0, ai_w[wid], r);
                 inst_prev = 0;
             }
-            apply_range<Rec>(d0, item, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            apply_range<Rec, KEY>(d0, item, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
             dobj += idobj;
             nappr += iappr;
             npins += ipins;
@@ -1204,7 +1280,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 if (o1) atomicAdd(reinterpret_cast<unsigned long long *>(d0.obj), o1);
                 if (a1) atomicAdd(row + ST_APPR, a1);
                 if (p1) atomicAdd(row + ST_MOVED, p1);
-                if (p1 && d0.rv_cnt) atomicAdd(d0.rv_cnt, p1);
+                if (KEY == KEY_T && p1 && d0.rv_cnt) atomicAdd(d0.rv_cnt, p1);
             }
         }
     }
@@ -1433,7 +1509,7 @@ __global__ void __launch_bounds__(kThreads) k_rv_revert(const Dev d, int32_t rr)
 }
 
 // thread per instance: per-round objective and heaviest block; advance the round state
-__global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr)
+__global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr, int32_t advance = 1)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inst) return;
@@ -1443,8 +1519,44 @@ __global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr)
     for (int t = 0; t < d.k; ++t) mx = d.bw[t] > mx ? d.bw[t] : mx;
     row[ST_OBJ] = (unsigned long long)*d.obj;
     row[ST_MAXW] = (unsigned long long)mx;
-    d.rs[0] += 1;
-    d.rs[1] = 1;
+    if (advance) {
+        d.rs[0] += 1;
+        d.rs[1] = 1;
+    }
+}
+
+// Rebalancing, source side (KEY_A): warp per range; marks the candidates that may leave their
+// block (bit 24) and adds their weights to the per-target totals of the target-side stage.
+__global__ void __launch_bounds__(kThreads) k_rb_mark(const Dev d)
+{
+    __shared__ ApplyInst ai_w[kWarps];
+    __shared__ unsigned long long run_w[kWarps][64];
+    __shared__ unsigned long long tot_w[kWarps][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int32_t range = blockIdx.x * kWarps + wid;
+    if (range >= d.n_ranges) return;
+    const int32_t ncand = d.cand_cnt[range];
+    if (ncand == 0) return;
+    int32_t r;
+    const bool any_thr = apply_refresh(d, ai_w[wid], r);
+    tot_w[wid][lane] = 0;
+    tot_w[wid][lane + 32] = 0;
+    uint64_t *cand = d.cand + (int64_t)range * kRange;
+    range_tie_prefix<KEY_A>(d, range, any_thr, ai_w[wid], run_w[wid], cand, ncand);
+    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+        const int idx = c0 + lane;
+        int t, key, ul;
+        int32_t g;
+        unsigned long long cw;
+        const bool sel = approve_slot<KEY_A>(d, range, cand, ncand, idx, ai_w[wid], run_w[wid], t, key, g, ul, cw);
+        if (sel) {
+            cand[idx] |= kSelBit;
+            atomicAdd(&tot_w[wid][t], cw);
+        }
+    }
+    __syncwarp();
+    for (int t = lane; t < 64 && t < d.k; t += 32)
+        if (tot_w[wid][t]) atomicAdd(reinterpret_cast<unsigned long long *>(&d.tot[t]), tot_w[wid][t]);
 }
 
 __global__ void k_expand_candidates(const Dev *devs, int32_t *target, int64_t *gain)
@@ -1864,6 +1976,117 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 }
 
 }  // namespace hgp
+
+// ================================================================== rebalancing (Sec. 8)
+namespace {
+
+// one approval stage over all candidates of the sub-round, grouped by KEY
+template <int KEY>
+int64_t launch_stage(const Plan &p, bool levels)
+{
+    int64_t n = 0;
+    k_hist<KEY><<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, 0);
+    k_select<KEY><<<p.n_blocks, kThreads, 0, p.st>>>(p.devs, p.blocks, p.n_blocks, 0);
+    n += 2;
+    if (levels) {
+        for (int level = 1; level <= 3; ++level) {
+            k_hist<KEY><<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, level);
+            k_select<KEY><<<p.n_blocks, kThreads, 0, p.st>>>(p.devs, p.blocks, p.n_blocks, level);
+            n += 2;
+        }
+    }
+    k_tie_sum<KEY><<<p.n_tiles, kThreads, 0, p.st>>>(p.devs, p.tiles, p.n_tiles);
+    k_tie_scan<<<p.n_blocks, 1024, 0, p.st>>>(p.devs, p.blocks, p.n_blocks);
+    return n + 2;
+}
+
+// one rebalancing pass: S sub-rounds of gain (vertices of overloaded blocks), source-side
+// selection, target-side approval and apply, then the pass's objective and heaviest block
+template <typename Rec>
+cudaError_t launch_rebalance_pass(const Plan &p, int32_t pass, RbArgs rb, bool levels)
+{
+    k_round_prep<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, rb.r);
+    *p.launches += 1;
+    for (int32_t s = 0; s < p.S_max; ++s) {
+        k_gain<Rec, false, true><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, pass, rb);
+        *p.launches += 1;
+        *p.launches += launch_stage<KEY_A>(p, levels);
+        k_rb_mark<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.d0);
+        *p.launches += 1;
+        *p.launches += launch_stage<KEY_TS>(p, levels);
+        k_apply<Rec, false, KEY_TS><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, pass);
+        *p.launches += 1;
+    }
+    k_round_end<<<1, 128, 0, p.st>>>(p.devs, 1, pass, 0);
+    *p.launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats *stats, int32_t *phases,
+                             int32_t *num_passes)
+{
+    if (!h || max_passes < 0) return HGP_ERR_INVALID;
+    if (num_passes) *num_passes = 0;
+    if (max_passes == 0) return HGP_OK;
+    // phase-2 priorities are gain + W_max in [0, 2 W_max]; they must fit the 31-bit gain field
+    const int64_t off = h->max_vertex_netweight;
+    if (2 * off >= ((int64_t)1 << 31)) return HGP_ERR_UNSUPPORTED;
+    int rc = ensure_stats(h, max_passes);
+    if (rc != HGP_OK) return rc;
+    cudaError_t e = sync_dev(h);
+    const cudaStream_t st = h->stream;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d.stats, 0, sizeof(int64_t) * ST_N * (size_t)max_passes, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    Plan p = single_plan(h);
+    p.prof = nullptr;
+    std::vector<int32_t> ph;
+    int32_t phase = 1, pass = 0;
+    while (pass < max_passes && e == cudaSuccess) {
+        int64_t bw[64];
+        e = cudaMemcpyAsync(bw, h->d.bw, sizeof(int64_t) * (size_t)h->d.k, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        int64_t heaviest = 0;
+        for (int i = 0; i < h->d.k; ++i) heaviest = bw[i] > heaviest ? bw[i] : heaviest;
+        if (heaviest <= h->d.lmax) break;
+        RbArgs rb;
+        rb.r = (1 << 30) + pass;
+        rb.phase = phase;
+        rb.off = phase == 2 ? (int32_t)off : 0;
+        const bool levels = (phase == 2 ? 2 * off : off) >= kBins - 1;
+        e = p.rec32 ? launch_rebalance_pass<Rec32>(p, pass, rb, levels)
+                    : launch_rebalance_pass<Rec16>(p, pass, rb, levels);
+        int64_t appr = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&appr, h->d.stats + (int64_t)pass * ST_N + ST_APPR, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        ph.push_back(phase);
+        ++pass;
+        if (appr == 0) {
+            if (phase == 2) break;
+            phase = 2;
+        }
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    if (pass > 0 && stats) {
+        rc = copy_stats_out(h, pass, stats);
+        if (rc != HGP_OK) return rc;
+    }
+    if (phases)
+        for (int32_t i = 0; i < pass; ++i) phases[i] = ph[i];
+    if (num_passes) *num_passes = pass;
+    return HGP_OK;
+}
 
 // ================================================================== batch of handles
 struct hgp_batch {

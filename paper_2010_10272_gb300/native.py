@@ -87,6 +87,7 @@ def load_library():
         lib.hgp_get_info.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
         lib.hgp_exact_gains.argtypes = [P, i32, P, P]
+        lib.hgp_rebalance.argtypes = [P, i32, P, P, P]
         lib.hgp_exact_gains.restype = ctypes.c_int
         lib.hgp_export_state.argtypes = [P, P, P, P, P]
         lib.hgp_import_state.argtypes = [P, P, P, i64, i32]
@@ -282,6 +283,19 @@ class HGP:
         _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
                "hgp_debug_candidates")
         return t, g
+
+    def rebalance(self, max_passes: int):
+        """Rebalancing passes (Sec. 8); returns (stats [passes x 7] int64 (STAT_FIELDS),
+        phases [passes] int32)."""
+        buf = (RoundStats * max(1, max_passes))()
+        ph = np.zeros(max(1, max_passes), dtype=np.int32)
+        n = ctypes.c_int32(0)
+        _check(self._lib.hgp_rebalance(self._h, int(max_passes), buf, _hptr(ph), ctypes.byref(n)),
+               "hgp_rebalance")
+        p = n.value
+        st = np.array([[getattr(buf[i], f) for f in STAT_FIELDS] for i in range(p)],
+                      dtype=np.int64).reshape(p, len(STAT_FIELDS))
+        return st, ph[:p].copy()
 
     def exact_gains(self, moves) -> np.ndarray:
         """Gains of a move sequence [(u, from, to), ...] performed in order (Lemma 1)."""
