@@ -255,7 +255,7 @@ def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None, 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    if args.workload in ("batch", "serving"):
+    if args.workload in ("batch", "serving", "rebalance"):
         args.workload = "small"
     value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup,
                                                 variant=args.variant)
@@ -504,6 +504,120 @@ def run_batch(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------------------------------ rebalancing
+def run_rebalance(args, world, rank, local):
+    """Rebalancing (Sec. 8) of the power-law instance from an overloaded start: the planted
+    partition with a hash-chosen `--skew` fraction of the vertices moved into block 0.  A step
+    resets that start (untimed) and runs hgp_rebalance until balanced (at most 64 passes).
+    value = pins x passes / s (the unit of an LP round)."""
+    import torch
+    from paper_2010_10272_gb300 import HGP, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    t_gen = time.perf_counter()
+    hg = load_instance("powerlaw", args.scale)
+    t_gen = time.perf_counter() - t_gen
+    S, P = args.subrounds, hg.num_pins
+    part = hg.part.copy()
+    pick = (np.arange(hg.n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(40)
+    part[pick < np.uint64(int(args.skew * (1 << 24)))] = 0
+    to_dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d_part = to_dev(part)
+    h = HGP(hg.n, hg.m, to_dev(hg.net_off), to_dev(hg.pins), hg.k, hg.eps, d_part, to_dev(hg.vertex_w),
+            to_dev(hg.net_w), subrounds=S, device=True, stream=stream)
+    info = h.info()
+    w0 = h.block_weights()
+    max_passes = 64
+
+    def step(ev=None):
+        h.set_partition(d_part, device=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        if ev is not None:
+            ev[0].record(stream)
+        st, ph = h.rebalance(max_passes)
+        if ev is not None:
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return st, ph
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, launches = [], 0
+    for _ in range(args.steps):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        l0 = h.launch_count()
+        st, ph = step(ev)
+        launches += h.launch_count() - l0
+        ms.append(ev[0].elapsed_time(ev[1]))
+    clocks = sampler.stop()
+    passes = int(st.shape[0])
+    total_ms = max_over_ranks(sum(ms), world)
+    value = world * args.steps * P * passes / (total_ms / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hp = [pin(hg.net_off), pin(hg.pins), pin(part), pin(hg.vertex_w), pin(hg.net_w)]
+        h2d = sum(a.nbytes for a in hp if a is not None)
+        h.close()
+        torch.cuda.empty_cache()
+        times = []
+        for i in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2 = HGP(hg.n, hg.m, hp[0], hp[1], hg.k, hg.eps, hp[2], hp[3], hp[4], subrounds=S, stream=stream)
+            st2, _ = h2.rebalance(max_passes)
+            out = h2.partition()
+            t1 = time.perf_counter()
+            h2.close()
+            if i > 0:
+                times.append(t1 - t0)
+            del out
+        e2e_t = max_over_ranks(statistics.mean(times), world)
+        e2e = {"value": world * P * int(st2.shape[0]) / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": hg.n * 4 + max_passes * (8 * 7 + 4), "ms_per_step": e2e_t * 1e3,
+               "steps": args.e2e_steps}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        scale = SAMPLE_SCALE["powerlaw"]
+        hs_ = load_instance("powerlaw", scale)
+        ps = hs_.part.copy()
+        pk = (np.arange(hs_.n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(40)
+        ps[pk < np.uint64(int(args.skew * (1 << 24)))] = 0
+        o = oracle.Oracle.from_hypergraph(hs_, subrounds=S, part=ps)
+        t0 = time.perf_counter()
+        ost, _, _ = o.rebalance(max_passes)
+        dt = time.perf_counter() - t0
+        o.close()
+        cpu = {"value": hs_.num_pins * max(1, ost.shape[0]) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{hs_.name} with the same skew (scale {scale:g}): {ost.shape[0]} passes in {dt:.1f} s"}
+    line = {
+        "metric": "rebalance pins/s per pass", "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["powerlaw"][1] + f", {args.skew:g} of the vertices moved into block 0",
+                   "n": hg.n, "m": hg.m, "pins": P, "k": hg.k, "lmax": info["lmax"], "subrounds": S,
+                   "start_heaviest_block": int(w0.max()), "parallelism": f"replicas x{world}",
+                   "step": "reset the overloaded start (untimed) + hgp_rebalance until balanced",
+                   "l2": "inputs larger than L2"},
+        "passes": passes, "phases": ph.tolist(), "moved": st[:, 2].tolist(),
+        "heaviest_after_pass": st[:, 4].tolist(), "objective_after_pass": st[:, 0].tolist(),
+        "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks,
+        "setup_s": {"generate_or_load": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------------ serving workload
 def run_serving(args, world, rank, local):
     """Poisson arrivals of refinement requests (planted, pins log-uniform 1e4-5e6, k in
@@ -585,7 +699,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving"], default="powerlaw")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving", "rebalance"],
+                    default="powerlaw")
+    ap.add_argument("--skew", type=float, default=0.2,
+                    help="rebalance workload: fraction of the vertices moved into block 0")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--serve-seed", type=int, default=1)
@@ -608,6 +725,8 @@ def main():
         rc = run_batch(args, world, rank, local)
     elif args.workload == "serving":
         rc = run_serving(args, world, rank, local)
+    elif args.workload == "rebalance":
+        rc = run_rebalance(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

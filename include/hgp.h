@@ -282,9 +282,10 @@ int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, con
  * than L_max, at most max_passes.  A pass splits the vertices into the handle's S sub-rounds
  * (hash round number 2^30 + pass index).  In a sub-round, against the state at its start,
  * every vertex u of an overloaded block a picks the block t != a with room (w(t) + c(u) <=
- * L_max) of highest gain (smaller id on ties).  Phase 1 keeps only gains >= 0 (the paper's
- * immediate non-negative moves); after a phase-1 pass without moves, phase 2 keeps any gain
- * (least connectivity increase first).  Candidates are ordered by (gain desc, id asc); per
+ * L_max) of highest gain (smaller id on ties).  The first pass is phase 1, which keeps only
+ * gains >= 0 (the paper's one sweep of immediate non-negative moves); later passes are phase
+ * 2, which keeps any gain (least connectivity increase first).  Candidates are ordered by
+ * (gain desc, id asc); per
  * source block, a candidate passes while the weight that left before it is below
  * w(a) - L_max; per target block, passing candidates are approved while their inclusive
  * prefix fits L_max - w(t).  A phase-2 pass without moves ends the call.  Rebalancing moves

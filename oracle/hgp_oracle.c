@@ -403,8 +403,9 @@ static int64_t heaviest_block(const oracle_t *o)
  * w(a) - L_max (its block is still overloaded when it leaves).  Target side: selected
  * candidates are approved while the inclusive prefix of their weights fits L_max - w(t).
  * Approved moves are applied; they do not count as moves for LP eligibility.
- * Passes run while a block is overloaded and at most max_passes times; phase 1 switches to
- * phase 2 after a pass without moves, and a phase-2 pass without moves ends it.
+ * Passes run while a block is overloaded and at most max_passes times: the first pass is
+ * phase 1 (one sweep over all vertices, as in the paper), every later pass is phase 2, and a
+ * phase-2 pass without moves ends it.
  * stats: NULL or [max_passes * ST_COUNT] per pass; phases: NULL or [max_passes].
  * moves as in oracle_refine (first field = pass * S + sub-round).  Returns 0, -1 on failure. */
 int oracle_rebalance(oracle_t *o, int32_t max_passes, int64_t *stats, int32_t *phases,
@@ -486,10 +487,8 @@ int oracle_rebalance(oracle_t *o, int32_t max_passes, int64_t *stats, int32_t *p
         }
         if (phases) phases[pass] = phase;
         pass++;
-        if (n_appr == 0) {
-            if (phase == 2) break;
-            phase = 2;
-        }
+        if (phase == 1) phase = 2;
+        else if (n_appr == 0) break;
     }
     if (num_passes) *num_passes = pass;
     if (num_moves) *num_moves = logged;

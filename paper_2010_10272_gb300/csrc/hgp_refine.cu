@@ -2069,10 +2069,8 @@ extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats 
         if (e != cudaSuccess) break;
         ph.push_back(phase);
         ++pass;
-        if (appr == 0) {
-            if (phase == 2) break;
-            phase = 2;
-        }
+        if (phase == 1) phase = 2;
+        else if (appr == 0) break;
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

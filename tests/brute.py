@@ -240,8 +240,8 @@ def rebalance(t: Tiny, part, max_passes: int, S: int = 4, seed: int = 0):
         stats.append((t.objective(part), n_cand, n_appr, n_cons, max(t.block_weights(part))))
         phases.append(phase)
         p += 1
-        if n_appr == 0:
-            if phase == 2:
-                break
+        if phase == 1:
             phase = 2
+        elif n_appr == 0:
+            break
     return part, stats, phases, log

@@ -65,6 +65,8 @@ MUTANTS = [
      "move_vertex_marked(o, u, t, 0); for (int64_t jj = o->vtx_off[u]; jj < o->vtx_off[u + 1]; ++jj) o->moved_prev[o->inc[jj]] = 1;"),
     ("rebalance tie to larger block", "if (best_t < 0 || g > best_g) { best_t = i; best_g = g; }",
      "if (best_t < 0 || g >= best_g) { best_t = i; best_g = g; }"),
+    ("rebalance repeats phase 1", "if (phase == 1) phase = 2;\n        else if (n_appr == 0) break;",
+     "if (n_appr == 0) { if (phase == 2) break; phase = 2; }"),
     ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
      "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
 ]

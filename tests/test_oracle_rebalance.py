@@ -45,6 +45,19 @@ def test_hand_example_non_negative_first():
     assert [tuple(x) for x in mv.tolist()] == [(0, 0, 0, 1)]
 
 
+def test_hand_example_single_phase_one_sweep():
+    # Path 0-1-2-3 (unit nets) and isolated 4, all in block 0; k = 2, eps = 0, c(V) = 5,
+    # L_max = 3.  Pass 0 (phase 1): only vertex 4 has a non-negative gain (0) and moves; block
+    # 0 still weighs 4.  Phase 1 is one sweep, so pass 1 is phase 2: gains -1 (ends 0, 3) and -2
+    # (1, 2); order 0, 3, 1, 2; block 0 sheds 1: vertex 0 moves, cutting net {0,1}.
+    t = Tiny(5, [[0, 1], [1, 2], [2, 3]], 2, 0.0)
+    o = _oracle(t, [0] * 5, S=1)
+    st, ph, mv = o.rebalance(5, log_moves=True)
+    assert ph.tolist() == [1, 2]
+    assert st.tolist() == [[0, 1, 1, 5, 4], [1, 4, 1, 4, 3]]
+    assert [tuple(x) for x in mv.tolist()] == [(0, 4, 0, 1), (1, 0, 0, 1)]
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_matches_bruteforce(seed):
     rng = np.random.default_rng(1200 + seed)
