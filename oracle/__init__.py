@@ -72,6 +72,11 @@ def _load():
         for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
             getattr(lib, name).argtypes = [P, P]
         lib.oracle_set_variant.argtypes = [P, i32, i32]
+        lib.oracle_contract.restype = ctypes.c_int
+        lib.oracle_contract.argtypes = [i32, i32, P, P, P, P, P, ctypes.POINTER(P)]
+        lib.oracle_coarse_destroy.argtypes = [P]
+        lib.oracle_coarse_sizes.argtypes = [P, P, P, P]
+        lib.oracle_coarse_copy.argtypes = [P, P, P, P, P, P]
         lib.oracle_rebalance.restype = ctypes.c_int
         lib.oracle_rebalance.argtypes = [P, i32, P, P, P, P, i64, P]
         lib.oracle_exact_gains.restype = ctypes.c_int
@@ -241,3 +246,29 @@ def sample_candidates(hg, sample, s: int = 0, subrounds: int = 4, seed: int = 0,
     if rc != 0:
         raise MemoryError("oracle_sample_candidates failed")
     return t, g
+
+
+def contract(n, m, net_off, pins, vertex_w, net_w, cluster) -> dict:
+    """Coarse hypergraph of a clustering (Sec. 3.2): dict with n, m, net_off int64[m+1],
+    pins int32, vertex_w int64[n], net_w int64[m] and map int32[fine n]."""
+    lib = _load()
+    keep = [_c(net_off, np.int64), _c(pins, np.int32), _c(vertex_w, np.int32), _c(net_w, np.int32),
+            _c(cluster, np.int32)]
+    h = ctypes.c_void_p()
+    rc = lib.oracle_contract(int(n), int(m), *[_ptr(x) for x in keep], ctypes.byref(h))
+    if rc == -2:
+        raise ValueError("cluster id outside [0, n)")
+    if rc != 0:
+        raise MemoryError("oracle_contract failed")
+    try:
+        n2, m2, p2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        lib.oracle_coarse_sizes(h, ctypes.byref(n2), ctypes.byref(m2), ctypes.byref(p2))
+        out = {"n": n2.value, "m": m2.value,
+               "net_off": np.zeros(m2.value + 1, np.int64), "pins": np.zeros(p2.value, np.int32),
+               "vertex_w": np.zeros(n2.value, np.int64), "net_w": np.zeros(m2.value, np.int64),
+               "map": np.zeros(int(n), np.int32)}
+        lib.oracle_coarse_copy(h, _ptr(out["net_off"]), _ptr(out["pins"]), _ptr(out["vertex_w"]),
+                               _ptr(out["net_w"]), _ptr(out["map"]))
+    finally:
+        lib.oracle_coarse_destroy(h)
+    return out

@@ -610,3 +610,163 @@ int oracle_exact_gains(const oracle_t *o, int32_t count, const int32_t *moves, i
     free(phi); free(part); free(seen);
     return rc;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Contraction (Sec. 3.2): coarse hypergraph of a vertex clustering.
+ *   cluster ids (values in [0, n)) are remapped to 0..n'-1 in increasing order (a prefix sum
+ *   over the used ids); c'(C) = sum of c(u) over the cluster; every net's pins are mapped to
+ *   their clusters, sorted and de-duplicated; nets left with fewer than two pins are removed;
+ *   identical nets (equal sorted pin lists) become one net whose weight is the sum of theirs,
+ *   kept at the position of the smallest original net id; the coarse nets keep the order of
+ *   those representatives.  map[u] = coarse id of u.
+ */
+typedef struct {
+    int32_t n, m;
+    int64_t P;
+    int64_t *net_off;   /* [m+1] */
+    int32_t *pins;      /* [P] */
+    int64_t *vw;        /* [n] */
+    int64_t *nw;        /* [m] */
+    int32_t *map;       /* [fine n] */
+    int32_t fine_n;
+} oracle_coarse_t;
+
+static int cmp_i32(const void *x, const void *y)
+{
+    const int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* context for ordering nets by (size, pin list, original id) */
+static const int64_t *g_ct_off;
+static const int32_t *g_ct_pins;
+static int by_pin_list(const void *x, const void *y)
+{
+    const int32_t e = *(const int32_t *)x, f = *(const int32_t *)y;
+    const int64_t se = g_ct_off[e + 1] - g_ct_off[e], sf = g_ct_off[f + 1] - g_ct_off[f];
+    if (se != sf) return se < sf ? -1 : 1;
+    for (int64_t j = 0; j < se; ++j) {
+        const int32_t a = g_ct_pins[g_ct_off[e] + j], b = g_ct_pins[g_ct_off[f] + j];
+        if (a != b) return a < b ? -1 : 1;
+    }
+    return (e > f) - (e < f);
+}
+
+void oracle_coarse_destroy(oracle_coarse_t *c)
+{
+    if (!c) return;
+    free(c->net_off); free(c->pins); free(c->vw); free(c->nw); free(c->map);
+    free(c);
+}
+
+/* Returns 0, -1 on allocation failure, -2 on a cluster id outside [0, n). */
+int oracle_contract(int32_t n, int32_t m, const int64_t *net_off, const int32_t *pins,
+                    const int32_t *vertex_w, const int32_t *net_w, const int32_t *cluster,
+                    oracle_coarse_t **out)
+{
+    *out = NULL;
+    for (int32_t u = 0; u < n; ++u) if (cluster[u] < 0 || cluster[u] >= n) return -2;
+    const int64_t P = net_off[m];
+    oracle_coarse_t *c = (oracle_coarse_t *)calloc(1, sizeof(oracle_coarse_t));
+    int32_t *cid = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int64_t *off1 = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+    int32_t *pins1 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)P + 1));
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m + 1));
+    int32_t *rep = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m + 1));
+    int64_t *wsum = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    if (!c || !cid || !off1 || !pins1 || !order || !rep || !wsum) goto oom;
+    c->fine_n = n;
+    /* (1) remap the used cluster ids by a prefix sum */
+    for (int32_t i = 0; i <= n; ++i) cid[i] = 0;
+    for (int32_t u = 0; u < n; ++u) cid[cluster[u]] = 1;
+    {
+        int32_t run = 0;
+        for (int32_t i = 0; i < n; ++i) { const int32_t used = cid[i]; cid[i] = run; run += used; }
+        c->n = run;
+    }
+    c->map = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    c->vw = (int64_t *)calloc((size_t)c->n + 1, sizeof(int64_t));
+    if (!c->map || !c->vw) goto oom;
+    /* (2) cluster weights */
+    for (int32_t u = 0; u < n; ++u) {
+        c->map[u] = cid[cluster[u]];
+        c->vw[c->map[u]] += vertex_w ? vertex_w[u] : 1;
+    }
+    /* (3) pins mapped, sorted and de-duplicated per net */
+    off1[0] = 0;
+    for (int32_t e = 0; e < m; ++e) {
+        int64_t w = off1[e];
+        for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) pins1[w++] = c->map[pins[j]];
+        qsort(pins1 + off1[e], (size_t)(w - off1[e]), sizeof(int32_t), cmp_i32);
+        int64_t k = off1[e];
+        for (int64_t j = off1[e]; j < w; ++j)
+            if (j == off1[e] || pins1[j] != pins1[j - 1]) pins1[k++] = pins1[j];
+        off1[e + 1] = k;
+    }
+    /* (4) nets with at least two pins, grouped by identical pin lists */
+    int32_t kept = 0;
+    for (int32_t e = 0; e < m; ++e) {
+        rep[e] = -1;
+        if (off1[e + 1] - off1[e] >= 2) order[kept++] = e;
+    }
+    g_ct_off = off1;
+    g_ct_pins = pins1;
+    qsort(order, (size_t)kept, sizeof(int32_t), by_pin_list);
+    for (int32_t i = 0; i < kept; ++i) {
+        const int32_t e = order[i];
+        int same = 0;
+        if (i > 0) {
+            const int32_t f = order[i - 1];
+            const int64_t s = off1[e + 1] - off1[e];
+            same = s == off1[f + 1] - off1[f] &&
+                   memcmp(pins1 + off1[e], pins1 + off1[f], sizeof(int32_t) * (size_t)s) == 0;
+        }
+        rep[e] = same ? rep[order[i - 1]] : e;   /* the group's first = its smallest id */
+        wsum[rep[e]] += net_w ? net_w[e] : 1;
+    }
+    /* (5) coarse nets: the representatives in original order */
+    {
+        int32_t m2 = 0;
+        int64_t P2 = 0;
+        for (int32_t e = 0; e < m; ++e)
+            if (rep[e] == e) { m2++; P2 += off1[e + 1] - off1[e]; }
+        c->m = m2;
+        c->P = P2;
+        c->net_off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m2 + 1));
+        c->pins = (int32_t *)malloc(sizeof(int32_t) * ((size_t)P2 + 1));
+        c->nw = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m2 + 1));
+        if (!c->net_off || !c->pins || !c->nw) goto oom;
+        int32_t i2 = 0;
+        c->net_off[0] = 0;
+        for (int32_t e = 0; e < m; ++e) {
+            if (rep[e] != e) continue;
+            const int64_t s = off1[e + 1] - off1[e];
+            memcpy(c->pins + c->net_off[i2], pins1 + off1[e], sizeof(int32_t) * (size_t)s);
+            c->nw[i2] = wsum[e];
+            c->net_off[i2 + 1] = c->net_off[i2] + s;
+            i2++;
+        }
+    }
+    free(cid); free(off1); free(pins1); free(order); free(rep); free(wsum);
+    *out = c;
+    return 0;
+oom:
+    free(cid); free(off1); free(pins1); free(order); free(rep); free(wsum);
+    oracle_coarse_destroy(c);
+    return -1;
+}
+
+void oracle_coarse_sizes(const oracle_coarse_t *c, int32_t *n, int32_t *m, int64_t *P)
+{
+    *n = c->n; *m = c->m; *P = c->P;
+}
+
+void oracle_coarse_copy(const oracle_coarse_t *c, int64_t *net_off, int32_t *pins, int64_t *vw,
+                        int64_t *nw, int32_t *map)
+{
+    memcpy(net_off, c->net_off, sizeof(int64_t) * ((size_t)c->m + 1));
+    memcpy(pins, c->pins, sizeof(int32_t) * (size_t)c->P);
+    memcpy(vw, c->vw, sizeof(int64_t) * (size_t)c->n);
+    memcpy(nw, c->nw, sizeof(int64_t) * (size_t)c->m);
+    memcpy(map, c->map, sizeof(int32_t) * (size_t)c->fine_n);
+}

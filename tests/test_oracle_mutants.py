@@ -18,7 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "hgp_oracle.c")
 
 # the pin suites run against each mutant
-PIN_FILES = ("test_oracle_pins.py", "test_oracle_rebalance.py", "test_oracle_exact_gains.py")
+PIN_FILES = ("test_oracle_pins.py", "test_oracle_rebalance.py", "test_oracle_exact_gains.py",
+             "test_oracle_contract.py")
 
 # (name, exact text in the oracle source, replacement)
 MUTANTS = [
@@ -67,6 +68,14 @@ MUTANTS = [
      "if (best_t < 0 || g >= best_g) { best_t = i; best_g = g; }"),
     ("rebalance repeats phase 1", "if (phase == 1) phase = 2;\n        else if (n_appr == 0) break;",
      "if (n_appr == 0) { if (phase == 2) break; phase = 2; }"),
+    ("contraction keeps single-pin nets", "if (off1[e + 1] - off1[e] >= 2) order[kept++] = e;",
+     "if (off1[e + 1] - off1[e] >= 1) order[kept++] = e;"),
+    ("contraction keeps duplicate pins", "if (j == off1[e] || pins1[j] != pins1[j - 1]) pins1[k++] = pins1[j];",
+     "pins1[k++] = pins1[j];"),
+    ("identical nets not merged", "rep[e] = same ? rep[order[i - 1]] : e;", "rep[e] = e;"),
+    ("identical net weights not summed", "wsum[rep[e]] += net_w ? net_w[e] : 1;",
+     "if (rep[e] == e) wsum[e] = net_w ? net_w[e] : 1;"),
+    ("cluster ids not remapped in order", "c->map[u] = cid[cluster[u]];", "c->map[u] = c->n - 1 - cid[cluster[u]];"),
     ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
      "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
 ]
