@@ -299,6 +299,38 @@ int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats *stats, int
                   int32_t *num_passes);
 
 /*
+ * Contraction (paper Sec. 3.2): the coarse hypergraph of a vertex clustering.
+ * Inputs are DEVICE arrays (as for hgp_create_device): net_off int64[m+1], pins int32[P]
+ * (P = net_off[m] < 2^31), vertex_w / net_w int32 or NULL (unit), cluster int32[n] with values
+ * in [0, n).  Cluster ids are remapped to 0..n'-1 in increasing order; the coarse weight of a
+ * cluster is the sum of its vertex weights; every net's pins are mapped to their clusters,
+ * sorted and de-duplicated; nets left with fewer than two pins are dropped; identical nets
+ * (equal sorted pin lists) become one net whose weight is the sum of theirs, at the position
+ * of the smallest original net id, and the coarse nets keep the order of those nets.
+ * Runs on cuda_stream (NULL: the legacy default stream) and synchronises it; on success *out
+ * owns the coarse arrays on the current device (release with hgp_coarse_destroy).
+ * HGP_ERR_INVALID for a cluster id out of range; HGP_ERR_UNSUPPORTED when a coarse vertex or
+ * net weight reaches 2^31 or P >= 2^31.  The coarse arrays are valid inputs of
+ * hgp_create_device (pins strictly increasing inside each net).
+ */
+typedef struct hgp_coarse hgp_coarse;
+int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const int32_t *pins,
+                 const int32_t *vertex_w, const int32_t *net_w, const int32_t *cluster,
+                 void *cuda_stream, hgp_coarse **out);
+/* n', m' and P' of the coarse hypergraph. */
+int hgp_coarse_get_sizes(const hgp_coarse *c, int32_t *n, int32_t *m, int64_t *num_pins);
+/* Device pointers owned by c (any may be NULL): net_off int64[m'+1], pins int32[P'],
+ * vertex_w int32[n'], net_w int32[m'], map int32[n] (coarse id of every fine vertex). */
+int hgp_coarse_get_device_arrays(const hgp_coarse *c, const int64_t **net_off, const int32_t **pins,
+                                 const int32_t **vertex_w, const int32_t **net_w, const int32_t **map);
+/* Copies the coarse arrays to host buffers of the sizes above (any may be NULL). */
+int hgp_coarse_copy_to_host(const hgp_coarse *c, int64_t *net_off, int32_t *pins, int32_t *vertex_w,
+                            int32_t *net_w, int32_t *map);
+/* fine_part[u] = coarse_part[map[u]] (device int32 arrays of n' and n entries). */
+int hgp_coarse_project(const hgp_coarse *c, const int32_t *coarse_part, int32_t *fine_part);
+void hgp_coarse_destroy(hgp_coarse *c);
+
+/*
  * Exact gains of a move sequence (paper Sec. 5.4, Lemma 1), computed in parallel.
  * moves: host int32[count][3] = (u, from, to) in sequence order, every vertex at most once,
  * from = its current block, to != from.  gains: host int64[count], gains[j] = the gain (Sec. 5)

@@ -1,0 +1,645 @@
+// libhgp: contraction of a vertex clustering into a coarse hypergraph (paper Sec. 3.2).
+//
+//   1. used cluster ids flagged and remapped to 0..n'-1 by an exclusive prefix sum;
+//   2. coarse vertex weights by atomic adds (checked to fit int32);
+//   3. every net's pins mapped to coarse ids, sorted and de-duplicated: a warp per net with at
+//      most 32 pins (bitonic sort in registers), a CTA per larger net (stable LSD radix sort of
+//      its segment in global memory, 8-bit digits, then an order-preserving compaction);
+//   4. nets with fewer than two pins dropped; identical nets found through a 64-bit
+//      fingerprint table (key -> smallest net id) and an exact comparison with that net; a
+//      net that only shares the fingerprint stays unresolved and takes part in the next round
+//      (each round resolves the smallest net of every remaining fingerprint group);
+//   5. the representatives (smallest id of each identical group) keep their original order;
+//      their weights are the sums over the group; offsets by prefix sums.
+// Everything is integer and the output is unique: pins sorted inside each net, nets ordered by
+// their smallest original id.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "hgp_host.cuh"
+
+using namespace hgp;
+
+struct hgp_coarse {
+    int32_t fine_n = 0, n = 0, m = 0;
+    int64_t P = 0;
+    int64_t *net_off = nullptr;   // device [m+1]
+    int32_t *pins = nullptr;      // device [P]
+    int32_t *vw = nullptr;        // device [n]
+    int32_t *nw = nullptr;        // device [m]
+    int32_t *map = nullptr;       // device [fine_n]
+    cudaStream_t stream = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kScanTile = 1024;
+constexpr int kSortThreads = 256;
+constexpr int kSmallNet = 32;
+constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr int32_t kUnresolved = -2, kDropped = -1;
+
+int grid_of(int64_t work, int threads)
+{
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 16) g = 65535LL * 16;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- device-wide exclusive scan
+// out[0..len] = exclusive prefix sums of in[0..len-1] (out[len] = total)
+template <typename T>
+__global__ void __launch_bounds__(kScanTile) k_scan_tile(const T *in, int64_t len, int64_t *out, int64_t *sums)
+{
+    __shared__ int64_t wt[32];
+    const int64_t i = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t v = i < len ? (int64_t)in[i] : 0;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int64_t t = wt[lane];
+        int64_t s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        wt[lane] = s - t;
+        if (lane == 31) sums[blockIdx.x] = s;
+    }
+    __syncthreads();
+    if (i <= len) out[i] = wt[wid] + x - v;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t len, const int64_t *block_prefix)
+{
+    const int64_t i = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+    if (i <= len) out[i] += block_prefix[blockIdx.x];
+}
+
+// exclusive scan with the total at out[len]; out has len + 1 entries
+template <typename T>
+cudaError_t scan_excl(const T *in, int64_t len, int64_t *out, cudaStream_t st)
+{
+    const int64_t tiles = len / kScanTile + 1;   // covers indices 0..len
+    int64_t *sums = nullptr, *pref = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&sums), sizeof(int64_t) * (size_t)tiles, st);
+    if (e != cudaSuccess) return e;
+    k_scan_tile<T><<<(unsigned)tiles, kScanTile, 0, st>>>(in, len, out, sums);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && tiles > 1) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&pref), sizeof(int64_t) * (size_t)(tiles + 1), st);
+        if (e == cudaSuccess) e = scan_excl<int64_t>(sums, tiles, pref, st);
+        if (e == cudaSuccess) {
+            k_scan_add<<<(unsigned)tiles, kScanTile, 0, st>>>(out, len, pref);
+            e = cudaGetLastError();
+        }
+        if (pref) cudaFreeAsync(pref, st);
+    }
+    cudaFreeAsync(sums, st);
+    return e;
+}
+
+// ---------------------------------------------------------------- input checks
+// offsets non-decreasing from 0 to P, pins in [0, n), weights >= 1
+__global__ void k_ct_check(const int64_t *off, const int32_t *pins, const int32_t *vw, const int32_t *nw,
+                           int32_t n, int32_t m, int64_t P, int32_t *err)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t e = t; e < m; e += stride) {
+        if (off[e] < 0 || off[e] > off[e + 1] || off[e + 1] > P || (e == 0 && off[0] != 0)) atomicOr(err, ERR_INVALID);
+        if (nw && nw[e] < 1) atomicOr(err, ERR_INVALID);
+    }
+    for (int64_t j = t; j < P; j += stride)
+        if (pins[j] < 0 || pins[j] >= n) atomicOr(err, ERR_INVALID);
+    if (vw)
+        for (int64_t u = t; u < n; u += stride)
+            if (vw[u] < 1) atomicOr(err, ERR_INVALID);
+}
+
+// ---------------------------------------------------------------- clusters and weights
+__global__ void k_ct_flag(const int32_t *cluster, int32_t n, int32_t *used, int32_t *err)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cluster[u];
+        if (c < 0 || c >= n) atomicOr(err, ERR_INVALID);
+        else used[c] = 1;
+    }
+}
+
+__global__ void k_ct_map(const int32_t *cluster, int32_t n, const int64_t *cid, const int32_t *vw,
+                         int32_t *map, unsigned long long *w64)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = (int32_t)cid[cluster[u]];
+        map[u] = c;
+        atomicAdd(&w64[c], (unsigned long long)(vw ? vw[u] : 1));
+    }
+}
+
+__global__ void k_ct_narrow(const unsigned long long *w64, int64_t len, int32_t *out, int32_t *err)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long w = w64[i];
+        if (w >= (1ull << 31)) atomicOr(err, ERR_UNSUPPORTED);
+        out[i] = (int32_t)w;
+    }
+}
+
+// ---------------------------------------------------------------- per-net sort + dedupe
+// warp per net with at most 32 pins: bitonic sort of the mapped pins across the lanes, then the
+// first of every run of equal values is kept, in order, at the start of the net's segment
+__global__ void k_ct_small(const int64_t *off, const int32_t *pins, int32_t m, const int32_t *map,
+                           int32_t *out, int32_t *size1)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        if (s > kSmallNet) continue;
+        int32_t v = lane < s ? map[pins[b + lane]] : 0x7fffffff;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t o = __shfl_xor_sync(kFull, v, j);
+                const bool up = (lane & k) == 0;            // ascending run of the merge
+                const bool low = (lane & j) == 0;           // lower partner of the pair
+                v = (low == up) ? min(v, o) : max(v, o);
+            }
+        }
+        const int32_t prev = __shfl_up_sync(kFull, v, 1);
+        const bool keep = lane < s && (lane == 0 || v != prev);
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) out[b + __popc(km & ((1u << lane) - 1))] = v;
+        if (lane == 0) size1[e] = __popc(km);
+    }
+}
+
+// CTA per net with more than 32 pins: stable LSD radix sort of the mapped pins of the net's
+// segment (8-bit digits, `passes` of them), ping-ponging between a and b, then an
+// order-preserving compaction of the first of every run into out (== a).
+__global__ void __launch_bounds__(kSortThreads) k_ct_large(const int64_t *off, const int32_t *pins, int32_t m,
+                                                           const int32_t *map, int32_t *a, int32_t *b,
+                                                           int32_t *size1, int passes)
+{
+    __shared__ int32_t base[256];
+    __shared__ int32_t tile_cnt[256];
+    __shared__ int32_t wcnt[kSortThreads / 32][256];
+    __shared__ int32_t wtot[kSortThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int kW = kSortThreads / 32;
+    for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+        const int64_t beg = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - beg);
+        if (s <= kSmallNet) continue;
+        for (int32_t j = tid; j < s; j += kSortThreads) a[beg + j] = map[pins[beg + j]];
+        __syncthreads();
+        int32_t *src = a + beg, *dst = b + beg;
+        for (int p = 0; p < passes; ++p) {
+            const int sh = 8 * p;
+            // digit histogram -> exclusive bases
+            base[tid] = 0;
+            __syncthreads();
+            for (int32_t j = tid; j < s; j += kSortThreads) atomicAdd(&base[(src[j] >> sh) & 255], 1);
+            __syncthreads();
+            if (tid == 0) {
+                int32_t run = 0;
+                for (int d = 0; d < 256; ++d) { const int32_t c = base[d]; base[d] = run; run += c; }
+            }
+            __syncthreads();
+            // stable scatter, one tile of kSortThreads elements at a time
+            for (int32_t t0 = 0; t0 < s; t0 += kSortThreads) {
+                const int32_t j = t0 + tid;
+                const bool has = j < s;
+                const int32_t v = has ? src[j] : 0;
+                const int d = (v >> sh) & 255;
+                for (int w = 0; w < kW; ++w) wcnt[w][tid] = 0;
+                __syncthreads();
+                const unsigned act = __ballot_sync(kFull, has);
+                int rank = 0;
+                if (has) {
+                    const unsigned peers = __match_any_sync(act, d);
+                    rank = __popc(peers & ((1u << lane) - 1));
+                    if (rank == 0) wcnt[wid][d] = __popc(peers);
+                }
+                __syncthreads();
+                {   // per digit (thread tid = digit): exclusive prefix over the warps
+                    int32_t run = 0;
+                    for (int w = 0; w < kW; ++w) { const int32_t c = wcnt[w][tid]; wcnt[w][tid] = run; run += c; }
+                    tile_cnt[tid] = run;
+                }
+                __syncthreads();
+                if (has) dst[base[d] + wcnt[wid][d] + rank] = v;
+                __syncthreads();
+                base[tid] += tile_cnt[tid];
+                __syncthreads();
+            }
+            int32_t *t = src; src = dst; dst = t;
+        }
+        // compaction: keep the first of every run of equal values, in order, into a
+        int32_t kept = 0;
+        for (int32_t t0 = 0; t0 < s; t0 += kSortThreads) {
+            const int32_t j = t0 + tid;
+            const bool has = j < s;
+            const int32_t v = has ? src[j] : 0;
+            const bool keep = has && (j == 0 || v != src[j - 1]);
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (lane == 0) wtot[wid] = __popc(km);
+            __syncthreads();
+            int32_t before = kept;
+            for (int w = 0; w < wid; ++w) before += wtot[w];
+            int32_t tile_total = 0;
+            for (int w = 0; w < kW; ++w) tile_total += wtot[w];
+            __syncthreads();   // every thread has read its input and the counts
+            if (keep) a[beg + before + __popc(km & ((1u << lane) - 1))] = v;
+            kept += tile_total;
+            __syncthreads();
+        }
+        if (tid == 0) size1[e] = kept;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- identical nets
+__device__ __forceinline__ unsigned long long net_key(const int32_t *p, int32_t s, int lane)
+{
+    unsigned long long h = 0;
+    for (int32_t j = lane; j < s; j += 32) h += splitmix64_output(0x6a09e667f3bcc908ull ^ (uint64_t)(uint32_t)p[j]);
+    for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+    unsigned long long k = splitmix64_output(h ^ ((uint64_t)(uint32_t)s << 32));
+    return k == kKeyEmpty ? k - 1 : k;
+}
+
+// warp per net: fingerprint of the sorted pin list, rep = dropped (< 2 pins) or unresolved
+__global__ void k_ct_key(const int64_t *off, const int32_t *a, const int32_t *size1, int32_t m,
+                         unsigned long long *key, int32_t *rep)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        const int32_t s = size1[e];
+        if (s < 2) {
+            if (lane == 0) rep[e] = kDropped;
+            continue;
+        }
+        const unsigned long long k = net_key(a + off[e], s, lane);
+        if (lane == 0) { key[e] = k; rep[e] = kUnresolved; }
+    }
+}
+
+struct KeySlot {
+    unsigned long long key;
+    int32_t min_id;
+    int32_t pad;
+};
+
+__global__ void k_ct_table_clear(KeySlot *tab, int64_t size)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < size; i += (int64_t)gridDim.x * blockDim.x) {
+        tab[i].key = kKeyEmpty;
+        tab[i].min_id = 0x7fffffff;
+    }
+}
+
+__device__ __forceinline__ KeySlot *key_find(KeySlot *tab, uint64_t mask, unsigned long long key, bool insert)
+{
+    uint64_t p = splitmix64_output(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        KeySlot *sl = tab + p;
+        unsigned long long cur = __ldcg(&sl->key);
+        if (cur == key) return sl;
+        if (cur == kKeyEmpty) {
+            if (!insert) return nullptr;
+            cur = atomicCAS(&sl->key, kKeyEmpty, key);
+            if (cur == kKeyEmpty || cur == key) return sl;
+        }
+        p = (p + 1) & mask;
+    }
+    return nullptr;
+}
+
+// thread per unresolved net: its fingerprint's smallest unresolved net id
+__global__ void k_ct_insert(const unsigned long long *key, const int32_t *rep, int32_t m, KeySlot *tab,
+                            uint64_t mask, int32_t *err)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        if (rep[e] != kUnresolved) continue;
+        KeySlot *sl = key_find(tab, mask, key[e], true);
+        if (!sl) { atomicOr(err, ERR_INVALID); continue; }
+        atomicMin(&sl->min_id, (int32_t)e);
+    }
+}
+
+// warp per unresolved net: resolved to the smallest net of its fingerprint if the pin lists are
+// equal (itself included); otherwise it stays unresolved for the next round
+__global__ void k_ct_resolve(const int64_t *off, const int32_t *a, const int32_t *size1,
+                             const unsigned long long *key, int32_t *rep, int32_t m, const KeySlot *tab,
+                             uint64_t mask, int32_t *left)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        if (rep[e] != kUnresolved) continue;
+        const KeySlot *sl = key_find(const_cast<KeySlot *>(tab), mask, key[e], false);
+        const int32_t r = sl ? sl->min_id : (int32_t)e;
+        bool same = r == (int32_t)e;
+        if (!same && size1[r] == size1[e]) {
+            const int32_t *pe = a + off[e], *pr = a + off[r];
+            bool eq = true;
+            for (int32_t j = lane; j < size1[e]; j += 32) eq = eq && pe[j] == pr[j];
+            same = __all_sync(kFull, eq);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (same) rep[e] = r;
+            else atomicAdd(left, 1);
+        }
+    }
+}
+
+// thread per net: representative flags and sizes for the prefix sums, group weights
+__global__ void k_ct_groups(const int32_t *rep, const int32_t *size1, const int32_t *nw, int32_t m,
+                            int32_t *is_rep, int32_t *rep_size, unsigned long long *w64)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = rep[e];
+        const bool self = r == (int32_t)e;
+        is_rep[e] = self;
+        rep_size[e] = self ? size1[e] : 0;
+        if (r >= 0) atomicAdd(&w64[r], (unsigned long long)(nw ? nw[e] : 1));
+    }
+}
+
+// warp per representative: its pins and weight at its coarse position
+__global__ void k_ct_emit(const int64_t *off, const int32_t *a, const int32_t *size1, const int32_t *rep,
+                          const int64_t *nid, const int64_t *poff, const unsigned long long *w64, int32_t m,
+                          int32_t *pins2, int64_t *off2, int32_t *nw2, int32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        if (rep[e] != (int32_t)e) continue;
+        const int64_t i = nid[e], dst = poff[e];
+        const int32_t s = size1[e];
+        for (int32_t j = lane; j < s; j += 32) pins2[dst + j] = a[off[e] + j];
+        if (lane == 0) {
+            off2[i] = dst;
+            const unsigned long long w = w64[e];
+            if (w >= (1ull << 31)) atomicOr(err, ERR_UNSUPPORTED);
+            nw2[i] = (int32_t)w;
+        }
+    }
+}
+
+__global__ void k_ct_project(const int32_t *map, int32_t n, const int32_t *coarse_part, int32_t *fine_part)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        fine_part[u] = coarse_part[map[u]];
+}
+
+void coarse_free(hgp_coarse *c)
+{
+    if (!c) return;
+    if (c->net_off) cudaFree(c->net_off);
+    if (c->pins) cudaFree(c->pins);
+    if (c->vw) cudaFree(c->vw);
+    if (c->nw) cudaFree(c->nw);
+    if (c->map) cudaFree(c->map);
+    delete c;
+}
+
+}  // namespace
+
+#define CT(x)                                   \
+    do {                                        \
+        e = (x);                                \
+        if (e != cudaSuccess) goto done;        \
+    } while (0)
+
+extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const int32_t *pins,
+                            const int32_t *vertex_w, const int32_t *net_w, const int32_t *cluster,
+                            void *cuda_stream, hgp_coarse **out)
+{
+    if (!out) return HGP_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || m < 0 || !net_off || !cluster || (m > 0 && !pins)) return HGP_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    hgp_coarse *c = new (std::nothrow) hgp_coarse;
+    if (!c) return HGP_ERR_OOM;
+    c->fine_n = n;
+    c->stream = st;
+    cudaGetDevice(&c->device);
+    cudaError_t e = cudaSuccess;
+    int rc = HGP_OK;
+    int32_t *err = nullptr, *used = nullptr, *a = nullptr, *b = nullptr, *size1 = nullptr, *rep = nullptr;
+    int32_t *is_rep = nullptr, *rep_size = nullptr, *left = nullptr;
+    int64_t *cid = nullptr, *nid = nullptr, *poff = nullptr;
+    unsigned long long *w64 = nullptr, *key = nullptr, *nw64 = nullptr;
+    KeySlot *tab = nullptr;
+    int64_t P = 0, n2 = 0, m2 = 0, P2 = 0;
+    int32_t herr = 0;
+    const int64_t mm = m > 0 ? m : 1;
+    CT(cudaMemcpyAsync(&P, net_off + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    if (P < 0 || (m == 0 && P != 0)) { rc = HGP_ERR_INVALID; goto done; }
+    if (P >= ((int64_t)1 << 31)) { rc = HGP_ERR_UNSUPPORTED; goto done; }
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int32_t) * 2, st));
+    CT(cudaMemsetAsync(err, 0, sizeof(int32_t) * 2, st));
+    left = err + 1;
+    k_ct_check<<<grid_of(P > n ? P : n, 256), 256, 0, st>>>(net_off, pins, vertex_w, net_w, n, m, P, err);
+    CT(cudaGetLastError());
+    CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    if (herr) { rc = HGP_ERR_INVALID; goto done; }
+    // (1) remap the used cluster ids
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&used), sizeof(int32_t) * (size_t)n, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&cid), sizeof(int64_t) * ((size_t)n + 1), st));
+    CT(cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)n, st));
+    k_ct_flag<<<grid_of(n, 256), 256, 0, st>>>(cluster, n, used, err);
+    CT(cudaGetLastError());
+    CT(scan_excl<int32_t>(used, n, cid, st));
+    CT(cudaMemcpyAsync(&n2, cid + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    if (herr) { rc = HGP_ERR_INVALID; goto done; }
+    c->n = (int32_t)n2;
+    // (2) map and cluster weights
+    CT(cudaMalloc(reinterpret_cast<void **>(&c->map), sizeof(int32_t) * (size_t)n));
+    CT(cudaMalloc(reinterpret_cast<void **>(&c->vw), sizeof(int32_t) * (size_t)n2));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&w64), sizeof(unsigned long long) * (size_t)(n > mm ? n : mm), st));
+    CT(cudaMemsetAsync(w64, 0, sizeof(unsigned long long) * (size_t)n2, st));
+    k_ct_map<<<grid_of(n, 256), 256, 0, st>>>(cluster, n, cid, vertex_w, c->map, w64);
+    k_ct_narrow<<<grid_of(n2, 256), 256, 0, st>>>(w64, n2, c->vw, err);
+    CT(cudaGetLastError());
+    // (3) per-net sort + dedupe
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&a), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&b), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&size1), sizeof(int32_t) * (size_t)mm, st));
+    if (m > 0) {
+        int passes = 1;
+        while (passes < 4 && ((n2 - 1) >> (8 * passes)) > 0) ++passes;
+        k_ct_small<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins, m, c->map, a, size1);
+        k_ct_large<<<grid_of(m, 1) < 4096 ? grid_of(m, 1) : 4096, kSortThreads, 0, st>>>(net_off, pins, m, c->map, a, b, size1, passes);
+        CT(cudaGetLastError());
+    }
+    // (4) identical nets
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&key), sizeof(unsigned long long) * (size_t)mm, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&rep), sizeof(int32_t) * (size_t)mm, st));
+    if (m > 0) {
+        uint64_t size = 1024;
+        while (size < 2 * (uint64_t)m) size <<= 1;
+        CT(cudaMallocAsync(reinterpret_cast<void **>(&tab), sizeof(KeySlot) * size, st));
+        k_ct_key<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, m, key, rep);
+        CT(cudaGetLastError());
+        for (int round = 0;; ++round) {
+            if (round >= 4096) { rc = HGP_ERR_INTERNAL; goto done; }
+            int32_t hleft = 0;
+            CT(cudaMemsetAsync(left, 0, sizeof(int32_t), st));
+            k_ct_table_clear<<<grid_of((int64_t)size, 256), 256, 0, st>>>(tab, (int64_t)size);
+            k_ct_insert<<<grid_of(m, 256), 256, 0, st>>>(key, rep, m, tab, size - 1, err);
+            k_ct_resolve<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, key, rep, m, tab, size - 1, left);
+            CT(cudaGetLastError());
+            CT(cudaMemcpyAsync(&hleft, left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CT(cudaStreamSynchronize(st));
+            if (hleft == 0) break;
+        }
+    }
+    // (5) representatives in original order, their weights and offsets
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&is_rep), sizeof(int32_t) * (size_t)mm, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&rep_size), sizeof(int32_t) * (size_t)mm, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&nid), sizeof(int64_t) * ((size_t)m + 1), st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&poff), sizeof(int64_t) * ((size_t)m + 1), st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&nw64), sizeof(unsigned long long) * (size_t)mm, st));
+    CT(cudaMemsetAsync(nw64, 0, sizeof(unsigned long long) * (size_t)mm, st));
+    if (m > 0) {
+        k_ct_groups<<<grid_of(m, 256), 256, 0, st>>>(rep, size1, net_w, m, is_rep, rep_size, nw64);
+        CT(cudaGetLastError());
+    }
+    CT(scan_excl<int32_t>(is_rep, m, nid, st));
+    CT(scan_excl<int32_t>(rep_size, m, poff, st));
+    CT(cudaMemcpyAsync(&m2, nid + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaMemcpyAsync(&P2, poff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    c->m = (int32_t)m2;
+    c->P = P2;
+    CT(cudaMalloc(reinterpret_cast<void **>(&c->net_off), sizeof(int64_t) * ((size_t)m2 + 1)));
+    CT(cudaMalloc(reinterpret_cast<void **>(&c->pins), sizeof(int32_t) * (size_t)(P2 > 0 ? P2 : 1)));
+    CT(cudaMalloc(reinterpret_cast<void **>(&c->nw), sizeof(int32_t) * (size_t)(m2 > 0 ? m2 : 1)));
+    CT(cudaMemcpyAsync(c->net_off + m2, &P2, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (m > 0) {
+        k_ct_emit<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64, m,
+                                                                 c->pins, c->net_off, c->nw, err);
+        CT(cudaGetLastError());
+    }
+    CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CT(cudaStreamSynchronize(st));
+    if (herr & ERR_UNSUPPORTED) rc = HGP_ERR_UNSUPPORTED;
+    else if (herr) rc = HGP_ERR_INTERNAL;
+done:
+    if (err) cudaFreeAsync(err, st);
+    if (used) cudaFreeAsync(used, st);
+    if (cid) cudaFreeAsync(cid, st);
+    if (w64) cudaFreeAsync(w64, st);
+    if (a) cudaFreeAsync(a, st);
+    if (b) cudaFreeAsync(b, st);
+    if (size1) cudaFreeAsync(size1, st);
+    if (key) cudaFreeAsync(key, st);
+    if (rep) cudaFreeAsync(rep, st);
+    if (tab) cudaFreeAsync(tab, st);
+    if (is_rep) cudaFreeAsync(is_rep, st);
+    if (rep_size) cudaFreeAsync(rep_size, st);
+    if (nid) cudaFreeAsync(nid, st);
+    if (poff) cudaFreeAsync(poff, st);
+    if (nw64) cudaFreeAsync(nw64, st);
+    {
+        const cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = status_of(e);
+    }
+    if (rc != HGP_OK) {
+        coarse_free(c);
+        return rc;
+    }
+    *out = c;
+    return HGP_OK;
+}
+
+extern "C" int hgp_coarse_get_sizes(const hgp_coarse *c, int32_t *n, int32_t *m, int64_t *num_pins)
+{
+    if (!c || !n || !m || !num_pins) return HGP_ERR_INVALID;
+    *n = c->n;
+    *m = c->m;
+    *num_pins = c->P;
+    return HGP_OK;
+}
+
+extern "C" int hgp_coarse_get_device_arrays(const hgp_coarse *c, const int64_t **net_off, const int32_t **pins,
+                                            const int32_t **vertex_w, const int32_t **net_w, const int32_t **map)
+{
+    if (!c) return HGP_ERR_INVALID;
+    if (net_off) *net_off = c->net_off;
+    if (pins) *pins = c->pins;
+    if (vertex_w) *vertex_w = c->vw;
+    if (net_w) *net_w = c->nw;
+    if (map) *map = c->map;
+    return HGP_OK;
+}
+
+extern "C" int hgp_coarse_copy_to_host(const hgp_coarse *c, int64_t *net_off, int32_t *pins, int32_t *vertex_w,
+                                       int32_t *net_w, int32_t *map)
+{
+    if (!c) return HGP_ERR_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (net_off) e = cudaMemcpyAsync(net_off, c->net_off, sizeof(int64_t) * ((size_t)c->m + 1), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && pins && c->P > 0)
+        e = cudaMemcpyAsync(pins, c->pins, sizeof(int32_t) * (size_t)c->P, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && vertex_w)
+        e = cudaMemcpyAsync(vertex_w, c->vw, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && net_w && c->m > 0)
+        e = cudaMemcpyAsync(net_w, c->nw, sizeof(int32_t) * (size_t)c->m, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && map)
+        e = cudaMemcpyAsync(map, c->map, sizeof(int32_t) * (size_t)c->fine_n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return HGP_OK;
+}
+
+extern "C" int hgp_coarse_project(const hgp_coarse *c, const int32_t *coarse_part, int32_t *fine_part)
+{
+    if (!c || !coarse_part || !fine_part) return HGP_ERR_INVALID;
+    k_ct_project<<<grid_of(c->fine_n, 256), 256, 0, c->stream>>>(c->map, c->fine_n, coarse_part, fine_part);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return HGP_OK;
+}
+
+extern "C" void hgp_coarse_destroy(hgp_coarse *c)
+{
+    if (c) cudaStreamSynchronize(c->stream);
+    coarse_free(c);
+}

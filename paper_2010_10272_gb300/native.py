@@ -88,6 +88,13 @@ def load_library():
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
         lib.hgp_exact_gains.argtypes = [P, i32, P, P]
         lib.hgp_rebalance.argtypes = [P, i32, P, P, P]
+        lib.hgp_contract.argtypes = [i32, i32, P, P, P, P, P, P, P]
+        lib.hgp_coarse_get_sizes.argtypes = [P, P, P, P]
+        lib.hgp_coarse_get_device_arrays.argtypes = [P, P, P, P, P, P]
+        lib.hgp_coarse_copy_to_host.argtypes = [P, P, P, P, P, P]
+        lib.hgp_coarse_project.argtypes = [P, P, P]
+        lib.hgp_coarse_destroy.argtypes = [P]
+        lib.hgp_coarse_destroy.restype = None
         lib.hgp_exact_gains.restype = ctypes.c_int
         lib.hgp_export_state.argtypes = [P, P, P, P, P]
         lib.hgp_import_state.argtypes = [P, P, P, i64, i32]
@@ -150,7 +157,11 @@ def _hptr(a):
 
 
 def _dptr(t):
-    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+    if t is None:
+        return None
+    if isinstance(t, int):          # a raw device pointer (e.g. one owned by a Coarse)
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(int(t.data_ptr()))
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -406,3 +417,61 @@ def probe_gather(array_bytes: int = 1600 << 20, n_gathers: int = 86_000_000):
     _check(lib.hgp_probe_gather(int(array_bytes), int(n_gathers), ctypes.byref(ms), ctypes.byref(rate)),
            "hgp_probe_gather")
     return ms.value, rate.value
+
+
+class Coarse:
+    """hgp_contract over device arrays (torch CUDA tensors): the coarse hypergraph of a
+    clustering (Sec. 3.2), owned on the device until close()."""
+
+    def __init__(self, n, m, net_off, pins, vertex_w, net_w, cluster, stream=None):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        self.fine_n = int(n)
+        sh = _stream_handle(stream)
+        _check(self._lib.hgp_contract(int(n), int(m), _dptr(net_off), _dptr(pins), _dptr(vertex_w),
+                                      _dptr(net_w), _dptr(cluster), ctypes.c_void_p(sh) if sh else None,
+                                      ctypes.byref(self._h)), "hgp_contract")
+        n2, m2, p2 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self._lib.hgp_coarse_get_sizes(self._h, ctypes.byref(n2), ctypes.byref(m2), ctypes.byref(p2)),
+               "hgp_coarse_get_sizes")
+        self.n, self.m, self.num_pins = n2.value, m2.value, p2.value
+
+    def device_arrays(self) -> dict:
+        """Raw device pointers (ints) owned by this object."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(self._lib.hgp_coarse_get_device_arrays(self._h, *[ctypes.byref(p) for p in ptrs]),
+               "hgp_coarse_get_device_arrays")
+        return dict(zip(("net_off", "pins", "vertex_w", "net_w", "map"), (p.value or 0 for p in ptrs)))
+
+    def to_host(self) -> dict:
+        out = {"n": self.n, "m": self.m, "net_off": np.empty(self.m + 1, np.int64),
+               "pins": np.empty(max(1, self.num_pins), np.int32), "vertex_w": np.empty(max(1, self.n), np.int32),
+               "net_w": np.empty(max(1, self.m), np.int32), "map": np.empty(self.fine_n, np.int32)}
+        _check(self._lib.hgp_coarse_copy_to_host(self._h, _hptr(out["net_off"]), _hptr(out["pins"]),
+                                                 _hptr(out["vertex_w"]), _hptr(out["net_w"]), _hptr(out["map"])),
+               "hgp_coarse_copy_to_host")
+        out["pins"] = out["pins"][:self.num_pins]
+        out["vertex_w"] = out["vertex_w"][:self.n]
+        out["net_w"] = out["net_w"][:self.m]
+        return out
+
+    def handle(self, k, eps, part, **kw) -> "HGP":
+        """An HGP over the coarse arrays (no copy through the host); part: device int32[n']."""
+        a = self.device_arrays()
+        return HGP(self.n, self.m, a["net_off"], a["pins"], k, eps, part, a["vertex_w"], a["net_w"],
+                   device=True, **kw)
+
+    def project(self, coarse_part, fine_part):
+        """fine_part[u] = coarse_part[map[u]] (device int32 tensors)."""
+        _check(self._lib.hgp_coarse_project(self._h, _dptr(coarse_part), _dptr(fine_part)), "hgp_coarse_project")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.hgp_coarse_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
