@@ -255,7 +255,7 @@ def oracle_sample(workload: str, steps: int, warmup: int, rounds_override=None, 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    if args.workload in ("batch", "serving", "rebalance"):
+    if args.workload in ("batch", "serving", "rebalance", "contract"):
         args.workload = "small"
     value, per_step, sample, hg = oracle_sample(args.workload, args.steps, args.warmup,
                                                 variant=args.variant)
@@ -618,6 +618,124 @@ def run_rebalance(args, world, rank, local):
     return 0
 
 
+# ------------------------------------------------------------------------------ contraction
+def pair_clustering(n: int, seed: int) -> np.ndarray:
+    """Seeded clustering into about n/2 clusters: a permutation cut into consecutive pairs (a
+    stand-in for the paper's clustering, which is out of scope)."""
+    perm = np.random.default_rng(seed).permutation(n)
+    cl = np.empty(n, np.int32)
+    cl[perm] = perm[(np.arange(n) // 2) * 2]
+    return cl
+
+
+def run_contract(args, world, rank, local):
+    """Contraction (Sec. 3.2) of the power-law instance by a seeded pair clustering, then of the
+    result again, down to four levels; a step contracts H0 -> H1 (timed, inputs in HBM).
+    value = fine pins contracted per second.  Also: the whole hierarchy refined in one batch
+    against the levels refined one after another."""
+    import torch
+    from paper_2010_10272_gb300 import HGP, Batch, Coarse, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    t_gen = time.perf_counter()
+    hg = load_instance("powerlaw", args.scale)
+    t_gen = time.perf_counter() - t_gen
+    P = hg.num_pins
+    to_dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = [to_dev(x) for x in (hg.net_off, hg.pins, hg.vertex_w, hg.net_w)]
+    cl = to_dev(pair_clustering(hg.n, 1))
+    for _ in range(args.warmup):
+        Coarse(hg.n, hg.m, *d, cl, stream=stream).close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        c = Coarse(hg.n, hg.m, *d, cl, stream=stream)      # synchronises its stream
+        ms.append((time.perf_counter() - t0) * 1e3)
+        c.close()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(ms), world)
+    value = world * args.steps * P / (total_ms / 1e3)
+    # bytes a contraction has to move at least: read offsets, pins, cluster ids of the pins and
+    # weights; write the remapped pins once, read them for the fingerprints, write the coarse pins
+    c1 = Coarse(hg.n, hg.m, *d, cl, stream=stream)
+    algo = 8 * (hg.m + 1) + 4 * P * 5 + 4 * hg.n * 3 + 4 * c1.num_pins * 2
+    peak, peak_kind = measured_peak_hbm()
+    achieved = algo / (total_ms / args.steps / 1e3) / 1e9
+    # hierarchy: H0..H3 by repeated pair contraction, refined together in one batch
+    levels = [(hg.n, hg.m, d[0], d[1], d[2], d[3])]
+    coarse = [c1]
+    for lv in range(1, 4):
+        a = coarse[-1].device_arrays()
+        cur = coarse[-1]
+        levels.append((cur.n, cur.m, a["net_off"], a["pins"], a["vertex_w"], a["net_w"]))
+        if lv < 3:
+            coarse.append(Coarse(cur.n, cur.m, a["net_off"], a["pins"], a["vertex_w"], a["net_w"],
+                                 to_dev(pair_clustering(cur.n, 1 + lv)), stream=stream))
+    parts = [to_dev((np.arange(L[0]) % hg.k).astype(np.int32)) for L in levels]
+    hs = [HGP(L[0], L[1], L[2], L[3], hg.k, hg.eps, parts[i], L[4], L[5], subrounds=4, device=True,
+              stream=stream) for i, L in enumerate(levels)]
+    R = hg.rounds
+
+    def reset():
+        for h, p in zip(hs, parts):
+            h.set_partition(p, device=True)
+        torch.cuda.synchronize()
+    batch = Batch(hs, graph=True, stream=stream)
+    hier = {}
+    for name, fn in (("batched", lambda: batch.refine(R, stats=False)),
+                     ("one_after_another", lambda: [h.refine(R, stats=False) for h in hs])):
+        reset()
+        fn()
+        torch.cuda.synchronize()
+        reset()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        hier[name + "_ms"] = ev[0].elapsed_time(ev[1])
+    hier["levels"] = [{"n": L[0], "m": L[1]} for L in levels]
+    hier["rounds"] = R
+    batch.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        scale = SAMPLE_SCALE["powerlaw"]
+        hs_ = load_instance("powerlaw", scale)
+        t0 = time.perf_counter()
+        oracle.contract(hs_.n, hs_.m, hs_.net_off, hs_.pins, hs_.vertex_w, hs_.net_w, pair_clustering(hs_.n, 1))
+        dt = time.perf_counter() - t0
+        cpu = {"value": hs_.num_pins / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{hs_.name}, pair clustering (scale {scale:g}): {dt:.2f} s"}
+    line = {
+        "metric": "contraction pins/s", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["powerlaw"][1] + ", seeded pair clustering",
+                   "n": hg.n, "m": hg.m, "pins": P, "coarse": {"n": c1.n, "m": c1.m, "pins": c1.num_pins},
+                   "parallelism": f"replicas x{world}", "step": "hgp_contract H0 -> H1 (inputs in HBM, "
+                   "wall clock around the call, which synchronises)", "l2": "inputs larger than L2"},
+        "roofline": {"bound": "hbm", "kernel": "hgp_contract (whole call)", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": None, "algorithmic_bytes_per_launch": algo},
+        "hierarchy_batch": hier, "cpu_baseline": cpu, "clocks": clocks,
+        "setup_s": {"generate_or_load": t_gen},
+    }
+    for c in coarse:
+        c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------------ serving workload
 def run_serving(args, world, rank, local):
     """Poisson arrivals of refinement requests (planted, pins log-uniform 1e4-5e6, k in
@@ -699,7 +817,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving", "rebalance"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serving", "rebalance", "contract"],
                     default="powerlaw")
     ap.add_argument("--skew", type=float, default=0.2,
                     help="rebalance workload: fraction of the vertices moved into block 0")
@@ -727,6 +845,8 @@ def main():
         rc = run_serving(args, world, rank, local)
     elif args.workload == "rebalance":
         rc = run_rebalance(args, world, rank, local)
+    elif args.workload == "contract":
+        rc = run_contract(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

@@ -2,9 +2,11 @@
 //
 //   1. used cluster ids flagged and remapped to 0..n'-1 by an exclusive prefix sum;
 //   2. coarse vertex weights by atomic adds (checked to fit int32);
-//   3. every net's pins mapped to coarse ids, sorted and de-duplicated: a warp per net with at
-//      most 32 pins (bitonic sort in registers), a CTA per larger net (stable LSD radix sort of
-//      its segment in global memory, 8-bit digits, then an order-preserving compaction);
+//   3. every net's pins mapped to coarse ids, sorted and de-duplicated by size class: a thread
+//      per net of at most 8 pins (sorting network in registers), a warp per net of 9..32 (bitonic
+//      across the lanes), a CTA per net of 33..2048 (bitonic in shared memory), and for larger
+//      nets 2048-pin chunks sorted by separate CTAs and merged pairwise by merge-path tiles
+//      spread over the whole grid; the net's fingerprint is taken during the de-duplication;
 //   4. nets with fewer than two pins dropped; identical nets found through a 64-bit
 //      fingerprint table (key -> smallest net id) and an exact comparison with that net; a
 //      net that only shares the fingerprint stays unresolved and takes part in the next round
@@ -39,7 +41,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kScanTile = 1024;
 constexpr int kSortThreads = 256;
-constexpr int kSmallNet = 32;
 constexpr unsigned long long kKeyEmpty = ~0ull;
 constexpr int32_t kUnresolved = -2, kDropped = -1;
 
@@ -160,17 +161,99 @@ __global__ void k_ct_narrow(const unsigned long long *w64, int64_t len, int32_t 
 }
 
 // ---------------------------------------------------------------- per-net sort + dedupe
-// warp per net with at most 32 pins: bitonic sort of the mapped pins across the lanes, then the
-// first of every run of equal values is kept, in order, at the start of the net's segment
-__global__ void k_ct_small(const int64_t *off, const int32_t *pins, int32_t m, const int32_t *map,
-                           int32_t *out, int32_t *size1)
+// Fingerprint of a sorted, de-duplicated pin list: the sum of a 64-bit mix of every pin
+// (independent of how the pins are split over threads), mixed with the list's length.
+__device__ __forceinline__ unsigned long long pin_mix(int32_t v)
+{
+    return splitmix64_output(0x6a09e667f3bcc908ull ^ (uint64_t)(uint32_t)v);
+}
+
+__device__ __forceinline__ unsigned long long key_final(unsigned long long h, int32_t s)
+{
+    const unsigned long long k = splitmix64_output(h ^ ((uint64_t)(uint32_t)s << 32));
+    return k == kKeyEmpty ? k - 1 : k;
+}
+
+// result of one net: its de-duplicated size, and its fingerprint (or dropped, < 2 pins)
+__device__ __forceinline__ void net_done(int64_t e, int32_t kept, unsigned long long h, int32_t *size1,
+                                         unsigned long long *key, int32_t *rep)
+{
+    size1[e] = kept;
+    if (kept < 2) {
+        rep[e] = kDropped;
+    } else {
+        key[e] = key_final(h, kept);
+        rep[e] = kUnresolved;
+    }
+}
+
+constexpr int kTiny = 8, kMedium = 2048;
+
+// thread per net: nets of at most kTiny pins are sorted in registers (an unrolled sorting
+// network), de-duplicated and fingerprinted; larger nets go to the lists of the warp (9..32
+// pins), CTA shared-memory (..kMedium) and CTA radix (larger) kernels
+__global__ void k_ct_tiny(const int64_t *off, const int32_t *pins, int32_t m, const int32_t *map, int32_t *a,
+                          int32_t *size1, unsigned long long *key, int32_t *rep, int32_t *lists, int32_t *counts)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < m; e0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        int cls = -1;
+        if (e < m) {
+            const int64_t b = off[e];
+            const int32_t s = (int32_t)(off[e + 1] - b);
+            if (s <= kTiny) {
+                int32_t v[kTiny];
+#pragma unroll
+                for (int i = 0; i < kTiny; ++i) v[i] = i < s ? map[pins[b + i]] : 0x7fffffff;
+#pragma unroll
+                for (int i = 1; i < kTiny; ++i) {
+#pragma unroll
+                    for (int j = i; j > 0; --j) {
+                        const int32_t lo = min(v[j - 1], v[j]), hi = max(v[j - 1], v[j]);
+                        v[j - 1] = lo;
+                        v[j] = hi;
+                    }
+                }
+                int32_t kept = 0;
+                unsigned long long h = 0;
+#pragma unroll
+                for (int i = 0; i < kTiny; ++i) {
+                    if (i < s && (i == 0 || v[i] != v[i - 1])) {
+                        a[b + kept] = v[i];
+                        h += pin_mix(v[i]);
+                        ++kept;
+                    }
+                }
+                net_done(e, kept, h, size1, key, rep);
+            } else {
+                cls = s <= 32 ? 0 : (s <= kMedium ? 1 : 2);
+            }
+        }
+        // warp-aggregated append of the larger nets to their class lists
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const unsigned mk = __ballot_sync(kFull, cls == c);
+            if (!mk) continue;
+            int32_t base = 0;
+            if (lane == __ffs(mk) - 1) base = atomicAdd(&counts[c], __popc(mk));
+            base = __shfl_sync(kFull, base, __ffs(mk) - 1);
+            if (cls == c) lists[(int64_t)c * m + base + __popc(mk & ((1u << lane) - 1))] = (int32_t)e;
+        }
+    }
+}
+
+// warp per listed net of 9..32 pins: bitonic sort across the lanes, de-duplication, fingerprint
+__global__ void k_ct_small(const int64_t *off, const int32_t *pins, const int32_t *map, const int32_t *list,
+                           const int32_t *count, int32_t *a, int32_t *size1, unsigned long long *key, int32_t *rep)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+    const int32_t cnt = *count;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += warps) {
+        const int64_t e = list[i];
         const int64_t b = off[e];
         const int32_t s = (int32_t)(off[e + 1] - b);
-        if (s > kSmallNet) continue;
         int32_t v = lane < s ? map[pins[b + lane]] : 0x7fffffff;
 #pragma unroll
         for (int k = 2; k <= 32; k <<= 1) {
@@ -185,123 +268,240 @@ __global__ void k_ct_small(const int64_t *off, const int32_t *pins, int32_t m, c
         const int32_t prev = __shfl_up_sync(kFull, v, 1);
         const bool keep = lane < s && (lane == 0 || v != prev);
         const unsigned km = __ballot_sync(kFull, keep);
-        if (keep) out[b + __popc(km & ((1u << lane) - 1))] = v;
-        if (lane == 0) size1[e] = __popc(km);
+        if (keep) a[b + __popc(km & ((1u << lane) - 1))] = v;
+        unsigned long long h = keep ? pin_mix(v) : 0ull;
+        for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        if (lane == 0) net_done(e, __popc(km), h, size1, key, rep);
     }
 }
 
-// CTA per net with more than 32 pins: stable LSD radix sort of the mapped pins of the net's
-// segment (8-bit digits, `passes` of them), ping-ponging between a and b, then an
-// order-preserving compaction of the first of every run into out (== a).
-__global__ void __launch_bounds__(kSortThreads) k_ct_large(const int64_t *off, const int32_t *pins, int32_t m,
-                                                           const int32_t *map, int32_t *a, int32_t *b,
-                                                           int32_t *size1, int passes)
+// block-wide: order-preserving compaction of the first of every run of equal values of the
+// sorted src[0..s) into dst (dst may equal src), fingerprint of the kept values
+__device__ __forceinline__ void compact_runs(const int32_t *src, int32_t *dst, int32_t s, int32_t *wtot,
+                                             unsigned long long *hsum, int32_t &kept_out, unsigned long long &h_out)
 {
-    __shared__ int32_t base[256];
-    __shared__ int32_t tile_cnt[256];
-    __shared__ int32_t wcnt[kSortThreads / 32][256];
-    __shared__ int32_t wtot[kSortThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int kW = kSortThreads / 32;
-    for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
-        const int64_t beg = off[e];
-        const int32_t s = (int32_t)(off[e + 1] - beg);
-        if (s <= kSmallNet) continue;
-        for (int32_t j = tid; j < s; j += kSortThreads) a[beg + j] = map[pins[beg + j]];
+    const int nw = blockDim.x >> 5;
+    int32_t kept = 0;
+    if (tid == 0) *hsum = 0;
+    for (int32_t t0 = 0; t0 < s; t0 += blockDim.x) {
+        const int32_t j = t0 + tid;
+        const bool has = j < s;
+        const int32_t v = has ? src[j] : 0;
+        const bool keep = has && (j == 0 || v != src[j - 1]);
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (lane == 0) wtot[wid] = __popc(km);
         __syncthreads();
-        int32_t *src = a + beg, *dst = b + beg;
-        for (int p = 0; p < passes; ++p) {
-            const int sh = 8 * p;
-            // digit histogram -> exclusive bases
-            base[tid] = 0;
-            __syncthreads();
-            for (int32_t j = tid; j < s; j += kSortThreads) atomicAdd(&base[(src[j] >> sh) & 255], 1);
-            __syncthreads();
-            if (tid == 0) {
-                int32_t run = 0;
-                for (int d = 0; d < 256; ++d) { const int32_t c = base[d]; base[d] = run; run += c; }
-            }
-            __syncthreads();
-            // stable scatter, one tile of kSortThreads elements at a time
-            for (int32_t t0 = 0; t0 < s; t0 += kSortThreads) {
-                const int32_t j = t0 + tid;
-                const bool has = j < s;
-                const int32_t v = has ? src[j] : 0;
-                const int d = (v >> sh) & 255;
-                for (int w = 0; w < kW; ++w) wcnt[w][tid] = 0;
-                __syncthreads();
-                const unsigned act = __ballot_sync(kFull, has);
-                int rank = 0;
-                if (has) {
-                    const unsigned peers = __match_any_sync(act, d);
-                    rank = __popc(peers & ((1u << lane) - 1));
-                    if (rank == 0) wcnt[wid][d] = __popc(peers);
+        int32_t before = kept, tile_total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) before += wtot[w];
+            tile_total += wtot[w];
+        }
+        __syncthreads();   // every thread has read its input and the counts
+        if (keep) dst[before + __popc(km & ((1u << lane) - 1))] = v;
+        if (km) {
+            unsigned long long h = keep ? pin_mix(v) : 0ull;
+            for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+            if (lane == 0) atomicAdd(hsum, h);
+        }
+        kept += tile_total;
+        __syncthreads();
+    }
+    kept_out = kept;
+    h_out = *hsum;
+}
+
+// CTA per listed net of 33..kMedium pins: bitonic sort of the mapped pins in shared memory
+// (padded to a power of two), then compaction into a and the fingerprint
+__global__ void __launch_bounds__(kSortThreads) k_ct_medium(const int64_t *off, const int32_t *pins,
+                                                            const int32_t *map, const int32_t *list,
+                                                            const int32_t *count, int32_t *a, int32_t *size1,
+                                                            unsigned long long *key, int32_t *rep)
+{
+    __shared__ int32_t buf[kMedium];
+    __shared__ int32_t wtot[kSortThreads / 32];
+    __shared__ unsigned long long hsum;
+    const int tid = threadIdx.x;
+    const int32_t cnt = *count;
+    for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int64_t e = list[i];
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        int32_t np2 = 64;
+        while (np2 < s) np2 <<= 1;
+        for (int32_t j = tid; j < np2; j += kSortThreads) buf[j] = j < s ? map[pins[b + j]] : 0x7fffffff;
+        __syncthreads();
+        for (int32_t k = 2; k <= np2; k <<= 1) {
+            for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                for (int32_t x = tid; x < np2; x += kSortThreads) {
+                    const int32_t y = x ^ j;
+                    if (y > x) {
+                        const bool up = (x & k) == 0;
+                        const int32_t vx = buf[x], vy = buf[y];
+                        if ((vx > vy) == up) { buf[x] = vy; buf[y] = vx; }
+                    }
                 }
                 __syncthreads();
-                {   // per digit (thread tid = digit): exclusive prefix over the warps
-                    int32_t run = 0;
-                    for (int w = 0; w < kW; ++w) { const int32_t c = wcnt[w][tid]; wcnt[w][tid] = run; run += c; }
-                    tile_cnt[tid] = run;
+            }
+        }
+        int32_t kept;
+        unsigned long long h;
+        compact_runs(buf, a + b, s, wtot, &hsum, kept, h);
+        if (tid == 0) net_done(e, kept, h, size1, key, rep);
+        __syncthreads();
+    }
+}
+
+// Nets of more than kMedium pins, load-balanced over the grid: every kMedium-pin chunk of every
+// such net is sorted by one CTA in shared memory (k_lg_chunk), then runs are merged pairwise,
+// each CTA producing kMedium outputs of one merge found by a merge-path search (k_lg_merge), and
+// finally one CTA per net de-duplicates and fingerprints it (k_lg_dedupe).
+constexpr int kLgThreads = 1024;
+
+// chunk task t -> (list index, chunk) through the exclusive prefix of the chunk counts
+__device__ __forceinline__ int32_t find_task(const int64_t *cpre, int32_t nl, int64_t t)
+{
+    int32_t lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (cpre[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_lg_count(const int64_t *off, const int32_t *list, const int32_t *count, int32_t *chunks,
+                           int32_t *max_size)
+{
+    const int32_t nl = *count;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = list[i];
+        const int32_t sz = (int32_t)(off[e + 1] - off[e]);
+        chunks[i] = (sz + kMedium - 1) / kMedium;
+        atomicMax(max_size, sz);
+    }
+}
+
+// CTA per large net: a representative's pins, offset and summed weight at its coarse position
+__global__ void __launch_bounds__(kLgThreads) k_lg_emit(const int64_t *off, const int32_t *a, const int32_t *size1,
+                                                        const int32_t *rep, const int64_t *nid, const int64_t *poff,
+                                                        const unsigned long long *w64, const int32_t *list,
+                                                        const int32_t *count, int32_t *pins2, int64_t *off2,
+                                                        int32_t *nw2, int32_t *err)
+{
+    const int32_t nl = *count;
+    for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
+        const int64_t e = list[i];
+        if (rep[e] != (int32_t)e) continue;
+        const int64_t src = off[e], dst = poff[e];
+        const int32_t s = size1[e];
+        for (int32_t j = threadIdx.x; j < s; j += kLgThreads) pins2[dst + j] = a[src + j];
+        if (threadIdx.x == 0) {
+            off2[nid[e]] = dst;
+            const unsigned long long w = w64[e];
+            if (w >= (1ull << 31)) atomicOr(err, ERR_UNSUPPORTED);
+            nw2[nid[e]] = (int32_t)w;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLgThreads) k_lg_chunk(const int64_t *off, const int32_t *pins, const int32_t *map,
+                                                         const int32_t *list, const int32_t *count,
+                                                         const int64_t *cpre, int64_t tasks, int32_t *a)
+{
+    __shared__ int32_t buf[kMedium];
+    const int tid = threadIdx.x;
+    const int32_t nl = *count;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int32_t li = find_task(cpre, nl, t);
+        const int64_t e = list[li];
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        const int32_t c0 = (int32_t)(t - cpre[li]) * kMedium;
+        const int32_t len = min(kMedium, s - c0);
+        for (int32_t j = tid; j < kMedium; j += kLgThreads) buf[j] = j < len ? map[pins[b + c0 + j]] : 0x7fffffff;
+        __syncthreads();
+        for (int32_t k = 2; k <= kMedium; k <<= 1) {
+            for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                for (int32_t x = tid; x < kMedium; x += kLgThreads) {
+                    const int32_t y = x ^ j;
+                    if (y > x) {
+                        const bool up = (x & k) == 0;
+                        const int32_t vx = buf[x], vy = buf[y];
+                        if ((vx > vy) == up) { buf[x] = vy; buf[y] = vx; }
+                    }
                 }
                 __syncthreads();
-                if (has) dst[base[d] + wcnt[wid][d] + rank] = v;
-                __syncthreads();
-                base[tid] += tile_cnt[tid];
-                __syncthreads();
             }
-            int32_t *t = src; src = dst; dst = t;
         }
-        // compaction: keep the first of every run of equal values, in order, into a
-        int32_t kept = 0;
-        for (int32_t t0 = 0; t0 < s; t0 += kSortThreads) {
-            const int32_t j = t0 + tid;
-            const bool has = j < s;
-            const int32_t v = has ? src[j] : 0;
-            const bool keep = has && (j == 0 || v != src[j - 1]);
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (lane == 0) wtot[wid] = __popc(km);
-            __syncthreads();
-            int32_t before = kept;
-            for (int w = 0; w < wid; ++w) before += wtot[w];
-            int32_t tile_total = 0;
-            for (int w = 0; w < kW; ++w) tile_total += wtot[w];
-            __syncthreads();   // every thread has read its input and the counts
-            if (keep) a[beg + before + __popc(km & ((1u << lane) - 1))] = v;
-            kept += tile_total;
-            __syncthreads();
+        for (int32_t j = tid; j < len; j += kLgThreads) a[b + c0 + j] = buf[j];
+        __syncthreads();
+    }
+}
+
+// merge path: number of elements taken from A among the first d outputs of merge(A, B)
+__device__ __forceinline__ int32_t merge_split(const int32_t *A, int32_t na, const int32_t *B, int32_t nb, int32_t d)
+{
+    int32_t lo = max(0, d - nb), hi = min(d, na);
+    while (lo < hi) {
+        const int32_t i = (lo + hi) >> 1;          // candidate count from A
+        if (A[i] <= B[d - 1 - i]) lo = i + 1;     // A[i] comes before B[d-1-i]: take more from A
+        else hi = i;
+    }
+    return lo;
+}
+
+// one merge pass over all large nets: runs of width w (sorted) of src are merged pairwise into
+// dst; task t = output tile of kMedium elements of one net (same task numbering as the chunks)
+__global__ void __launch_bounds__(kLgThreads) k_lg_merge(const int64_t *off, const int32_t *list, const int32_t *count,
+                                                         const int64_t *cpre, int64_t tasks, const int32_t *src,
+                                                         int32_t *dst, int32_t w)
+{
+    const int tid = threadIdx.x;
+    const int32_t nl = *count;
+    constexpr int kPer = kMedium / kLgThreads;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int32_t li = find_task(cpre, nl, t);
+        const int64_t e = list[li];
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        const int32_t o0 = (int32_t)(t - cpre[li]) * kMedium + tid * kPer;   // this thread's outputs
+        if (o0 >= s) continue;
+        const int32_t base = (o0 / (2 * w)) * (2 * w);
+        const int32_t na = min(w, s - base), nb = max(0, min(w, s - base - w));
+        const int32_t *A = src + b + base, *B = A + na;
+        int32_t i = merge_split(A, na, B, nb, o0 - base);
+        int32_t j = o0 - base - i;
+        int32_t *out = dst + b + o0;
+        const int32_t cnt = min(kPer, s - o0);
+        for (int q = 0; q < cnt; ++q) {
+            const bool takeA = j >= nb || (i < na && A[i] <= B[j]);
+            out[q] = takeA ? A[i++] : B[j++];
         }
-        if (tid == 0) size1[e] = kept;
+    }
+}
+
+// CTA per large net: compaction of the first of every run into a, and the fingerprint
+__global__ void __launch_bounds__(kLgThreads) k_lg_dedupe(const int64_t *off, const int32_t *list, const int32_t *count,
+                                                          const int32_t *src, int32_t *a, int32_t *size1,
+                                                          unsigned long long *key, int32_t *rep)
+{
+    __shared__ int32_t wtot[kLgThreads / 32];
+    __shared__ unsigned long long hsum;
+    const int32_t nl = *count;
+    for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
+        const int64_t e = list[i];
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        int32_t kept;
+        unsigned long long h;
+        compact_runs(src + b, a + b, s, wtot, &hsum, kept, h);
+        if (threadIdx.x == 0) net_done(e, kept, h, size1, key, rep);
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- identical nets
-__device__ __forceinline__ unsigned long long net_key(const int32_t *p, int32_t s, int lane)
-{
-    unsigned long long h = 0;
-    for (int32_t j = lane; j < s; j += 32) h += splitmix64_output(0x6a09e667f3bcc908ull ^ (uint64_t)(uint32_t)p[j]);
-    for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
-    unsigned long long k = splitmix64_output(h ^ ((uint64_t)(uint32_t)s << 32));
-    return k == kKeyEmpty ? k - 1 : k;
-}
-
-// warp per net: fingerprint of the sorted pin list, rep = dropped (< 2 pins) or unresolved
-__global__ void k_ct_key(const int64_t *off, const int32_t *a, const int32_t *size1, int32_t m,
-                         unsigned long long *key, int32_t *rep)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        const int32_t s = size1[e];
-        if (s < 2) {
-            if (lane == 0) rep[e] = kDropped;
-            continue;
-        }
-        const unsigned long long k = net_key(a + off[e], s, lane);
-        if (lane == 0) { key[e] = k; rep[e] = kUnresolved; }
-    }
-}
-
 struct KeySlot {
     unsigned long long key;
     int32_t min_id;
@@ -345,30 +545,45 @@ __global__ void k_ct_insert(const unsigned long long *key, const int32_t *rep, i
     }
 }
 
-// warp per unresolved net: resolved to the smallest net of its fingerprint if the pin lists are
-// equal (itself included); otherwise it stays unresolved for the next round
+// 32 nets per warp, one per lane: an unresolved net whose fingerprint's smallest net is itself
+// is resolved to itself; the others compare their pin lists with that net, the whole warp on
+// one net at a time, and are resolved to it if equal, else stay unresolved for the next round
 __global__ void k_ct_resolve(const int64_t *off, const int32_t *a, const int32_t *size1,
                              const unsigned long long *key, int32_t *rep, int32_t m, const KeySlot *tab,
                              uint64_t mask, int32_t *left)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        if (rep[e] != kUnresolved) continue;
-        const KeySlot *sl = key_find(const_cast<KeySlot *>(tab), mask, key[e], false);
-        const int32_t r = sl ? sl->min_id : (int32_t)e;
-        bool same = r == (int32_t)e;
-        if (!same && size1[r] == size1[e]) {
-            const int32_t *pe = a + off[e], *pr = a + off[r];
-            bool eq = true;
-            for (int32_t j = lane; j < size1[e]; j += 32) eq = eq && pe[j] == pr[j];
-            same = __all_sync(kFull, eq);
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x; e0 < m; e0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        int32_t r = -1;
+        bool todo = false;
+        if (e < m && rep[e] == kUnresolved) {
+            const KeySlot *sl = key_find(const_cast<KeySlot *>(tab), mask, key[e], false);
+            r = sl ? sl->min_id : (int32_t)e;
+            if (r == (int32_t)e) rep[e] = (int32_t)e;
+            else todo = true;
         }
-        __syncwarp();
-        if (lane == 0) {
-            if (same) rep[e] = r;
-            else atomicAdd(left, 1);
+        unsigned tm = __ballot_sync(kFull, todo);
+        int32_t nleft = 0;
+        while (tm) {
+            const int src = __ffs(tm) - 1;
+            tm &= tm - 1;
+            const int64_t ee = __shfl_sync(kFull, e, src);
+            const int32_t rr = __shfl_sync(kFull, r, src);
+            const int32_t se = size1[ee];
+            bool eq = size1[rr] == se;
+            if (eq) {
+                const int32_t *pe = a + off[ee], *pr = a + off[rr];
+                for (int32_t j = lane; j < se; j += 32) eq = eq && pe[j] == pr[j];
+                eq = __all_sync(kFull, eq);
+            }
+            if (lane == src) {
+                if (eq) rep[ee] = rr;
+                else ++nleft;
+            }
         }
+        nleft = __reduce_add_sync(kFull, nleft);
+        if (lane == 0 && nleft) atomicAdd(left, nleft);
     }
 }
 
@@ -385,24 +600,54 @@ __global__ void k_ct_groups(const int32_t *rep, const int32_t *size1, const int3
     }
 }
 
-// warp per representative: its pins and weight at its coarse position
+__device__ __forceinline__ int slot_in(const int32_t *off33, int32_t i)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1)
+        if (off33[lo + step] <= i) lo += step;
+    return lo;
+}
+
+// 32 nets per warp, one per lane: the representatives' pins are copied to their coarse
+// positions over the warp's flattened pin range (every lane copies a pin per step), and each
+// representative's offset and summed weight are written by its lane
 __global__ void k_ct_emit(const int64_t *off, const int32_t *a, const int32_t *size1, const int32_t *rep,
                           const int64_t *nid, const int64_t *poff, const unsigned long long *w64, int32_t m,
                           int32_t *pins2, int64_t *off2, int32_t *nw2, int32_t *err)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        if (rep[e] != (int32_t)e) continue;
-        const int64_t i = nid[e], dst = poff[e];
-        const int32_t s = size1[e];
-        for (int32_t j = lane; j < s; j += 32) pins2[dst + j] = a[off[e] + j];
-        if (lane == 0) {
-            off2[i] = dst;
+    __shared__ int32_t off33_w[8][33];
+    __shared__ int64_t src_w[8][32], dst_w[8][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *off33 = off33_w[wid];
+    for (int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) ; e0 < m; e0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = e0 + threadIdx.x;
+        int32_t s = 0;
+        if (e < m && rep[e] == (int32_t)e && off[e + 1] - off[e] <= kMedium) {   // larger: k_lg_emit
+            s = size1[e];
+            src_w[wid][lane] = off[e];
+            dst_w[wid][lane] = poff[e];
+            off2[nid[e]] = poff[e];
             const unsigned long long w = w64[e];
             if (w >= (1ull << 31)) atomicOr(err, ERR_UNSUPPORTED);
-            nw2[i] = (int32_t)w;
+            nw2[nid[e]] = (int32_t)w;
         }
+        int32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        off33[lane] = incl - s;
+        if (lane == 31) off33[32] = incl;
+        __syncwarp();
+        const int32_t total = off33[32];
+        for (int32_t i = lane; i < total; i += 32) {
+            const int v = slot_in(off33, i);
+            const int32_t k = i - off33[v];
+            pins2[dst_w[wid][v] + k] = a[src_w[wid][v] + k];
+        }
+        __syncwarp();
     }
 }
 
@@ -447,7 +692,10 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     cudaError_t e = cudaSuccess;
     int rc = HGP_OK;
     int32_t *err = nullptr, *used = nullptr, *a = nullptr, *b = nullptr, *size1 = nullptr, *rep = nullptr;
-    int32_t *is_rep = nullptr, *rep_size = nullptr, *left = nullptr;
+    int32_t *is_rep = nullptr, *rep_size = nullptr, *left = nullptr, *lists = nullptr, *counts = nullptr;
+    void *lg_scratch[2] = {nullptr, nullptr};
+    int32_t n_large = 0;
+    int sms = 1;
     int64_t *cid = nullptr, *nid = nullptr, *poff = nullptr;
     unsigned long long *w64 = nullptr, *key = nullptr, *nw64 = nullptr;
     KeySlot *tab = nullptr;
@@ -490,29 +738,62 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(cudaMallocAsync(reinterpret_cast<void **>(&a), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
     CT(cudaMallocAsync(reinterpret_cast<void **>(&b), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
     CT(cudaMallocAsync(reinterpret_cast<void **>(&size1), sizeof(int32_t) * (size_t)mm, st));
-    if (m > 0) {
-        int passes = 1;
-        while (passes < 4 && ((n2 - 1) >> (8 * passes)) > 0) ++passes;
-        k_ct_small<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins, m, c->map, a, size1);
-        k_ct_large<<<grid_of(m, 1) < 4096 ? grid_of(m, 1) : 4096, kSortThreads, 0, st>>>(net_off, pins, m, c->map, a, b, size1, passes);
-        CT(cudaGetLastError());
-    }
-    // (4) identical nets
     CT(cudaMallocAsync(reinterpret_cast<void **>(&key), sizeof(unsigned long long) * (size_t)mm, st));
     CT(cudaMallocAsync(reinterpret_cast<void **>(&rep), sizeof(int32_t) * (size_t)mm, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&lists), sizeof(int32_t) * 3 * (size_t)mm + 16, st));
+    counts = lists + 3 * mm;
+    CT(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 3, st));
+    if (m > 0) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        k_ct_tiny<<<grid_of(m, 256), 256, 0, st>>>(net_off, pins, m, c->map, a, size1, key, rep, lists, counts);
+        k_ct_small<<<sms * 8, 256, 0, st>>>(net_off, pins, c->map, lists, counts, a, size1, key, rep);
+        k_ct_medium<<<sms * 8, kSortThreads, 0, st>>>(net_off, pins, c->map, lists + mm, counts + 1, a, size1, key, rep);
+        CT(cudaGetLastError());
+        // nets of more than kMedium pins: chunk sorts, merge passes, de-duplication
+        int32_t hcnt[4] = {0, 0, 0, 0};
+        CT(cudaMemcpyAsync(hcnt, counts, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, st));
+        CT(cudaStreamSynchronize(st));
+        n_large = hcnt[2];
+        if (n_large > 0) {
+            int32_t *chunks = nullptr;
+            int64_t *cpre = nullptr;
+            CT(cudaMallocAsync(reinterpret_cast<void **>(&chunks), sizeof(int32_t) * ((size_t)n_large + 1), st));
+            CT(cudaMallocAsync(reinterpret_cast<void **>(&cpre), sizeof(int64_t) * ((size_t)n_large + 1), st));
+            lg_scratch[0] = chunks;
+            lg_scratch[1] = cpre;
+            CT(cudaMemsetAsync(counts + 3, 0, sizeof(int32_t), st));
+            k_lg_count<<<grid_of(n_large, 256), 256, 0, st>>>(net_off, lists + 2 * mm, counts + 2, chunks, counts + 3);
+            CT(cudaGetLastError());
+            CT(scan_excl<int32_t>(chunks, n_large, cpre, st));
+            int64_t tasks = 0;
+            int32_t max_size = 0;
+            CT(cudaMemcpyAsync(&tasks, cpre + n_large, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            CT(cudaMemcpyAsync(&max_size, counts + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CT(cudaStreamSynchronize(st));
+            const int g = (int)(tasks < (int64_t)sms * 2 ? tasks : (int64_t)sms * 2);
+            k_lg_chunk<<<g, kLgThreads, 0, st>>>(net_off, pins, c->map, lists + 2 * mm, counts + 2, cpre, tasks, a);
+            int32_t *src = a, *dst = b;
+            for (int64_t w = kMedium; w < max_size; w *= 2) {
+                k_lg_merge<<<g, kLgThreads, 0, st>>>(net_off, lists + 2 * mm, counts + 2, cpre, tasks, src, dst, (int32_t)w);
+                int32_t *t = src; src = dst; dst = t;
+            }
+            k_lg_dedupe<<<n_large < sms * 2 ? n_large : sms * 2, kLgThreads, 0, st>>>(net_off, lists + 2 * mm, counts + 2,
+                                                                                     src, a, size1, key, rep);
+            CT(cudaGetLastError());
+        }
+    }
+    // (4) identical nets
     if (m > 0) {
         uint64_t size = 1024;
         while (size < 2 * (uint64_t)m) size <<= 1;
         CT(cudaMallocAsync(reinterpret_cast<void **>(&tab), sizeof(KeySlot) * size, st));
-        k_ct_key<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, m, key, rep);
-        CT(cudaGetLastError());
         for (int round = 0;; ++round) {
             if (round >= 4096) { rc = HGP_ERR_INTERNAL; goto done; }
             int32_t hleft = 0;
             CT(cudaMemsetAsync(left, 0, sizeof(int32_t), st));
             k_ct_table_clear<<<grid_of((int64_t)size, 256), 256, 0, st>>>(tab, (int64_t)size);
             k_ct_insert<<<grid_of(m, 256), 256, 0, st>>>(key, rep, m, tab, size - 1, err);
-            k_ct_resolve<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, key, rep, m, tab, size - 1, left);
+            k_ct_resolve<<<grid_of(m, 256), 256, 0, st>>>(net_off, a, size1, key, rep, m, tab, size - 1, left);
             CT(cudaGetLastError());
             CT(cudaMemcpyAsync(&hleft, left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             CT(cudaStreamSynchronize(st));
@@ -542,7 +823,11 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(cudaMalloc(reinterpret_cast<void **>(&c->nw), sizeof(int32_t) * (size_t)(m2 > 0 ? m2 : 1)));
     CT(cudaMemcpyAsync(c->net_off + m2, &P2, sizeof(int64_t), cudaMemcpyHostToDevice, st));
     if (m > 0) {
-        k_ct_emit<<<grid_of((int64_t)m * 32, 256), 256, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64, m,
+        if (n_large > 0)
+            k_lg_emit<<<n_large < sms * 2 ? n_large : sms * 2, kLgThreads, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64,
+                                                                                   lists + 2 * mm, counts + 2, c->pins,
+                                                                                   c->net_off, c->nw, err);
+        k_ct_emit<<<grid_of(m, 256), 256, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64, m,
                                                                  c->pins, c->net_off, c->nw, err);
         CT(cudaGetLastError());
     }
@@ -561,6 +846,9 @@ done:
     if (key) cudaFreeAsync(key, st);
     if (rep) cudaFreeAsync(rep, st);
     if (tab) cudaFreeAsync(tab, st);
+    if (lists) cudaFreeAsync(lists, st);
+    for (void *q : lg_scratch)
+        if (q) cudaFreeAsync(q, st);
     if (is_rep) cudaFreeAsync(is_rep, st);
     if (rep_size) cudaFreeAsync(rep_size, st);
     if (nid) cudaFreeAsync(nid, st);

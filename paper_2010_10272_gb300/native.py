@@ -379,7 +379,7 @@ class Batch:
                                           ctypes.byref(self._b)), "hgp_batch_create")
 
     def refine(self, rounds: int, stats: bool = True):
-        """Runs `rounds` rounds on every member; returns int64 [count x rounds x 6] or None."""
+        """Runs `rounds` rounds on every member; returns int64 [count x rounds x 7] or None."""
         n = len(self.handles)
         if stats:
             buf = (RoundStats * max(1, n * rounds))()

@@ -109,3 +109,41 @@ def test_invalid_cluster_ids():
     bad[5] = hg.n
     with pytest.raises(HGPError):
         Coarse(hg.n, hg.m, _dev(hg.net_off), _dev(hg.pins), None, None, _dev(bad))
+
+
+def test_all_levels_of_one_hierarchy_in_one_batch():
+    """Levels H0..H3 from repeated contraction, refined together in one batch (one launch per
+    phase over all levels): every level's result equals the level refined alone, and the
+    oracle's on the coarse arrays."""
+    from paper_2010_10272_gb300 import HGP, Batch, Coarse
+    hg = synth.random_small(420, 30000, 26000, 8, max_size=8, weighted=True, eps=0.05)
+    levels = [hg]
+    coarse = []
+    cur = {"n": hg.n, "m": hg.m, "net_off": hg.net_off, "pins": hg.pins,
+           "vertex_w": hg.vertex_w, "net_w": hg.net_w}
+    for lv in range(3):
+        c = Coarse(cur["n"], cur["m"], _dev(cur["net_off"]), _dev(cur["pins"]), _dev(cur["vertex_w"]),
+                   _dev(cur["net_w"]), _dev(_pairs(cur["n"], 10 + lv).astype(np.int32)))
+        coarse.append(c)
+        cur = c.to_host()
+    arrays = [{"n": hg.n, "m": hg.m, "net_off": hg.net_off, "pins": hg.pins, "vertex_w": hg.vertex_w,
+               "net_w": hg.net_w}] + [c.to_host() for c in coarse]
+    rng = np.random.default_rng(5)
+    parts = [rng.integers(0, hg.k, size=a["n"]).astype(np.int32) for a in arrays]
+
+    def make(i):
+        a = arrays[i]
+        return HGP(a["n"], a["m"], a["net_off"], a["pins"], hg.k, hg.eps, parts[i], a["vertex_w"], a["net_w"],
+                   subrounds=3, seed=i)
+    hs = [make(i) for i in range(len(arrays))]
+    b = Batch(hs)
+    got = b.refine(4)
+    for i, a in enumerate(arrays):
+        alone = make(i)
+        np.testing.assert_array_equal(got[i][:, :5], alone.refine(4)[:, :5])
+        np.testing.assert_array_equal(hs[i].partition(), alone.partition())
+        o = oracle.Oracle(a["n"], a["m"], a["net_off"], a["pins"], hg.k, hg.eps, parts[i], a["vertex_w"],
+                          a["net_w"], 3, i)
+        np.testing.assert_array_equal(got[i][:, :5], o.refine(4)[0])
+    b.close()
+    assert arrays[-1]["n"] < arrays[0]["n"] // 6
