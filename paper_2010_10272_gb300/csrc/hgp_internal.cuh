@@ -24,6 +24,7 @@ namespace hgp {
 constexpr int kRange = 256;              // consecutive vertices handled by one warp
 constexpr int kWarps = 8;                // warps per tile CTA
 constexpr int kRvSlotBytes = 32;         // one slot of the revert variant's hash table
+constexpr int kWqPerRow = 128;           // work counters per stats row: 64 sub-rounds x 2 kernels
 constexpr int kTile = kRange * kWarps;   // vertices per tile (one CTA)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kBins = 4096;              // approval histogram bins (gains 1..4094 exact)
@@ -95,6 +96,8 @@ struct Dev {
     Sel *sel;               // [k]
     int64_t *tie;           // [k * n_tiles]
     int64_t *stats;         // [rounds * ST_N]
+    int32_t *wq;            // [rounds * kWqPerRow] work counters of the single-instance persistent
+                            // kernels (nullptr in batches: static assignment)
     int32_t *err;
     uint64_t seed;          // sub-round hash seed
     int32_t variant;        // bit 0: zero-gain balance moves; bit 1: revert negative moves

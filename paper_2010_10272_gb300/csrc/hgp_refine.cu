@@ -552,6 +552,25 @@ __device__ __forceinline__ void gain_refresh(const Dev &d, long long *slack, Gai
     gi.all_elig = d.rs[1] == 0;
 }
 
+// Dynamic work distribution of the single-instance persistent kernels: a warp takes its next
+// range item from a per-launch device counter (zeroed before the launch), so the last items go
+// to whichever warps are free instead of a fixed stride.
+__device__ __forceinline__ int32_t take_item(int32_t *counter)
+{
+    int32_t it = 0;
+    if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1);
+    return __shfl_sync(kFull, it, 0);
+}
+
+// the counter increment is issued by lane 0 before the current item is processed; its result
+// is only read (broadcast) when the item is done, so the round trip overlaps the work
+__device__ __forceinline__ int32_t take_item_early(int32_t *counter)
+{
+    int32_t it = 0;
+    if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1);
+    return it;
+}
+
 // copies devs[inst] into a warp's shared slot
 __device__ __forceinline__ void load_dev(Dev &dst, const Dev *src)
 {
@@ -590,7 +609,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
     int32_t nelig = 0, ncand = 0;
     int inst_prev = -1;
     const int32_t n_it = B ? n_items : d0.n_ranges;
-    for (int32_t item = blockIdx.x * kWarps + wid; item < n_it; item += gridDim.x * kWarps) {
+    int32_t *wq = B ? nullptr : d0.wq + ((int64_t)rr * 64 + s) * 2;
+    int32_t next_raw = 0;
+    for (int32_t item = B ? blockIdx.x * kWarps + wid : take_item(wq); item < n_it;
+         item = B ? item + gridDim.x * kWarps : __shfl_sync(kFull, next_raw, 0)) {
+        if (!B) next_raw = take_item_early(wq);
         if (B) {
             const int2 it = items[item];
             if (it.x != inst_prev) {
@@ -1183,7 +1206,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
 // B as for k_gain.
 template <typename Rec, bool B, int KEY = KEY_T>
 __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *devs, const int2 *items,
-                                                       int32_t n_items, int32_t rr)
+                                                       int32_t n_items, int32_t rr, int32_t sub)
 {
     __shared__ ApplyInst ai_w[kWarps];
     __shared__ unsigned long long run[kWarps][64];
@@ -1198,6 +1221,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
     int inst_prev = -1;
     bool any_thr = false;
     const int32_t n_it = B ? n_items : d0.n_ranges;
+    // static assignment: the 8 warps of a CTA take the 8 ranges of one tile, whose candidates
+    // the tie prefixes read (measured faster here than the gain step's dynamic distribution)
+    (void)sub;
     for (int32_t item = blockIdx.x * kWarps + wid; item < n_it; item += gridDim.x * kWarps) {
         long long idobj = 0;
         int32_t iappr = 0, ipins = 0;
@@ -1727,10 +1753,10 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         if (e == cudaSuccess) e = phase_begin(p.prof);
         if (e != cudaSuccess) break;
         const bool b = p.ranges != nullptr;
-        if (p.rec32 && b) k_apply<Rec32, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
-        else if (p.rec32) k_apply<Rec32, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
-        else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
-        else k_apply<Rec16, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr);
+        if (p.rec32 && b) k_apply<Rec32, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
+        else if (p.rec32) k_apply<Rec32, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
+        else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
+        else k_apply<Rec16, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
         *p.launches += 1;
         e = cudaGetLastError();
         if (e == cudaSuccess) e = phase_end(p.prof, PH_APPLY, 1);
@@ -1807,6 +1833,7 @@ Plan single_plan(hgp_handle *h)
 cudaError_t enqueue_rounds(const Plan &p, int64_t *stats, int32_t rounds)
 {
     cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int64_t) * ST_N * (size_t)rounds, p.st);
+    if (e == cudaSuccess && p.d0.wq) e = cudaMemsetAsync(p.d0.wq, 0, sizeof(int32_t) * kWqPerRow * (size_t)rounds, p.st);
     for (int32_t rr = 0; rr < rounds && e == cudaSuccess; ++rr) e = launch_round(p, rr);
     return e;
 }
@@ -1821,7 +1848,10 @@ int ensure_stats(hgp_handle *h, int32_t rounds)
     int32_t cap = h->stats_cap ? h->stats_cap : 16;
     while (cap < rounds) cap *= 2;
     int64_t *dev = nullptr, *host = nullptr;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dev), sizeof(int64_t) * ST_N * (size_t)cap);
+    // stats rows, then the work counters of the persistent kernels: 64 sub-rounds x (gain, apply)
+    // per row
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dev), sizeof(int64_t) * ST_N * (size_t)cap +
+                                                                    sizeof(int32_t) * kWqPerRow * (size_t)cap);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&host), sizeof(int64_t) * ST_N * (size_t)cap);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1832,6 +1862,7 @@ int ensure_stats(hgp_handle *h, int32_t rounds)
     if (h->d.stats) cudaFree(h->d.stats);
     if (h->h_stats) cudaFreeHost(h->h_stats);
     h->d.stats = dev;
+    h->d.wq = reinterpret_cast<int32_t *>(dev + (size_t)ST_N * cap);
     h->h_stats = host;
     h->stats_cap = cap;
     h->dev_dirty = true;
@@ -1940,6 +1971,8 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
 
 int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 {
+    const int rc = ensure_stats(h, 1);
+    if (rc != HGP_OK) return rc;
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     cudaError_t e = sync_dev(h);
@@ -1956,6 +1989,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     if (e == cudaSuccess) e = cudaMemsetAsync(g_d, 0, sizeof(int64_t) * (size_t)d.n, st);
     // the stats row written here is scratch: refine() clears the stats before use
     if (e == cudaSuccess) e = launch_prep(p);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.wq, 0, sizeof(int32_t) * kWqPerRow, st);
     if (e == cudaSuccess) e = launch_gain(p, s, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tot, 0, sizeof(int64_t) * 64, st);
     if (e == cudaSuccess) {
@@ -2014,7 +2048,7 @@ cudaError_t launch_rebalance_pass(const Plan &p, int32_t pass, RbArgs rb, bool l
         k_rb_mark<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.d0);
         *p.launches += 1;
         *p.launches += launch_stage<KEY_TS>(p, levels);
-        k_apply<Rec, false, KEY_TS><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, pass);
+        k_apply<Rec, false, KEY_TS><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, pass, s);
         *p.launches += 1;
     }
     k_round_end<<<1, 128, 0, p.st>>>(p.devs, 1, pass, 0);
@@ -2038,6 +2072,7 @@ extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats 
     cudaError_t e = sync_dev(h);
     const cudaStream_t st = h->stream;
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d.stats, 0, sizeof(int64_t) * ST_N * (size_t)max_passes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d.wq, 0, sizeof(int32_t) * kWqPerRow * (size_t)max_passes, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
