@@ -160,27 +160,7 @@ __global__ void k_check_nets(const int32_t *nw, int32_t m, int32_t *err)
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
 }
 
-// ------------------------------------------------------------------ transpose
-__global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg)
-{
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
-         j += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&deg[pins[j]], 1);
-}
-
-__global__ void k_scatter(const int32_t *off, const int32_t *pins, int32_t m, int32_t *fill, int32_t *inc)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        const int32_t b = off[e], end = off[e + 1];
-        for (int32_t j = b + lane; j < end; j += 32) {
-            const int32_t pos = atomicAdd(&fill[pins[j]], 1);
-            inc[pos] = (int32_t)e;
-        }
-    }
-}
-
+// ------------------------------------------------------------------ per-vertex net weight
 // W(u) = sum of incident net weights must stay below 2^31 (int32 gain arithmetic)
 __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, const int32_t *nw,
                                    int32_t n, int32_t *err, unsigned long long *max_w)
@@ -189,7 +169,7 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         int64_t s = 0;
-        for (int32_t j = vtx_off[v]; j < vtx_off[v + 1]; ++j) s += nw ? nw[inc[j]] : 1;
+        for (int32_t j = vtx_off[v]; j < vtx_off[v + 1]; ++j) s += nw ? nw[inc[j] & kNetMask] : 1;
         if (s >= (int64_t)1 << 31) atomicOr(err, ERR_UNSUPPORTED);
         local = max(local, (unsigned long long)s);
     }
@@ -197,13 +177,116 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
     if ((threadIdx.x & 31) == 0) atomicMax(max_w, local);
 }
 
-// bit 31 of inc[j] marks incidences of nets whose Phi row lives in the wide table
-__global__ void k_flag_wide_inc(const int32_t *off, int32_t *inc, int64_t P, int32_t narrow_max)
+// ------------------------------------------------------------------ transpose (net -> vertex)
+// Bucketed: vertices are grouped into buckets of 2^bshift consecutive ids (at most
+// kTpMaxBuckets buckets).  k_tp_hist counts the pins per bucket; k_tp_scatter writes every pin
+// as a (vertex, net | wide flag) pair into its bucket's region, reserving one range per (CTA,
+// bucket) with a single global atomic; k_tp_place, a CTA per bucket, counts the degrees of its
+// vertices, scans them into vtx_off and places the nets into inc.  Every step but the pair
+// scatter stays inside one bucket's few hundred KB, so the random accesses hit L2.
+constexpr int kTpMaxBuckets = 4096;
+constexpr int kTpMinShift = 16;          // at least 65536 vertices per bucket
+constexpr int kTpNetsPerCta = 32768;
+
+__global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P, int bshift, int32_t nb,
+                                                 int32_t *bucket_cnt)
 {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = inc[j];
-        if (off[e + 1] - off[e] > narrow_max) inc[j] = e | (int32_t)kWideFlag;
+    __shared__ int32_t h[kTpMaxBuckets];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P; j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[pins[j] >> bshift], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (h[i]) atomicAdd(&bucket_cnt[i], h[i]);
+}
+
+// CTA per kTpNetsPerCta nets; pass 0 counts its pins per bucket, then one range per bucket is
+// reserved, pass 1 writes the pairs.  A net of at most 32 pins is walked by one lane, a larger
+// one by the whole warp.
+__global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m, int bshift,
+                                                    int32_t nb, int32_t narrow_max, int32_t *bucket_cur,
+                                                    unsigned long long *pairs)
+{
+    __shared__ int32_t cur[kTpMaxBuckets];
+    const int lane = threadIdx.x & 31;
+    const int64_t e_lo = (int64_t)blockIdx.x * kTpNetsPerCta;
+    const int64_t e_hi = min((int64_t)m, e_lo + kTpNetsPerCta);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t e0 = e_lo + (threadIdx.x & ~31); e0 < e_hi; e0 += blockDim.x) {
+            const int64_t e = e0 + lane;
+            int32_t b = 0, sz = 0;
+            if (e < e_hi) {
+                b = off[e];
+                sz = off[e + 1] - b;
+            }
+            const bool small = e < e_hi && sz <= 32;
+            if (small) {
+                const uint32_t ef = (uint32_t)e | (sz > narrow_max ? kWideFlag : 0u);
+                for (int32_t j = b; j < b + sz; ++j) {
+                    const int32_t v = pins[j];
+                    const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
+                    if (pass == 1) pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+                }
+            }
+            unsigned big = __ballot_sync(kFull, e < e_hi && !small);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const int64_t ee = e0 + src;
+                const int32_t bb = __shfl_sync(kFull, b, src), s2 = __shfl_sync(kFull, sz, src);
+                const uint32_t ef = (uint32_t)ee | (s2 > narrow_max ? kWideFlag : 0u);
+                for (int32_t j = bb + lane; j < bb + s2; j += 32) {
+                    const int32_t v = pins[j];
+                    const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
+                    if (pass == 1) pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+                }
+            }
+        }
+        __syncthreads();
+        if (pass == 0) {
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+                const int32_t c = cur[i];
+                cur[i] = c ? atomicAdd(&bucket_cur[i], c) : 0;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// CTA per bucket: degrees, their exclusive prefix (from the bucket's first pair position) into
+// vtx_off, then the nets of the bucket's pairs into inc.  cursor: zeroed int32[n].
+__global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pairs, const int32_t *bucket_off,
+                                                   int bshift, int32_t n, int32_t nb, int32_t *cursor,
+                                                   int32_t *vtx_off, int32_t *inc)
+{
+    __shared__ int32_t wt[32];
+    __shared__ int32_t tot;
+    const int32_t bkt = blockIdx.x;
+    const int64_t v0 = (int64_t)bkt << bshift;
+    const int64_t v1 = min((int64_t)n, v0 + ((int64_t)1 << bshift));
+    const int32_t p0 = bucket_off[bkt], p1 = bucket_off[bkt + 1];
+    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) atomicAdd(&cursor[(int32_t)(pairs[i] >> 32)], 1);
+    __syncthreads();
+    int32_t carry = p0;
+    for (int64_t base = v0; base < v1; base += blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        const int32_t dv = v < v1 ? __ldcg(&cursor[v]) : 0;
+        const int32_t ex = block_exclusive_scan(dv, wt, &tot);
+        if (v < v1) {
+            vtx_off[v] = carry + ex;
+            cursor[v] = carry + ex;
+        }
+        carry += tot;
+    }
+    if (bkt == nb - 1 && threadIdx.x == 0) vtx_off[n] = p1;
+    __syncthreads();
+    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+        const unsigned long long pr = pairs[i];
+        const int32_t pos = atomicAdd(&cursor[(int32_t)(pr >> 32)], 1);
+        inc[pos] = (int32_t)(uint32_t)pr;
     }
 }
 
@@ -235,8 +318,36 @@ __global__ void k_block_weights(Dev d)
         atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[threadIdx.x]), w[threadIdx.x]);
 }
 
-// Warp per net: counts Phi(e, .) from the partition, writes the Phi row, the record
-// (Lambda, S1, omega, stamp) and adds (lambda(e) - 1) * omega(e) to the objective.
+// Counts Phi(e, .) from the partition, writes the Phi row (into a zeroed table), the record
+// (Lambda, S1, omega, stamp) and adds (lambda(e) - 1) * omega(e) to the objective.  A warp takes
+// 32 consecutive nets, one per lane: a net of at most kSmallNet pins is counted by its lane in
+// registers (only its non-zero Phi entries are stored); larger nets are then counted by the
+// whole warp, one at a time, with shared-memory counters.
+constexpr int kSmallNet = 8;
+
+template <typename Rec>
+__device__ __forceinline__ void write_record(const Dev &d, int64_t e, uint64_t lam, uint64_t s1, int32_t wf)
+{
+    Rec *rec = reinterpret_cast<Rec *>(d.rec) + e;
+    if constexpr (sizeof(Rec) == 16) {
+        Rec r;
+        r.s1 = (uint32_t)s1;
+        r.w = wf;
+        r.mv = kNever * 2;
+        r.lam = (uint32_t)lam;
+        *rec = r;
+    } else {
+        Rec r;
+        r.s1 = s1;
+        r.w = wf;
+        r.mv = kNever * 2;
+        r.lam = lam;
+        r.w2 = wf;
+        r.pad = 0;
+        *rec = r;
+    }
+}
+
 template <typename Rec>
 __global__ void k_init_nets(Dev d)
 {
@@ -244,57 +355,94 @@ __global__ void k_init_nets(Dev d)
     __shared__ long long part_obj[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t warps = (int64_t)gridDim.x * kWarps;
+    const int32_t narrow_max = d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff);
     long long obj = 0;
-    for (int64_t e = (int64_t)blockIdx.x * kWarps + wid; e < d.m; e += warps) {
-        cnt[wid][lane] = 0;
-        cnt[wid][lane + 32] = 0;
-        __syncwarp();
-        const int32_t b = d.net_off[e], end = d.net_off[e + 1];
-        for (int32_t base = b; base < end; base += 32) {
-            const int32_t j = base + lane;
-            const bool act = j < end;
-            const unsigned mask = __ballot_sync(kFull, act);
-            if (act) {
-                const int blk = d.part[d.pins[j]];
-                const unsigned peers = __match_any_sync(mask, blk);
-                if (lane == __ffs(peers) - 1) cnt[wid][blk] += __popc(peers);
+    for (int64_t e0 = ((int64_t)blockIdx.x * kWarps + wid) * 32; e0 < d.m; e0 += warps * 32) {
+        const int64_t e = e0 + lane;
+        int32_t b = 0, size = 0;
+        if (e < d.m) {
+            b = d.net_off[e];
+            size = d.net_off[e + 1] - b;
+        }
+        const bool small = e < d.m && size <= kSmallNet;
+        if (small) {
+            int32_t blk[kSmallNet], c[kSmallNet];
+            int nd = 0;
+#pragma unroll
+            for (int i = 0; i < kSmallNet; ++i) {
+                blk[i] = -1;
+                c[i] = 0;
+            }
+#pragma unroll
+            for (int i = 0; i < kSmallNet; ++i) {
+                if (i < size) {
+                    const int bk = d.part[d.pins[b + i]];
+                    bool found = false;
+#pragma unroll
+                    for (int j = 0; j < kSmallNet; ++j) {
+                        if (blk[j] == bk) { ++c[j]; found = true; }
+                    }
+                    if (!found) {
+#pragma unroll
+                        for (int j = 0; j < kSmallNet; ++j)
+                            if (j == nd) { blk[j] = bk; c[j] = 1; }
+                        ++nd;
+                    }
+                }
+            }
+            uint64_t lam = 0, s1 = 0;
+#pragma unroll
+            for (int j = 0; j < kSmallNet; ++j) {
+                if (j < nd) {
+                    lam |= 1ull << blk[j];
+                    if (c[j] == 1) s1 |= 1ull << blk[j];
+                    phi_set(d, (int32_t)e, blk[j], c[j], false, 0);
+                }
+            }
+            const int32_t wv = d.nw ? d.nw[e] : 1;
+            write_record<Rec>(d, e, lam, s1, wv);
+            if (nd > 0) obj += (long long)(nd - 1) * wv;
+        }
+        // larger nets: the whole warp on one net at a time
+        unsigned big = __ballot_sync(kFull, e < d.m && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t ee = e0 + src;
+            const int32_t bb = __shfl_sync(kFull, b, src), sz = __shfl_sync(kFull, size, src);
+            cnt[wid][lane] = 0;
+            cnt[wid][lane + 32] = 0;
+            __syncwarp();
+            for (int32_t base = bb; base < bb + sz; base += 32) {
+                const int32_t j = base + lane;
+                const bool act = j < bb + sz;
+                const unsigned mask = __ballot_sync(kFull, act);
+                if (act) {
+                    const int blk = d.part[d.pins[j]];
+                    const unsigned peers = __match_any_sync(mask, blk);
+                    if (lane == __ffs(peers) - 1) cnt[wid][blk] += __popc(peers);
+                }
+                __syncwarp();
+            }
+            const int32_t wv = d.nw ? d.nw[ee] : 1;
+            const bool wide = d.widx != nullptr && sz > narrow_max;
+            const int32_t wrow = wide ? d.widx[ee] : 0;
+            for (int i = lane; i < d.k; i += 32) phi_set(d, (int32_t)ee, i, cnt[wid][i], wide, wrow);
+            const unsigned lo_lam = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] > 0);
+            const unsigned lo_s1 = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] == 1);
+            const unsigned hi_lam = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] > 0);
+            const unsigned hi_s1 = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] == 1);
+            if (lane == 0) {
+                const int32_t wf = wv | (wide ? (int32_t)kWideFlag : 0);
+                write_record<Rec>(d, ee, (uint64_t)lo_lam | ((uint64_t)hi_lam << 32),
+                                  (uint64_t)lo_s1 | ((uint64_t)hi_s1 << 32), wf);
+                const int lambda = __popc(lo_lam) + __popc(hi_lam);
+                if (lambda > 0) obj += (long long)(lambda - 1) * wv;
             }
             __syncwarp();
         }
-        const int32_t size = end - b;
-        const int32_t wv = d.nw ? d.nw[e] : 1;
-        const bool wide = d.widx != nullptr && size > (d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff));
-        const int32_t wrow = wide ? d.widx[e] : 0;
-        for (int i = lane; i < d.k; i += 32) phi_set(d, (int32_t)e, i, cnt[wid][i], wide, wrow);
-        const unsigned lo_lam = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] > 0);
-        const unsigned lo_s1 = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] == 1);
-        const unsigned hi_lam = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] > 0);
-        const unsigned hi_s1 = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] == 1);
-        if (lane == 0) {
-            const int32_t wf = wv | (wide ? (int32_t)kWideFlag : 0);
-            Rec *rec = reinterpret_cast<Rec *>(d.rec) + e;
-            if constexpr (sizeof(Rec) == 16) {
-                Rec r;
-                r.s1 = lo_s1;
-                r.w = wf;
-                r.mv = kNever * 2;
-                r.lam = lo_lam;
-                *rec = r;
-            } else {
-                Rec r;
-                r.s1 = (uint64_t)lo_s1 | ((uint64_t)hi_s1 << 32);
-                r.w = wf;
-                r.mv = kNever * 2;
-                r.lam = (uint64_t)lo_lam | ((uint64_t)hi_lam << 32);
-                r.w2 = wf;
-                r.pad = 0;
-                *rec = r;
-            }
-            const int lambda = __popc(lo_lam) + __popc(hi_lam);
-            if (lambda > 0) obj += (long long)(lambda - 1) * wv;
-        }
-        __syncwarp();
     }
+    for (int o = 16; o; o >>= 1) obj += __shfl_xor_sync(kFull, obj, o);
     if (lane == 0) part_obj[wid] = obj;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -417,9 +565,13 @@ int init_state(hgp_handle *h)
     CK(cudaMemsetAsync(d.obj, 0, sizeof(int64_t), st));
     // round 0, every vertex eligible
     CK(cudaMemsetAsync(d.rs, 0, 2 * sizeof(int32_t), st));
+    // the net kernel stores only the non-zero Phi entries of small nets
+    const int64_t words = ((int64_t)d.m * d.k * d.phi_w + 3) / 4;
+    CK(cudaMemsetAsync(d.phi, 0, sizeof(uint32_t) * (size_t)(words < 1 ? 1 : words), st));
+    if (d.phi_wide && h->n_wide > 0) CK(cudaMemsetAsync(d.phi_wide, 0, sizeof(int32_t) * (size_t)h->n_wide * d.k, st));
     k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
     CK(cudaGetLastError());
-    const int g = grid_for((int64_t)d.m * 32, kThreads, 152 * 16);
+    const int g = grid_for(((int64_t)d.m + 31) / 32 * 32, kThreads, 152 * 16);
     if (d.k <= 32) { k_init_nets<Rec16><<<g, kThreads, 0, st>>>(d); h->launches++; }
     else { k_init_nets<Rec32><<<g, kThreads, 0, st>>>(d); h->launches++; }
     CK(cudaGetLastError());
@@ -581,16 +733,33 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         d.phi_wide = pw;
     }
 
-    // ---- vertex -> nets CSR
+    // ---- vertex -> nets CSR (bucketed transpose; the wide flag goes into inc on the way)
     int32_t *vtx_off = nullptr, *inc = nullptr;
     CKF(dalloc(h, &vtx_off, (int64_t)n + 1));
     CKF(dalloc(h, &inc, P));
     CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
-    if (P) { k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp); h->launches++; }
-    CKF(scan(tmp, vtx_off, n));
-    CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    if (m > 0) { k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, tmp, inc); h->launches++; }
-    CKF(cudaGetLastError());
+    if (P > 0) {
+        int bshift = kTpMinShift;
+        while ((((int64_t)n + ((int64_t)1 << bshift) - 1) >> bshift) > kTpMaxBuckets) ++bshift;
+        const int32_t nbk = (int32_t)(((int64_t)n + ((int64_t)1 << bshift) - 1) >> bshift);
+        int32_t *bk = nullptr;           // counts [nbk + 1], offsets [nbk + 1], cursors [nbk]
+        unsigned long long *pairs = nullptr;
+        CKF(cudaMallocAsync(reinterpret_cast<void **>(&bk), sizeof(int32_t) * (3 * (size_t)nbk + 2), st));
+        CKF(cudaMallocAsync(reinterpret_cast<void **>(&pairs), sizeof(unsigned long long) * (size_t)P, st));
+        int32_t *bk_cnt = bk, *bk_off = bk + nbk + 1, *bk_cur = bk + 2 * nbk + 2;
+        CKF(cudaMemsetAsync(bk_cnt, 0, sizeof(int32_t) * ((size_t)nbk + 1), st));
+        k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt); h->launches++;
+        CKF(scan(bk_cnt, bk_off, nbk));
+        CKF(cudaMemcpyAsync(bk_cur, bk_off, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st));
+        const int64_t sc = ((int64_t)m + kTpNetsPerCta - 1) / kTpNetsPerCta;
+        k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, bshift, nbk, narrow_max, bk_cur, pairs); h->launches++;
+        k_tp_place<<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc); h->launches++;
+        CKF(cudaGetLastError());
+        CKF(cudaFreeAsync(pairs, st));
+        CKF(cudaFreeAsync(bk, st));
+    } else {
+        CKF(cudaMemsetAsync(vtx_off, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+    }
     d.vtx_off = vtx_off;
     d.inc = inc;
 
@@ -604,10 +773,6 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(cudaStreamSynchronize(st));
     if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
     h->max_vertex_netweight = (int64_t)maxw;
-    if (h->n_wide > 0 && P > 0) {
-        k_flag_wide_inc<<<grid_for(P, 256), 256, 0, st>>>(net_off, inc, P, narrow_max); h->launches++;
-        CKF(cudaGetLastError());
-    }
 
     // ---- state
     uint8_t *part = nullptr;
@@ -618,8 +783,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     const int64_t words = (entries * w + 3) / 4;
     uint32_t *phi = nullptr;
     CKF(dalloc(h, &phi, words));
-    CKF(cudaMemsetAsync(phi, 0, sizeof(uint32_t) * (size_t)(words < 1 ? 1 : words), st));
-    d.phi = phi;
+    d.phi = phi;   // zeroed by init_state
     const size_t rec_bytes = k <= 32 ? sizeof(Rec16) : sizeof(Rec32);
     uint4 *rec = nullptr;
     CKF(dalloc(h, &rec, (int64_t)m * (int64_t)(rec_bytes / 16)));

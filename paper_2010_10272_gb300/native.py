@@ -258,11 +258,16 @@ class HGP:
         _check(self._lib.hgp_objective_from_phi(self._h, ctypes.byref(out)), "hgp_objective_from_phi")
         return out.value
 
-    def partition(self, out_device=None) -> Optional[np.ndarray]:
+    def partition(self, out_device=None, out=None) -> Optional[np.ndarray]:
+        """The partition as int32[n]: into the device tensor out_device, into the host array
+        `out` (e.g. page-locked, for a faster copy), or into a new numpy array."""
         if out_device is not None:
             _check(self._lib.hgp_get_partition(self._h, _dptr(out_device), 1), "hgp_get_partition")
             return None
-        out = np.empty(self.n, dtype=np.int32)
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        elif out.dtype != np.int32 or out.size < self.n or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous int32 array of at least n entries")
         _check(self._lib.hgp_get_partition(self._h, _hptr(out), 0), "hgp_get_partition")
         return out
 
