@@ -185,8 +185,9 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
 // vertices, scans them into vtx_off and places the nets into inc.  Every step but the pair
 // scatter stays inside one bucket's few hundred KB, so the random accesses hit L2.
 constexpr int kTpMaxBuckets = 4096;
-constexpr int kTpMinShift = 16;          // at least 65536 vertices per bucket
-constexpr int kTpNetsPerCta = 32768;
+constexpr int kTpMinShift = 14;          // at least 16384 vertices per bucket
+constexpr int kTpSmemShift = 14;         // buckets up to this size count in shared memory
+constexpr int kTpNetsPerCta = 16384;
 
 __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P, int bshift, int32_t nb,
                                                  int32_t *bucket_cnt)
@@ -257,27 +258,36 @@ __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const in
 }
 
 // CTA per bucket: degrees, their exclusive prefix (from the bucket's first pair position) into
-// vtx_off, then the nets of the bucket's pairs into inc.  cursor: zeroed int32[n].
+// vtx_off, then the nets of the bucket's pairs into inc.  SMEM: the bucket's counters live in
+// shared memory (buckets of at most 2^kTpSmemShift vertices); otherwise in cursor (zeroed
+// int32[n], global).
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pairs, const int32_t *bucket_off,
                                                    int bshift, int32_t n, int32_t nb, int32_t *cursor,
                                                    int32_t *vtx_off, int32_t *inc)
 {
     __shared__ int32_t wt[32];
     __shared__ int32_t tot;
+    extern __shared__ int32_t sc[];
     const int32_t bkt = blockIdx.x;
     const int64_t v0 = (int64_t)bkt << bshift;
     const int64_t v1 = min((int64_t)n, v0 + ((int64_t)1 << bshift));
     const int32_t p0 = bucket_off[bkt], p1 = bucket_off[bkt + 1];
-    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) atomicAdd(&cursor[(int32_t)(pairs[i] >> 32)], 1);
+    int32_t *cnt = SMEM ? sc : cursor + v0;          // indexed by v - v0
+    if (SMEM)
+        for (int64_t i = threadIdx.x; i < v1 - v0; i += blockDim.x) sc[i] = 0;
+    __syncthreads();
+    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x)
+        atomicAdd(&cnt[(int32_t)(pairs[i] >> 32) - v0], 1);
     __syncthreads();
     int32_t carry = p0;
     for (int64_t base = v0; base < v1; base += blockDim.x) {
         const int64_t v = base + threadIdx.x;
-        const int32_t dv = v < v1 ? __ldcg(&cursor[v]) : 0;
+        const int32_t dv = v < v1 ? (SMEM ? sc[v - v0] : __ldcg(&cnt[v - v0])) : 0;
         const int32_t ex = block_exclusive_scan(dv, wt, &tot);
         if (v < v1) {
             vtx_off[v] = carry + ex;
-            cursor[v] = carry + ex;
+            cnt[v - v0] = carry + ex;
         }
         carry += tot;
     }
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pai
     __syncthreads();
     for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
         const unsigned long long pr = pairs[i];
-        const int32_t pos = atomicAdd(&cursor[(int32_t)(pr >> 32)], 1);
+        const int32_t pos = atomicAdd(&cnt[(int32_t)(pr >> 32) - v0], 1);
         inc[pos] = (int32_t)(uint32_t)pr;
     }
 }
@@ -753,7 +763,14 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         CKF(cudaMemcpyAsync(bk_cur, bk_off, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st));
         const int64_t sc = ((int64_t)m + kTpNetsPerCta - 1) / kTpNetsPerCta;
         k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, bshift, nbk, narrow_max, bk_cur, pairs); h->launches++;
-        k_tp_place<<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc); h->launches++;
+        if (bshift <= kTpSmemShift) {
+            const int smem = (int)(sizeof(int32_t) << bshift);
+            cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_tp_place<true><<<nbk, 1024, smem, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
+        } else {
+            k_tp_place<false><<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
+        }
+        h->launches++;
         CKF(cudaGetLastError());
         CKF(cudaFreeAsync(pairs, st));
         CKF(cudaFreeAsync(bk, st));
