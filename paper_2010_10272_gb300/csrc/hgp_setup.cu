@@ -178,16 +178,46 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
 }
 
 // ------------------------------------------------------------------ transpose (net -> vertex)
-// Bucketed: vertices are grouped into buckets of 2^bshift consecutive ids (at most
+// Direct form, for instances whose vertex counters fit in L2: degrees by atomic increments,
+// an exclusive scan into vtx_off, then every pin takes the next slot of its vertex (warp per
+// net) and stores the net id with the wide flag.
+constexpr int32_t kTpDirectMaxN = 1 << 21;
+
+__global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
+         j += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[pins[j]], 1);
+}
+
+__global__ void k_scatter(const int32_t *off, const int32_t *pins, int32_t m, int32_t narrow_max, int32_t *fill,
+                          int32_t *inc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
+        const int32_t b = off[e], end = off[e + 1];
+        const int32_t ef = (int32_t)((uint32_t)e | (end - b > narrow_max ? kWideFlag : 0u));
+        for (int32_t j = b + lane; j < end; j += 32) {
+            const int32_t pos = atomicAdd(&fill[pins[j]], 1);
+            inc[pos] = ef;
+        }
+    }
+}
+
+// Bucketed form, for large instances:
+// vertices are grouped into buckets of 2^bshift consecutive ids (at most
 // kTpMaxBuckets buckets).  k_tp_hist counts the pins per bucket; k_tp_scatter writes every pin
 // as a (vertex, net | wide flag) pair into its bucket's region, reserving one range per (CTA,
 // bucket) with a single global atomic; k_tp_place, a CTA per bucket, counts the degrees of its
 // vertices, scans them into vtx_off and places the nets into inc.  Every step but the pair
 // scatter stays inside one bucket's few hundred KB, so the random accesses hit L2.
 constexpr int kTpMaxBuckets = 4096;
-constexpr int kTpMinShift = 14;          // at least 16384 vertices per bucket
+constexpr int kTpShift = 14;             // 16384 vertices per bucket, unless that gives too few
+constexpr int kTpMinShift = 8;           // buckets for the GPU (small instances) or too many
 constexpr int kTpSmemShift = 14;         // buckets up to this size count in shared memory
-constexpr int kTpNetsPerCta = 16384;
+constexpr int kTpNetsPerCta = 16384;     // at most; fewer when the instance has few nets
+constexpr int kTpMinCtas = 608;          // target CTAs per launch (4 per SM)
 
 __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P, int bshift, int32_t nb,
                                                  int32_t *bucket_cnt)
@@ -202,17 +232,17 @@ __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P,
         if (h[i]) atomicAdd(&bucket_cnt[i], h[i]);
 }
 
-// CTA per kTpNetsPerCta nets; pass 0 counts its pins per bucket, then one range per bucket is
+// CTA per per_cta nets; pass 0 counts its pins per bucket, then one range per bucket is
 // reserved, pass 1 writes the pairs.  A net of at most 32 pins is walked by one lane, a larger
 // one by the whole warp.
 __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m, int bshift,
-                                                    int32_t nb, int32_t narrow_max, int32_t *bucket_cur,
-                                                    unsigned long long *pairs)
+                                                    int32_t nb, int32_t narrow_max, int32_t per_cta,
+                                                    int32_t *bucket_cur, unsigned long long *pairs)
 {
     __shared__ int32_t cur[kTpMaxBuckets];
     const int lane = threadIdx.x & 31;
-    const int64_t e_lo = (int64_t)blockIdx.x * kTpNetsPerCta;
-    const int64_t e_hi = min((int64_t)m, e_lo + kTpNetsPerCta);
+    const int64_t e_lo = (int64_t)blockIdx.x * per_cta;
+    const int64_t e_hi = min((int64_t)m, e_lo + per_cta);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
@@ -748,10 +778,20 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(dalloc(h, &vtx_off, (int64_t)n + 1));
     CKF(dalloc(h, &inc, P));
     CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
-    if (P > 0) {
-        int bshift = kTpMinShift;
-        while ((((int64_t)n + ((int64_t)1 << bshift) - 1) >> bshift) > kTpMaxBuckets) ++bshift;
-        const int32_t nbk = (int32_t)(((int64_t)n + ((int64_t)1 << bshift) - 1) >> bshift);
+    if (P > 0 && n <= kTpDirectMaxN) {
+        k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp); h->launches++;
+        CKF(scan(tmp, vtx_off, n));
+        CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, narrow_max, tmp, inc); h->launches++;
+        CKF(cudaGetLastError());
+    } else if (P > 0) {
+        auto buckets = [&](int sh) { return (((int64_t)n + ((int64_t)1 << sh) - 1) >> sh); };
+        int bshift = kTpShift;
+        while (bshift > kTpMinShift && buckets(bshift) < kTpMinCtas) --bshift;
+        while (buckets(bshift) > kTpMaxBuckets) ++bshift;
+        const int32_t nbk = (int32_t)buckets(bshift);
+        int64_t per_cta = ((int64_t)m + kTpMinCtas - 1) / kTpMinCtas;
+        per_cta = per_cta < 512 ? 512 : (per_cta > kTpNetsPerCta ? kTpNetsPerCta : per_cta);
         int32_t *bk = nullptr;           // counts [nbk + 1], offsets [nbk + 1], cursors [nbk]
         unsigned long long *pairs = nullptr;
         CKF(cudaMallocAsync(reinterpret_cast<void **>(&bk), sizeof(int32_t) * (3 * (size_t)nbk + 2), st));
@@ -761,8 +801,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt); h->launches++;
         CKF(scan(bk_cnt, bk_off, nbk));
         CKF(cudaMemcpyAsync(bk_cur, bk_off, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st));
-        const int64_t sc = ((int64_t)m + kTpNetsPerCta - 1) / kTpNetsPerCta;
-        k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, bshift, nbk, narrow_max, bk_cur, pairs); h->launches++;
+        const int64_t sc = ((int64_t)m + per_cta - 1) / per_cta;
+        k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, bshift, nbk, narrow_max, (int32_t)per_cta,
+                                                   bk_cur, pairs); h->launches++;
         if (bshift <= kTpSmemShift) {
             const int smem = (int)(sizeof(int32_t) << bshift);
             cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -69,3 +69,31 @@ def test_single_handle_graph_mode_replay():
     h.set_partition(hg.part)              # reset also restarts the device round state
     o2 = oracle.Oracle.from_hypergraph(hg, subrounds=4)
     np.testing.assert_array_equal(h.refine(2)[:, :5], o2.refine(2)[0])
+
+
+def test_launch_shapes_do_not_change_results_and_autotune_restores_state():
+    from paper_2010_10272_gb300 import HGP, Batch
+    from paper_2010_10272_gb300.autotune import tune_batch
+    members = _members()[:8]
+
+    def make():
+        return [HGP.from_hypergraph(hg, subrounds=S, phi_width=pw, seed=3) for hg, S, pw in members]
+    ref_handles = make()
+    ref = Batch(ref_handles).refine(3)
+    for g, a in [(1, 1), (3, 2), (4, 4)]:
+        hs = make()
+        got = Batch(hs, gain_ctas_per_sm=g, apply_ctas_per_sm=a).refine(3)
+        np.testing.assert_array_equal(got[:, :, :6], ref[:, :, :6])
+        for h, r in zip(hs, ref_handles):
+            np.testing.assert_array_equal(h.partition(), r.partition())
+    hs = make()
+    before = [h.export_state() for h in hs]
+    best = tune_batch(hs, rounds=2, candidates=[(0, 0), (2, 2)], repeats=1)
+    assert (best["gain_ctas_per_sm"], best["apply_ctas_per_sm"]) in best["ms"]
+    for h, s in zip(hs, before):
+        st = h.export_state()
+        np.testing.assert_array_equal(st["partition"], s["partition"])
+        assert st["next_round"] == s["next_round"] and st["first_round"] == s["first_round"]
+    # refining after tuning equals refining a fresh set
+    got = Batch(hs).refine(3)
+    np.testing.assert_array_equal(got[:, :, :6], ref[:, :, :6])
