@@ -65,7 +65,9 @@ typedef struct {
     uint64_t seed;       /* sub-round hash seed [0] */
     int32_t debug;       /* bit 0 (check mode): hgp_refine recomputes the objective from the
                             Phi table after the call and returns HGP_ERR_INTERNAL if it differs
-                            from the incrementally maintained one [0] */
+                            from the incrementally maintained one; bit 1: build the vertex ->
+                            nets lists with the bucketed transpose whatever the size (it is
+                            otherwise used above 2^21 vertices) [0] */
     int32_t graph;       /* 1: hgp_refine captures its launches as a CUDA graph on the first call
                             with a given round count and replays it afterwards [0]; ignored
                             while profiling is on */

@@ -778,7 +778,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(dalloc(h, &vtx_off, (int64_t)n + 1));
     CKF(dalloc(h, &inc, P));
     CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
-    if (P > 0 && n <= kTpDirectMaxN) {
+    if (P > 0 && n <= kTpDirectMaxN && !(o.debug & 2)) {
         k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp); h->launches++;
         CKF(scan(tmp, vtx_off, n));
         CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));

@@ -338,3 +338,40 @@ def test_exact_gains_of_lp_moves_sum_to_objective_change():
     st = h.refine(1)
     o0 = oracle.Oracle.from_hypergraph(hg, subrounds=1)
     assert o0.objective() - st[0, 0] == g.sum()
+
+
+# ---------------------------------------------------------------- creation paths
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[7], CASES[9]],
+                         ids=["k2", "k16-w2", "k64", "wide"])
+def test_bucketed_transpose_forced(case):
+    """The bucketed net -> vertex transpose (used above 2^21 vertices) forced at small sizes
+    (down to 256-vertex buckets): same rounds, Phi and partition as the oracle."""
+    seed, n, m, k, max_size, weighted, S, w = case
+    hg = synth.random_small(seed, n, m, k, max_size=max_size, weighted=weighted, rounds=4)
+    h = HGP.from_hypergraph(hg, subrounds=S, seed=seed, phi_width=w, debug=2)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=seed)
+    compare_state(h, o)
+    np.testing.assert_array_equal(h.refine(4)[:, :5], o.refine(4)[0])
+    compare_state(h, o)
+
+
+def test_bucketed_transpose_degenerate():
+    # empty nets, single-pin nets, isolated vertices, a vertex in every net
+    n, m = 3000, 2000
+    rng = np.random.default_rng(5)
+    nets = []
+    for e in range(m):
+        s = int(rng.integers(0, 6))
+        pins = set(rng.choice(n - 100, size=s, replace=False).tolist()) if s else set()
+        if e % 3 == 0:
+            pins.add(n - 101)                        # the hub
+        nets.append(sorted(pins))
+    off = np.zeros(m + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in nets])
+    pins = np.array([v for x in nets for v in x], np.int32)
+    part = rng.integers(0, 4, size=n).astype(np.int32)
+    h = HGP(n, m, off, pins, 4, 0.1, part, subrounds=2, debug=2)
+    o = oracle.Oracle(n, m, off, pins, 4, 0.1, part, None, None, 2, 0)
+    compare_state(h, o)
+    np.testing.assert_array_equal(h.refine(3)[:, :5], o.refine(3)[0])
+    compare_state(h, o)
