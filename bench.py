@@ -174,13 +174,17 @@ def algorithmic_bytes(hg, info, stats, S):
     return {"gain": gain_total / launches, "apply": apply_total / launches}
 
 
-def traffic_from_profile(kernel: str, workload: str):
+def traffic_from_profile(kernel: str, workload: str, phi_width: int):
     """dram bytes per launch recorded in profiles/ for `kernel` on `workload`, if the kernel
-    source has not changed since the capture (its sha256 is stored with the figure)."""
+    source has not changed since the capture (its sha256 is stored with the figure) and the
+    capture used the same Phi entry width."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
+    pw = re.search(r"phi_width:\s*(\d+)", text)
+    if not pw or int(pw.group(1)) != phi_width:
+        return None
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
@@ -343,7 +347,7 @@ def run_gpu(args, world, rank, local):
     kname = {"gain": "k_gain", "apply": "k_apply"}[kern]
     avg_ms = prof[kern][0] / max(1, prof[kern][1])
     achieved = algo[kern] / (avg_ms / 1e3) / 1e9
-    traffic = traffic_from_profile(kname, args.workload)
+    traffic = traffic_from_profile(kname, args.workload, info["phi_width"])
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": traffic, "algorithmic_bytes_per_launch": algo[kern],

@@ -59,9 +59,10 @@ typedef struct hgp_batch hgp_batch;
 /* Options.  Zero-initialised fields select the defaults given in brackets. */
 typedef struct {
     int32_t subrounds;   /* S, 1..64 [4] */
-    int32_t phi_width;   /* bytes per Phi entry: 1, 2 or 4; 0 = auto [0]: 1 if every net has
-                            at most 255 pins, else 2.  Nets larger than the width can count
-                            (255 or 65535 pins) keep 4-byte rows in a separate wide table. */
+    int32_t phi_width;   /* bytes per Phi entry: 1, 2 or 4; 0 = auto [0]: 1 unless more than
+                            1/64 of the nets have more than 255 pins, else 2.  Nets larger than
+                            the width can count (255 or 65535 pins) keep 4-byte rows in a
+                            separate wide table. */
     uint64_t seed;       /* sub-round hash seed [0] */
     int32_t debug;       /* bit 0 (check mode): hgp_refine recomputes the objective from the
                             Phi table after the call and returns HGP_ERR_INTERNAL if it differs

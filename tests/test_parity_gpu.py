@@ -86,9 +86,20 @@ def test_powerlaw_scaled_with_wide_tier():
 
 def test_powerlaw_scaled_u16():
     hg = synth.config_powerlaw(scale=0.004)
-    h, _, stats = run_both(hg, S=4, check_phi=False)
+    h, _, stats = run_both(hg, S=4, phi_width=2, check_phi=False)
     assert h.info()["phi_width"] == 2
     assert stats[0, 2] > 0
+
+
+def test_phi_width_auto_choice():
+    # few nets above 255 pins: 1-byte entries with those nets in the wide table
+    hg = synth.config_powerlaw(scale=0.004)
+    h, _, _ = run_both(hg, S=4, check_phi=False)
+    assert h.info()["phi_width"] == 1 and h.info()["wide_nets"] > 0
+    # many nets above 255 pins: 2-byte entries
+    hg2 = synth.random_small(77, 3000, 400, 4, max_size=600)
+    h2, _, _ = run_both(hg2, S=2)
+    assert h2.info()["phi_width"] == 2
 
 
 # ---------------------------------------------------------------- approval edge cases
