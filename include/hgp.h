@@ -59,10 +59,9 @@ typedef struct hgp_batch hgp_batch;
 /* Options.  Zero-initialised fields select the defaults given in brackets. */
 typedef struct {
     int32_t subrounds;   /* S, 1..64 [4] */
-    int32_t phi_width;   /* bytes per Phi entry: 1, 2 or 4; 0 = auto [0]: 1 unless more than
-                            1/64 of the nets have more than 255 pins, else 2.  Nets larger than
-                            the width can count (255 or 65535 pins) keep 4-byte rows in a
-                            separate wide table. */
+    int32_t phi_width;   /* bytes per Phi entry: 1, 2 or 4; 0 = auto [0]: 1 if every net has
+                            at most 255 pins, else 2.  Nets larger than the width can count
+                            (255 or 65535 pins) keep 4-byte rows in a separate wide table. */
     uint64_t seed;       /* sub-round hash seed [0] */
     int32_t debug;       /* bit 0 (check mode): hgp_refine recomputes the objective from the
                             Phi table after the call and returns HGP_ERR_INTERNAL if it differs
@@ -83,6 +82,9 @@ typedef struct {
                                 counts as a move for eligibility.  Adds a table of 32 * 2^ceil(
                                 log2(2P)) bytes and n bytes.  Single handles only (a batch
                                 rejects it) [0] */
+    int32_t gain_ctas_per_sm;   /* persistent grid of the gain kernel, CTAs per SM; 0 = occupancy
+                                   [0].  Results do not depend on it. */
+    int32_t apply_ctas_per_sm;  /* the same for the apply kernel [0] */
 } hgp_options;
 
 /* Per-round statistics written by hgp_refine. */
@@ -279,6 +281,13 @@ int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_offsets, con
                            const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
                            const int32_t *part, int32_t subrounds, uint64_t seed, int32_t s,
                            int32_t *target, int64_t *gain, void *cuda_stream);
+
+/*
+ * Sets the persistent grids of the handle's gain and apply kernels (CTAs per SM; 0 = derived
+ * from occupancy), as the options of the same names do at creation.  Results never depend on
+ * them.  Waits for the handle's stream; drops a captured CUDA graph.
+ */
+int hgp_set_launch_shape(hgp_handle *h, int32_t gain_ctas_per_sm, int32_t apply_ctas_per_sm);
 
 /*
  * Rebalancing (paper Sec. 8), in a synchronous form.  Runs passes while a block is heavier

@@ -35,6 +35,8 @@ struct hgp_handle {
     int64_t launches = 0;
     int grid_gain = 0;            // persistent grid sizes (CTAs), set at first launch
     int grid_apply = 0;
+    int32_t gain_ctas = 0;        // per-SM CTA overrides of those grids (0: occupancy)
+    int32_t apply_ctas = 0;
     bool profiling = false;
     double prof_ms[HGP_PHASES] = {};
     int64_t prof_launches[HGP_PHASES] = {};

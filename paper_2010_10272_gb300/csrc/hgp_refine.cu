@@ -1803,6 +1803,18 @@ cudaError_t sync_dev(hgp_handle *h)
     return e;
 }
 
+// persistent grid of ctas_per_sm CTAs per SM (at most one warp per range item), or `fallback`
+int grid_override(int device, int ctas_per_sm, int fallback, int32_t n_ranges)
+{
+    if (ctas_per_sm <= 0) return fallback;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int64_t g = (int64_t)sms * ctas_per_sm;
+    const int64_t need = (n_ranges + kWarps - 1) / kWarps;
+    if (g > need) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
 Plan single_plan(hgp_handle *h)
 {
     Plan p;
@@ -1819,8 +1831,8 @@ Plan single_plan(hgp_handle *h)
     if (!h->grid_gain) {
         Plan q = p;
         set_grids(q, h->device);
-        h->grid_gain = q.grid_gain;
-        h->grid_apply = q.grid_apply;
+        h->grid_gain = grid_override(h->device, h->gain_ctas, q.grid_gain, p.n_ranges);
+        h->grid_apply = grid_override(h->device, h->apply_ctas, q.grid_apply, p.n_ranges);
     }
     p.grid_gain = h->grid_gain;
     p.grid_apply = h->grid_apply;
@@ -2011,6 +2023,27 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 
 }  // namespace hgp
 
+// ================================================================== launch shape
+extern "C" int hgp_set_launch_shape(hgp_handle *h, int32_t gain_ctas_per_sm, int32_t apply_ctas_per_sm)
+{
+    if (!h || gain_ctas_per_sm < 0 || apply_ctas_per_sm < 0) return HGP_ERR_INVALID;
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    h->gain_ctas = gain_ctas_per_sm;
+    h->apply_ctas = apply_ctas_per_sm;
+    h->grid_gain = 0;   // recomputed at the next launch
+    h->grid_apply = 0;
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_rounds = 0;
+    }
+    return HGP_OK;
+}
+
 // ================================================================== rebalancing (Sec. 8)
 namespace {
 
@@ -2157,17 +2190,6 @@ void free_groups(hgp_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->graph_rounds = 0;
-}
-
-int grid_override(int device, int ctas_per_sm, int fallback, int32_t n_ranges)
-{
-    if (ctas_per_sm <= 0) return fallback;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    int64_t g = (int64_t)sms * ctas_per_sm;
-    const int64_t need = (n_ranges + kWarps - 1) / kWarps;
-    if (g > need) g = need;
-    return (int)(g < 1 ? 1 : g);
 }
 
 // (re)builds the per-group device arrays for a stats capacity of `cap` rounds

@@ -330,16 +330,6 @@ __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pai
     }
 }
 
-// number of nets with more than `limit` pins
-__global__ void k_count_large(const int32_t *off, int32_t m, int32_t limit, int32_t *count)
-{
-    int32_t c = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        c += off[e + 1] - off[e] > limit;
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
 __global__ void k_wide_flags(const int32_t *off, int32_t m, int32_t narrow_max, int32_t *flags)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
@@ -681,6 +671,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     h->seed = o.seed;
     h->debug = o.debug;
+    if (o.gain_ctas_per_sm < 0 || o.apply_ctas_per_sm < 0) return fail(HGP_ERR_INVALID);
+    h->gain_ctas = o.gain_ctas_per_sm;
+    h->apply_ctas = o.apply_ctas_per_sm;
     h->graph = o.graph;
     d.n = n;
     d.m = m;
@@ -745,22 +738,10 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     const int32_t max_size = host_err[1];
 
-    // ---- Phi width: 1-byte entries unless more than 1/64 of the nets have more than 255 pins
-    // (those rows go to the int32 wide table), else 2 bytes; narrower rows put Phi(e, a) and
-    // Phi(e, t) of a move into fewer sectors
+    // ---- Phi width chosen by the largest net: 1 byte if every net fits, else 2 bytes; nets
+    // beyond the entry's range keep int32 rows in the wide table
     int w = o.phi_width;
-    if (w == 0) {
-        w = 1;
-        if (max_size > 255) {
-            int32_t *cnt_d = misc32 + 4, large = 0;
-            CKF(cudaMemsetAsync(cnt_d, 0, sizeof(int32_t), st));
-            k_count_large<<<grid_for(m, 256), 256, 0, st>>>(net_off, m, 255, cnt_d); h->launches++;
-            CKF(cudaGetLastError());
-            CKF(cudaMemcpyAsync(&large, cnt_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            CKF(cudaStreamSynchronize(st));
-            if ((int64_t)large * 64 > (int64_t)m) w = 2;
-        }
-    }
+    if (w == 0) w = max_size <= 255 ? 1 : 2;
     d.phi_w = w;
     const int32_t narrow_max = w == 1 ? 255 : (w == 2 ? 65535 : 0x7fffffff);
 

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
     _fields_ = [("subrounds", ctypes.c_int32), ("phi_width", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("debug", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("balance_moves", ctypes.c_int32),
-                ("revert_negative", ctypes.c_int32)]
+                ("revert_negative", ctypes.c_int32), ("gain_ctas_per_sm", ctypes.c_int32),
+                ("apply_ctas_per_sm", ctypes.c_int32)]
 
 
 class BatchOptions(ctypes.Structure):
@@ -88,6 +89,7 @@ def load_library():
         lib.hgp_debug_candidates.argtypes = [P, i32, P, P]
         lib.hgp_exact_gains.argtypes = [P, i32, P, P]
         lib.hgp_rebalance.argtypes = [P, i32, P, P, P]
+        lib.hgp_set_launch_shape.argtypes = [P, i32, i32]
         lib.hgp_contract.argtypes = [i32, i32, P, P, P, P, P, P, P]
         lib.hgp_coarse_get_sizes.argtypes = [P, P, P, P]
         lib.hgp_coarse_get_device_arrays.argtypes = [P, P, P, P, P, P]
@@ -183,13 +185,14 @@ class HGP:
     def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None, *,
                  subrounds: int = 4, seed: int = 0, phi_width: int = 0, debug: int = 0,
                  graph: int = 0, stream=None, device: bool = False, balance_moves: bool = False,
-                 revert_negative: bool = False):
+                 revert_negative: bool = False, gain_ctas_per_sm: int = 0, apply_ctas_per_sm: int = 0):
         self._lib = load_library()
         self._h = ctypes.c_void_p()
         o = default_options()
         o.subrounds, o.phi_width, o.seed = int(subrounds), int(phi_width), int(seed)
         o.debug, o.graph = int(debug), int(graph)
         o.balance_moves, o.revert_negative = int(bool(balance_moves)), int(bool(revert_negative))
+        o.gain_ctas_per_sm, o.apply_ctas_per_sm = int(gain_ctas_per_sm), int(apply_ctas_per_sm)
         sh = _stream_handle(stream)
         o.cuda_stream = ctypes.c_void_p(sh) if sh else None
         self.n, self.m, self.k = int(n), int(m), int(k)
@@ -299,6 +302,10 @@ class HGP:
         _check(self._lib.hgp_debug_candidates(self._h, int(s), _hptr(t), _hptr(g)),
                "hgp_debug_candidates")
         return t, g
+
+    def set_launch_shape(self, gain_ctas_per_sm: int = 0, apply_ctas_per_sm: int = 0):
+        _check(self._lib.hgp_set_launch_shape(self._h, int(gain_ctas_per_sm), int(apply_ctas_per_sm)),
+               "hgp_set_launch_shape")
 
     def rebalance(self, max_passes: int):
         """Rebalancing passes (Sec. 8); returns (stats [passes x 7] int64 (STAT_FIELDS),

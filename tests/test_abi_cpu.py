@@ -54,10 +54,11 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "hgp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hgp_options), offsetof(hgp_options, phi_width),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hgp_options), offsetof(hgp_options, phi_width),
          offsetof(hgp_options, seed), offsetof(hgp_options, debug), offsetof(hgp_options, graph),
          offsetof(hgp_options, cuda_stream), offsetof(hgp_options, balance_moves),
-         offsetof(hgp_options, revert_negative), sizeof(hgp_round_stats), sizeof(hgp_profile),
+         offsetof(hgp_options, revert_negative), offsetof(hgp_options, gain_ctas_per_sm),
+         offsetof(hgp_options, apply_ctas_per_sm), sizeof(hgp_round_stats), sizeof(hgp_profile),
          offsetof(hgp_profile, launches));
   return 0;
 }
@@ -70,8 +71,9 @@ int main(void) {
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(Options), Options.phi_width.offset, Options.seed.offset,
             Options.debug.offset, Options.graph.offset, Options.cuda_stream.offset,
-            Options.balance_moves.offset, Options.revert_negative.offset, ctypes.sizeof(RoundStats),
-            ctypes.sizeof(Profile), Profile.launches.offset]
+            Options.balance_moves.offset, Options.revert_negative.offset, Options.gain_ctas_per_sm.offset,
+            Options.apply_ctas_per_sm.offset, ctypes.sizeof(RoundStats), ctypes.sizeof(Profile),
+            Profile.launches.offset]
     assert vals == want
 
 

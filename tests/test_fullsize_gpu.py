@@ -72,7 +72,7 @@ def test_powerlaw_full_sampled_and_properties():
     assert hg.n == 50_000_000 and hg.k == 64
     h = _device_handle(hg)
     info = h.info()
-    assert info["lmax"] == 804_687 and info["phi_width"] == 1 and info["wide_nets"] > 0
+    assert info["lmax"] == 804_687 and info["phi_width"] == 2 and info["wide_nets"] > 0
     # (a) round 0, sub-round 0: sampled candidates against the oracle's sample routine
     rng = np.random.default_rng(2024)
     sample = np.sort(rng.choice(hg.n, size=20_000, replace=False)).astype(np.int32)

@@ -7,7 +7,7 @@ No expected value here comes from the oracle itself or from the CUDA library:
 * brute force on tiny inputs (objective from connectivity sets, gains as objective
   differences, eligibility from neighbourhoods), see tests/brute.py;
 * invariants (sum of Phi over blocks = |e|, block weights sum to c(V), balance);
-* exhaustive optimal bipartitions of hypergraphs with at most 10 vertices.
+* exhaustive optimal bipartitions of hypergraphs with at most 12 vertices.
 """
 import itertools
 
@@ -204,7 +204,7 @@ def _optimum(t: Tiny):
 
 
 @pytest.mark.parametrize("seed,n,k", [(0, 10, 2), (1, 10, 2), (2, 9, 2), (3, 8, 3),
-                                      (4, 10, 2), (5, 7, 3)])
+                                      (4, 10, 2), (5, 7, 3), (6, 12, 2), (7, 12, 2), (8, 11, 2)])
 def test_exhaustive_optimum(seed, n, k):
     rng = np.random.default_rng(500 + seed)
     t = random_tiny(rng, n, n + 2, k, max_size=4, weighted=seed % 2 == 1, eps=0.25)

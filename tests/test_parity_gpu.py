@@ -91,15 +91,14 @@ def test_powerlaw_scaled_u16():
     assert stats[0, 2] > 0
 
 
-def test_phi_width_auto_choice():
-    # few nets above 255 pins: 1-byte entries with those nets in the wide table
+def test_phi_width_choices():
+    # automatic: chosen by the largest net (2 bytes here); forced 1 byte: the nets above 255
+    # pins go to the wide table; both give the oracle's rounds
     hg = synth.config_powerlaw(scale=0.004)
     h, _, _ = run_both(hg, S=4, check_phi=False)
-    assert h.info()["phi_width"] == 1 and h.info()["wide_nets"] > 0
-    # many nets above 255 pins: 2-byte entries
-    hg2 = synth.random_small(77, 3000, 400, 4, max_size=600)
-    h2, _, _ = run_both(hg2, S=2)
-    assert h2.info()["phi_width"] == 2
+    assert h.info()["phi_width"] == 2
+    h1, _, _ = run_both(hg, S=4, phi_width=1, check_phi=False)
+    assert h1.info()["phi_width"] == 1 and h1.info()["wide_nets"] > h.info()["wide_nets"]
 
 
 # ---------------------------------------------------------------- approval edge cases
@@ -386,3 +385,27 @@ def test_bucketed_transpose_degenerate():
     compare_state(h, o)
     np.testing.assert_array_equal(h.refine(3)[:, :5], o.refine(3)[0])
     compare_state(h, o)
+
+
+def test_launch_shape_and_instance_autotune():
+    """Launch shapes never change results; the instance tuner returns one of its candidates,
+    and a handle created with the tuned choices matches the oracle."""
+    from paper_2010_10272_gb300.autotune import tune_instance
+    hg = synth.random_small(91, 20000, 18000, 16, max_size=300, weighted=True, rounds=3)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4, seed=1)
+    want, _ = o.refine(3)
+    for g, a in [(1, 1), (2, 3), (4, 4)]:
+        h = HGP.from_hypergraph(hg, subrounds=4, seed=1, gain_ctas_per_sm=g, apply_ctas_per_sm=a)
+        np.testing.assert_array_equal(h.refine(3)[:, :5], want)
+    h = HGP.from_hypergraph(hg, subrounds=4, seed=1)
+    h.refine(1)
+    h.set_launch_shape(3, 1)
+    np.testing.assert_array_equal(h.refine(2)[:, :5], want[1:])
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    best = tune_instance(hg.n, hg.m, dev(hg.net_off), dev(hg.pins), hg.k, hg.eps, dev(hg.part),
+                         dev(hg.vertex_w), dev(hg.net_w), rounds=2, shapes=[(0, 0), (2, 2)], repeats=1,
+                         seed=1)
+    assert best["phi_width"] in (1, 2) and (best["gain_ctas_per_sm"], best["apply_ctas_per_sm"]) in [(0, 0), (2, 2)]
+    ht = HGP.from_hypergraph(hg, subrounds=4, seed=1, phi_width=best["phi_width"],
+                             gain_ctas_per_sm=best["gain_ctas_per_sm"], apply_ctas_per_sm=best["apply_ctas_per_sm"])
+    np.testing.assert_array_equal(ht.refine(3)[:, :5], want)
