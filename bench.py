@@ -352,6 +352,16 @@ def run_gpu(args, world, rank, local):
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                 "traffic": traffic, "algorithmic_bytes_per_launch": algo[kern],
                 "avg_launch_ms": avg_ms}
+    # DRAM bytes actually moved by the gain and update kernels together (ncu dram__bytes of one
+    # launch each, from profiles/) over their live average launch times
+    t_gain = traffic_from_profile("k_gain", args.workload, info["phi_width"])
+    t_apply = traffic_from_profile("k_apply", args.workload, info["phi_width"])
+    if t_gain and t_apply:
+        ms_g = prof["gain"][0] / max(1, prof["gain"][1])
+        ms_a = prof["apply"][0] / max(1, prof["apply"][1])
+        gbs = (t_gain + t_apply) / ((ms_g + ms_a) / 1e3) / 1e9
+        roofline["dram_gain_plus_update"] = {"achieved_gbs": gbs, "frac": gbs / peak,
+                                             "source": "ncu dram__bytes per launch (profiles/) / live launch time"}
     # second roofline: the gain step is bound by random record gathers (one per incidence of an
     # active vertex), compared with the device's measured random 32-byte gather rate
     from paper_2010_10272_gb300.native import probe_gather

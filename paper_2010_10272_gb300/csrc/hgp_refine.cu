@@ -531,6 +531,12 @@ __device__ __forceinline__ int32_t gain_range(const Dev &d, int32_t range, int32
                     atomicAdd(&tot[t_best], (unsigned long long)cu);
                 }
             }
+            if (!RB && t_best >= 0) {
+                // level-0 histogram of the approval step: candidate weight by target block and
+                // gain bin (no return value: a reduction in L2)
+                const int bin = g_best < kBins - 1 ? g_best : kBins - 1;
+                atomicAdd(&d.hist[(int64_t)t_best * kBins + bin], (unsigned long long)cu);
+            }
             nout += __popc(cm);
             __syncwarp();
         }
@@ -826,6 +832,12 @@ __global__ void __launch_bounds__(kThreads) k_select(const Dev *devs, const int2
         const long long tot = d.tot[t];
         cap = stage_cap<KEY>(d, t);
         if (tot == 0 || tot <= cap) {
+            if (KEY == KEY_T) {
+                // the gain step filled the level-0 row of every target block
+                unsigned long long *row0 = d.hist + (int64_t)t * kBins;
+                if (tot)
+                    for (int b = tid; b < kBins; b += kThreads) row0[b] = 0;
+            }
             if (tid == 0) {
                 Sel o;
                 o.mode = SEL_ALL; o.level = 0; o.g = 0; o.rem = 0;
@@ -1734,9 +1746,9 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         if (e == cudaSuccess) e = phase_begin(p.prof);
         if (e != cudaSuccess) break;
         int32_t n = 0;
-        k_hist<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, 0);
+        // the level-0 histogram was filled by the gain step
         k_select<<<p.n_blocks, kThreads, 0, p.st>>>(p.devs, p.blocks, p.n_blocks, 0);
-        n += 2;
+        n += 1;
         if (p.levels) {
             for (int level = 1; level <= 3; ++level) {
                 k_hist<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.devs, p.ranges, p.n_ranges, level);
@@ -2004,6 +2016,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     if (e == cudaSuccess) e = cudaMemsetAsync(d.wq, 0, sizeof(int32_t) * kWqPerRow, st);
     if (e == cudaSuccess) e = launch_gain(p, s, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tot, 0, sizeof(int64_t) * 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.hist, 0, sizeof(unsigned long long) * (size_t)d.k * kBins, st);
     if (e == cudaSuccess) {
         k_expand_candidates<<<(d.n_ranges * 32 + 255) / 256, 256, 0, st>>>(h->d_dev, t_d, g_d);
         h->launches++;
