@@ -615,11 +615,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
     int32_t nelig = 0, ncand = 0;
     int inst_prev = -1;
     const int32_t n_it = B ? n_items : d0.n_ranges;
-    int32_t *wq = B ? nullptr : d0.wq + ((int64_t)rr * 64 + s) * 2;
+    int32_t *wq = d0.wq + ((int64_t)rr * 64 + s) * 2;
     int32_t next_raw = 0;
-    for (int32_t item = B ? blockIdx.x * kWarps + wid : take_item(wq); item < n_it;
-         item = B ? item + gridDim.x * kWarps : __shfl_sync(kFull, next_raw, 0)) {
-        if (!B) next_raw = take_item_early(wq);
+    for (int32_t item = take_item(wq); item < n_it; item = __shfl_sync(kFull, next_raw, 0)) {
+        next_raw = take_item_early(wq);
         if (B) {
             const int2 it = items[item];
             if (it.x != inst_prev) {
@@ -2180,6 +2179,7 @@ struct hgp_batch {
         std::vector<int32_t> members;           // indices into hs
         Dev *d_devs = nullptr;
         int2 *d_items = nullptr;                // ranges, then tiles, then blocks
+        int32_t *d_wq = nullptr;                // gain-step work counters [stats_cap * kWqPerRow]
     } g[2];
     int64_t *d_stats = nullptr;
     int64_t *h_stats = nullptr;
@@ -2197,8 +2197,10 @@ void free_groups(hgp_batch *b)
     for (auto &gr : b->g) {
         if (gr.d_devs) cudaFree(gr.d_devs);
         if (gr.d_items) cudaFree(gr.d_items);
+        if (gr.d_wq) cudaFree(gr.d_wq);
         gr.d_devs = nullptr;
         gr.d_items = nullptr;
+        gr.d_wq = nullptr;
     }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -2246,6 +2248,7 @@ int build_groups(hgp_batch *b, int32_t cap)
         const size_t n_items = ranges.size() + tiles.size() + blocks.size();
         e = cudaMalloc(reinterpret_cast<void **>(&gr.d_devs), sizeof(Dev) * devs.size());
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&gr.d_items), sizeof(int2) * n_items);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&gr.d_wq), sizeof(int32_t) * kWqPerRow * (size_t)cap);
         std::vector<int2> all;
         all.reserve(n_items);
         all.insert(all.end(), ranges.begin(), ranges.end());
@@ -2258,6 +2261,7 @@ int build_groups(hgp_batch *b, int32_t cap)
             return status_of(e);
         }
         Plan &p = gr.plan;
+        p.d0.wq = gr.d_wq;   // the batch kernels read only the work counters from d0
         p.devs = gr.d_devs;
         p.ranges = gr.d_items;
         p.tiles = gr.d_items + ranges.size();
@@ -2287,7 +2291,8 @@ cudaError_t enqueue_batch(hgp_batch *b, int32_t rounds, int64_t *launch_counter)
             if (gr.members.empty() || e != cudaSuccess) continue;
             Plan p = gr.plan;
             p.launches = launch_counter;
-            e = launch_round(p, rr);
+            if (rr == 0) e = cudaMemsetAsync(p.d0.wq, 0, sizeof(int32_t) * kWqPerRow * (size_t)rounds, b->stream);
+            if (e == cudaSuccess) e = launch_round(p, rr);
         }
     return e;
 }
