@@ -80,7 +80,7 @@ typedef struct {
                                 ascending vertex id (computed by Lemma 1, Sec. 5.4); after the
                                 sub-round every move with a negative one is undone, and still
                                 counts as a move for eligibility.  Adds a table of 32 * 2^ceil(
-                                log2(2P)) bytes and n bytes.  Single handles only (a batch
+                                log2(2P)) bytes, n bytes and 4 m bytes.  Single handles only (a batch
                                 rejects it) [0] */
     int32_t gain_ctas_per_sm;   /* persistent grid of the gain kernel, CTAs per SM; 0 = occupancy
                                    [0].  Results do not depend on it. */

@@ -109,7 +109,9 @@ struct Dev {
                             // | 0x80 when it is to be undone; 0xFF when not approved
     void *rv_tab;           // hash table of (net, block) order statistics of the sub-round's moves
     int64_t rv_cap;         // its capacity in slots (a power of two >= 2 P)
-    unsigned long long *rv_cnt;  // [1] incidences of the vertices moved in the current sub-round
+    unsigned long long *rv_cnt;  // [2] incidences of the vertices moved in the current sub-round,
+                                 // and those of them on nets with several movers
+    int32_t *rv_net;        // [m] movers of each net in the current sub-round
 };
 
 __device__ __forceinline__ int lam_bits_ctz(uint32_t x) { return __ffs(x) - 1; }

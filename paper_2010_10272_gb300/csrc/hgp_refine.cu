@@ -997,9 +997,12 @@ struct alignas(16) ApplyWarp {
 // result is used, so their latencies overlap.
 constexpr int kPins = 4;
 
-template <typename Rec, bool STAMP = true>
+// RVC (LP apply with the revert variant on): also counts the movers of every net (d.rv_net)
+// and, in `shared`, the moved incidences on nets with several movers (a second mover adds its
+// own incidence and the first one's, later movers their own).
+template <typename Rec, bool STAMP = true, bool RVC = false>
 __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const ApplyWarp &w_,
-                                                int32_t i0, int32_t total, int32_t r)
+                                                int32_t i0, int32_t total, int32_t r, int32_t *shared = nullptr)
 {
     typedef typename RecIO<Rec>::Lam Lam;
     int32_t e[kPins], a[kPins], t[kPins], oa[kPins], ot[kPins], w[kPins], mv[kPins];
@@ -1027,6 +1030,10 @@ __device__ __forceinline__ long long apply_pins(const Dev &d, Rec *recs, const A
         w[q] = __ldg(&rc->w) & 0x7fffffff;
         oa[q] = phi_add(d, ee, a[q], -1, wide, wrow);
         ot[q] = phi_add(d, ee, t[q], +1, wide, wrow);
+        if (RVC && d.rv_net) {
+            const int32_t before = atomicAdd(&d.rv_net[ee], 1);
+            *shared += before == 1 ? 2 : (before >= 2 ? 1 : 0);
+        }
     }
     long long dobj = 0;
 #pragma unroll
@@ -1163,7 +1170,7 @@ template <typename Rec, int KEY>
 __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t r, bool any_thr,
                                             const ApplyInst &ai, unsigned long long *run,
                                             unsigned long long *bwd, ApplyWarp &w_, long long &idobj,
-                                            int32_t &iappr, int32_t &ipins)
+                                            int32_t &iappr, int32_t &ipins, int32_t &ishared)
 {
     const int lane = threadIdx.x & 31;
     Rec *recs = reinterpret_cast<Rec *>(d.rec);
@@ -1204,7 +1211,7 @@ __device__ __forceinline__ void apply_range(const Dev &d, int32_t range, int32_t
         if (lane == 31) w_.off[32] = total;
         __syncwarp();
         for (int32_t i0 = 0; i0 < total; i0 += 32 * kPins)
-            idobj += apply_pins<Rec, KEY == KEY_T>(d, recs, w_, i0 + lane, total, r);
+            idobj += apply_pins<Rec, KEY == KEY_T, KEY == KEY_T>(d, recs, w_, i0 + lane, total, r, &ishared);
         __syncwarp();
     }
 }
@@ -1228,7 +1235,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
     bwd_w[wid][lane] = 0;
     bwd_w[wid][lane + 32] = 0;
     long long dobj = 0;
-    int32_t nappr = 0, npins = 0, r = 0;
+    int32_t nappr = 0, npins = 0, r = 0, nshared = 0;
     int inst_prev = -1;
     bool any_thr = false;
     const int32_t n_it = B ? n_items : d0.n_ranges;
@@ -1237,7 +1244,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
     (void)sub;
     for (int32_t item = blockIdx.x * kWarps + wid; item < n_it; item += gridDim.x * kWarps) {
         long long idobj = 0;
-        int32_t iappr = 0, ipins = 0;
+        int32_t iappr = 0, ipins = 0, ishared = 0;
         if (B) {
             const int2 it = items[item];
             if (it.x != inst_prev) {
@@ -1246,7 +1253,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 inst_prev = it.x;
             }
             const Dev &d = dsm[wid];
-            apply_range<Rec, KEY>(d, it.y, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            apply_range<Rec, KEY>(d, it.y, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins,
+                                  ishared);
             for (int o = 16; o; o >>= 1) {
                 idobj += __shfl_xor_sync(kFull, idobj, o);
                 iappr += __shfl_xor_sync(kFull, iappr, o);
@@ -1273,11 +1281,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
                 any_thr = apply_refresh(d0, ai_w[wid], r);
                 inst_prev = 0;
             }
-            apply_range<Rec, KEY>(d0, item, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins);
+            apply_range<Rec, KEY>(d0, item, r, any_thr, ai_w[wid], run[wid], bwd_w[wid], aw[wid], idobj, iappr, ipins,
+                                  ishared);
             dobj += idobj;
             nappr += iappr;
             npins += ipins;
+            nshared += ishared;
         }
+    }
+    if (!B && KEY == KEY_T && d0.rv_cnt) {
+        // revert variant: moved incidences on nets with several movers (sizes the order-statistics table)
+        nshared = __reduce_add_sync(kFull, nshared);
+        if (lane == 0 && nshared) atomicAdd(d0.rv_cnt + 1, (unsigned long long)nshared);
     }
     if (!B) {
         // as in k_gain: partial sums into warp 0's slots, the last warp to finish flushes
@@ -1331,10 +1346,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
 //     +omega(e)  iff  Psi(e, a) = 0, u = max out(e, a), min in(e, a) > u
 //     -omega(e)  iff  Psi(e, b) = 0, u = min in(e, b),  max out(e, b) < u
 // where Psi(e, i) is the number of pins of e that were in block i at the start of the sub-round
-// and stayed: Phi(e, i) after the moves minus |in(e, i)|.  Pass 1 records max out, min in and
-// |in| per touched (e, i) in an open-addressing table sized to the sub-round's moved
-// incidences; pass 2 sums the terms per move and marks the moves whose sum is negative; the
-// revert step moves those back (Sec. 6).  Balance holds after it: each block's approval was
+// and stayed: Phi(e, i) after the moves minus |in(e, i)|.  Most touched nets have one mover in
+// a sub-round; for them the two conditions reduce to Phi(e, a) = 0 and Phi(e, b) = 1 after the
+// move.  The apply step counts the movers of every net and the moved incidences of nets with
+// several movers; INSERT records max out, min in and |in| of those nets' (e, i) in an
+// open-addressing table sized to that count, EVAL sums the terms per move and marks the moves
+// whose sum is negative, and the revert step moves those back (Sec. 6).  Balance holds after it: each block's approval was
 // checked against its weight at the start of the sub-round, without credit for departures.
 struct alignas(16) RvSlot {
     unsigned long long key;   // e * 64 + i, kRvEmpty when free
@@ -1346,11 +1363,11 @@ struct alignas(16) RvSlot {
 static_assert(sizeof(RvSlot) == kRvSlotBytes, "revert table slot size");
 constexpr unsigned long long kRvEmpty = ~0ull;
 
-// slots in use this sub-round: a power of two >= 4 x moved incidences (>= 2 x keys), at most
-// the capacity (>= 2 P >= keys, so a free slot always exists)
+// slots in use this sub-round: a power of two >= 4 x moved incidences of shared nets (>= 2 x
+// keys), at most the capacity (>= 2 P >= keys, so a free slot always exists)
 __device__ __forceinline__ uint64_t rv_slots(const Dev &d)
 {
-    const uint64_t need = 4ull * __ldcg(d.rv_cnt);
+    const uint64_t need = 4ull * __ldcg(d.rv_cnt + 1);
     uint64_t c = 1024;
     while (c < need && c < (uint64_t)d.rv_cap) c <<= 1;
     return c;
@@ -1396,8 +1413,10 @@ struct alignas(16) RvWarp {
     int32_t g[32];
 };
 
+enum { RV_INSERT = 0, RV_EVAL = 1 };
+
 // Warp per range: the approved movers of each 32 candidates, their incidences flattened over
-// the lanes.  PASS 1 records the order statistics, PASS 2 sums each mover's attributed gain.
+// the lanes, one of the passes above per launch.
 template <typename Rec, int PASS>
 __global__ void __launch_bounds__(kThreads) k_rv_pass(const Dev d)
 {
@@ -1408,7 +1427,7 @@ __global__ void __launch_bounds__(kThreads) k_rv_pass(const Dev d)
     const int32_t ncand = d.cand_cnt[range];
     if (ncand == 0) return;
     RvWarp &rw = rw_[wid];
-    const uint64_t mask = rv_slots(d) - 1;
+    const uint64_t mask = (PASS == RV_INSERT || PASS == RV_EVAL) ? rv_slots(d) - 1 : 0;
     RvSlot *tab = reinterpret_cast<RvSlot *>(d.rv_tab);
     const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
     const uint64_t *cand = d.cand + (int64_t)range * kRange;
@@ -1447,15 +1466,16 @@ __global__ void __launch_bounds__(kThreads) k_rv_pass(const Dev d)
             const int v = slot_of(rw.w.off, i);
             const int32_t e = d.inc[rw.w.jb[v] + (i - rw.w.off[v])];
             const int32_t ee = e & kNetMask;
+            const int32_t movers = __ldcg(&d.rv_net[ee]);
             const int32_t av = rw.w.a[v], bv = rw.w.t[v], uv = rw.u[v];
-            const unsigned long long ka = (unsigned long long)ee * 64 + av, kb = (unsigned long long)ee * 64 + bv;
-            RvSlot *s_a = rv_find(tab, mask, ka, PASS == 1);
-            RvSlot *s_b = rv_find(tab, mask, kb, PASS == 1);
-            if (!s_a || !s_b) {
-                lost = true;
-                continue;
-            }
-            if (PASS == 1) {
+            if (PASS == RV_INSERT) {
+                if (movers < 2) continue;
+                RvSlot *s_a = rv_find(tab, mask, (unsigned long long)ee * 64 + av, true);
+                RvSlot *s_b = rv_find(tab, mask, (unsigned long long)ee * 64 + bv, true);
+                if (!s_a || !s_b) {
+                    lost = true;
+                    continue;
+                }
                 atomicMax(&s_a->max_out, uv);
                 atomicMin(&s_b->min_in, uv);
                 atomicAdd(&s_b->n_in, 1);
@@ -1465,13 +1485,25 @@ __global__ void __launch_bounds__(kThreads) k_rv_pass(const Dev d)
                 const int32_t pa = phi_get(d, ee, av, wide, wrow), pb = phi_get(d, ee, bv, wide, wrow);
                 const int32_t w = __ldg(&recs[ee].w) & 0x7fffffff;
                 int32_t g = 0;
-                if (pa == s_a->n_in && s_a->max_out == uv && s_a->min_in > uv) g += w;
-                if (pb == s_b->n_in && s_b->min_in == uv && s_b->max_out < uv) g -= w;
+                if (movers < 2) {
+                    // the only mover of e: Phi(e, a) went 1 -> 0, or Phi(e, b) went 0 -> 1
+                    if (pa == 0) g += w;
+                    if (pb == 1) g -= w;
+                } else {
+                    const RvSlot *s_a = rv_find(tab, mask, (unsigned long long)ee * 64 + av, false);
+                    const RvSlot *s_b = rv_find(tab, mask, (unsigned long long)ee * 64 + bv, false);
+                    if (!s_a || !s_b) {
+                        lost = true;
+                        continue;
+                    }
+                    if (pa == s_a->n_in && s_a->max_out == uv && s_a->min_in > uv) g += w;
+                    if (pb == s_b->n_in && s_b->min_in == uv && s_b->max_out < uv) g -= w;
+                }
                 if (g) atomicAdd(&rw.g[v], g);
             }
         }
         __syncwarp();
-        if (PASS == 2 && sa != kRvNone && rw.g[lane] < 0) src[idx] = (uint8_t)(sa | kRvBack);
+        if (PASS == RV_EVAL && sa != kRvNone && rw.g[lane] < 0) src[idx] = (uint8_t)(sa | kRvBack);
         __syncwarp();
     }
     if (lost) atomicOr(d.err, ERR_TABLE);
@@ -1486,7 +1518,10 @@ __global__ void __launch_bounds__(kThreads) k_rv_revert(const Dev d, int32_t rr)
     __shared__ ApplyWarp aw[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int32_t range = blockIdx.x * kWarps + wid;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *d.rv_cnt = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.rv_cnt[0] = 0;
+        d.rv_cnt[1] = 0;
+    }
     if (range >= d.n_ranges) return;
     const int32_t ncand = d.cand_cnt[range];
     if (ncand == 0) return;
@@ -1764,6 +1799,8 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         if (e == cudaSuccess) e = phase_begin(p.prof);
         if (e != cudaSuccess) break;
         const bool b = p.ranges != nullptr;
+        if (p.revert) e = cudaMemsetAsync(p.d0.rv_net, 0, sizeof(int32_t) * (size_t)p.d0.m, p.st);
+        if (e != cudaSuccess) break;
         if (p.rec32 && b) k_apply<Rec32, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
         else if (p.rec32) k_apply<Rec32, false><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
         else if (b) k_apply<Rec16, true><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, rr, s);
@@ -1774,14 +1811,15 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
         if (p.revert && e == cudaSuccess) e = phase_begin(p.prof);
         if (e == cudaSuccess && p.revert) {
             const unsigned g = warp_grid(p.n_ranges);
+            // the apply step counted the movers of every net and the shared incidences
             k_rv_clear<<<p.grid_apply * 4, kThreads, 0, p.st>>>(p.d0);
             if (p.rec32) {
-                k_rv_pass<Rec32, 1><<<g, kThreads, 0, p.st>>>(p.d0);
-                k_rv_pass<Rec32, 2><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec32, RV_INSERT><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec32, RV_EVAL><<<g, kThreads, 0, p.st>>>(p.d0);
                 k_rv_revert<Rec32><<<g, kThreads, 0, p.st>>>(p.d0, rr);
             } else {
-                k_rv_pass<Rec16, 1><<<g, kThreads, 0, p.st>>>(p.d0);
-                k_rv_pass<Rec16, 2><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec16, RV_INSERT><<<g, kThreads, 0, p.st>>>(p.d0);
+                k_rv_pass<Rec16, RV_EVAL><<<g, kThreads, 0, p.st>>>(p.d0);
                 k_rv_revert<Rec16><<<g, kThreads, 0, p.st>>>(p.d0, rr);
             }
             *p.launches += 4;

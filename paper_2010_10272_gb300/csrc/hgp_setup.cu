@@ -888,10 +888,13 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         unsigned long long *rv_cnt = nullptr;
         int64_t cap = 1024;
         while (cap < 2 * (int64_t)P) cap <<= 1;
+        int32_t *rv_net = nullptr;
         CKF(dalloc(h, &rv_src, (int64_t)d.n_ranges * kRange));
-        CKF(dalloc(h, &rv_cnt, 1));
+        CKF(dalloc(h, &rv_cnt, 2));
+        CKF(dalloc(h, &rv_net, m));
         CKF(dalloc(h, reinterpret_cast<uint4 **>(&d.rv_tab), cap * kRvSlotBytes / 16));
-        CKF(cudaMemsetAsync(rv_cnt, 0, sizeof(unsigned long long), st));
+        CKF(cudaMemsetAsync(rv_cnt, 0, 2 * sizeof(unsigned long long), st));
+        d.rv_net = rv_net;
         d.rv_src = rv_src;
         d.rv_cnt = rv_cnt;
         d.rv_cap = cap;
