@@ -358,12 +358,14 @@ __global__ void k_block_weights(Dev d)
         atomicAdd(reinterpret_cast<unsigned long long *>(&d.bw[threadIdx.x]), w[threadIdx.x]);
 }
 
-// Counts Phi(e, .) from the partition, writes the Phi row (into a zeroed table), the record
-// (Lambda, S1, omega, stamp) and adds (lambda(e) - 1) * omega(e) to the objective.  A warp takes
-// 32 consecutive nets, one per lane: a net of at most kSmallNet pins is counted by its lane in
-// registers (only its non-zero Phi entries are stored); larger nets are then counted by the
-// whole warp, one at a time, with shared-memory counters.
+// Counts Phi(e, .) from the partition, writes the Phi rows, the records (Lambda, S1, omega,
+// stamp) and adds (lambda(e) - 1) * omega(e) to the objective.  A warp takes 32 consecutive nets,
+// one per lane: a net of at most kSmallNet pins is counted by its lane in registers; larger nets
+// are then counted by the whole warp, one at a time, with shared-memory counters.  The 32 Phi
+// rows are assembled in shared memory and written as one contiguous block (coalesced, and no
+// separate zeroing of the table); the rows of nets in the wide table stay zero there.
 constexpr int kSmallNet = 8;
+constexpr int kInitWarps = 8;
 
 template <typename Rec>
 __device__ __forceinline__ void write_record(const Dev &d, int64_t e, uint64_t lam, uint64_t s1, int32_t wf)
@@ -388,16 +390,33 @@ __device__ __forceinline__ void write_record(const Dev &d, int64_t e, uint64_t l
     }
 }
 
-template <typename Rec>
-__global__ void k_init_nets(Dev d)
+// entry i of the staged row block (rows of `wb` bytes per net, entries of `w` bytes)
+__device__ __forceinline__ void stage_set(uint8_t *blk, int row, int i, int w, int wb, int32_t v)
 {
-    __shared__ int32_t cnt[kWarps][64];
-    __shared__ long long part_obj[kWarps];
+    uint8_t *p = blk + row * wb + i * w;
+    if (w == 1) *p = (uint8_t)v;
+    else if (w == 2) *reinterpret_cast<uint16_t *>(p) = (uint16_t)v;
+    else *reinterpret_cast<int32_t *>(p) = v;
+}
+
+template <typename Rec>
+__global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d)
+{
+    __shared__ int32_t cnt[kInitWarps][64];
+    __shared__ long long part_obj[kInitWarps];
+    extern __shared__ __align__(16) uint32_t stage_dyn[];   // kInitWarps blocks of 32 rows
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t warps = (int64_t)gridDim.x * kWarps;
+    const int64_t warps = (int64_t)gridDim.x * kInitWarps;
     const int32_t narrow_max = d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff);
+    const int w = d.phi_w, wb = d.k * d.phi_w;       // bytes per entry / per row
+    const int blk_words = (32 * wb + 15) / 16 * 4;   // one warp's block, 16-byte multiple
+    uint32_t *stage_w = stage_dyn + wid * blk_words;
+    uint8_t *stage = reinterpret_cast<uint8_t *>(stage_w);
     long long obj = 0;
-    for (int64_t e0 = ((int64_t)blockIdx.x * kWarps + wid) * 32; e0 < d.m; e0 += warps * 32) {
+    for (int64_t e0 = ((int64_t)blockIdx.x * kInitWarps + wid) * 32; e0 < d.m; e0 += warps * 32) {
+        const int32_t rows = (int32_t)min((int64_t)32, (int64_t)d.m - e0);
+        for (int i = lane; i < blk_words; i += 32) stage_w[i] = 0;
+        __syncwarp();
         const int64_t e = e0 + lane;
         int32_t b = 0, size = 0;
         if (e < d.m) {
@@ -436,7 +455,7 @@ __global__ void k_init_nets(Dev d)
                 if (j < nd) {
                     lam |= 1ull << blk[j];
                     if (c[j] == 1) s1 |= 1ull << blk[j];
-                    phi_set(d, (int32_t)e, blk[j], c[j], false, 0);
+                    stage_set(stage, lane, blk[j], w, wb, c[j]);
                 }
             }
             const int32_t wv = d.nw ? d.nw[e] : 1;
@@ -467,7 +486,10 @@ __global__ void k_init_nets(Dev d)
             const int32_t wv = d.nw ? d.nw[ee] : 1;
             const bool wide = d.widx != nullptr && sz > narrow_max;
             const int32_t wrow = wide ? d.widx[ee] : 0;
-            for (int i = lane; i < d.k; i += 32) phi_set(d, (int32_t)ee, i, cnt[wid][i], wide, wrow);
+            for (int i = lane; i < d.k; i += 32) {
+                if (wide) d.phi_wide[(int64_t)wrow * d.k + i] = cnt[wid][i];
+                else stage_set(stage, src, i, w, wb, cnt[wid][i]);
+            }
             const unsigned lo_lam = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] > 0);
             const unsigned lo_s1 = __ballot_sync(kFull, lane < d.k && cnt[wid][lane] == 1);
             const unsigned hi_lam = __ballot_sync(kFull, lane + 32 < d.k && cnt[wid][lane + 32] > 0);
@@ -481,13 +503,26 @@ __global__ void k_init_nets(Dev d)
             }
             __syncwarp();
         }
+        __syncwarp();
+        // the block of rows e0 .. e0 + rows - 1 starts at byte e0 * wb of the table
+        const int64_t byte0 = e0 * (int64_t)wb;
+        uint8_t *dst = reinterpret_cast<uint8_t *>(d.phi) + byte0;
+        if ((byte0 & 15) == 0 && (rows * wb) % 16 == 0) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(stage_w);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (int i = lane; i < rows * wb / 16; i += 32) d4[i] = s4[i];
+        } else {
+            // byte-exact tail (the table's rows need not be 16-byte multiples for small k)
+            for (int i = lane; i < rows * wb; i += 32) dst[i] = stage[i];
+        }
+        __syncwarp();
     }
     for (int o = 16; o; o >>= 1) obj += __shfl_xor_sync(kFull, obj, o);
     if (lane == 0) part_obj[wid] = obj;
     __syncthreads();
     if (threadIdx.x == 0) {
         long long s = 0;
-        for (int w = 0; w < kWarps; ++w) s += part_obj[w];
+        for (int i = 0; i < kInitWarps; ++i) s += part_obj[i];
         if (s) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)s);
     }
 }
@@ -605,15 +640,20 @@ int init_state(hgp_handle *h)
     CK(cudaMemsetAsync(d.obj, 0, sizeof(int64_t), st));
     // round 0, every vertex eligible
     CK(cudaMemsetAsync(d.rs, 0, 2 * sizeof(int32_t), st));
-    // the net kernel stores only the non-zero Phi entries of small nets
-    const int64_t words = ((int64_t)d.m * d.k * d.phi_w + 3) / 4;
-    CK(cudaMemsetAsync(d.phi, 0, sizeof(uint32_t) * (size_t)(words < 1 ? 1 : words), st));
+    // the net kernel writes every narrow Phi row (zeros included); the wide table's rows are
+    // written by their nets, but a row of a net with zero pins in range stays as zeroed here
     if (d.phi_wide && h->n_wide > 0) CK(cudaMemsetAsync(d.phi_wide, 0, sizeof(int32_t) * (size_t)h->n_wide * d.k, st));
     k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
     CK(cudaGetLastError());
-    const int g = grid_for(((int64_t)d.m + 31) / 32 * 32, kThreads, 152 * 16);
-    if (d.k <= 32) { k_init_nets<Rec16><<<g, kThreads, 0, st>>>(d); h->launches++; }
-    else { k_init_nets<Rec32><<<g, kThreads, 0, st>>>(d); h->launches++; }
+    const int g = grid_for(((int64_t)d.m + 31) / 32 * 32, kInitWarps * 32, 152 * 16);
+    const int smem = kInitWarps * (32 * d.k * d.phi_w + 15) / 16 * 16;
+    if (d.k <= 32) {
+        cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d); h->launches++;
+    } else {
+        cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d); h->launches++;
+    }
     CK(cudaGetLastError());
     h->next_round = 0;
     h->all_eligible = true;
