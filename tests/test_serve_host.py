@@ -1,0 +1,110 @@
+"""Host logic of the serving loop on CPU: admission by a memory budget, waiting while the
+queue head does not fit, refusal of a request that can never fit, retirement after its rounds,
+latencies from the server clock.  The device handles and the batch are replaced by fakes, so no
+GPU is needed; tests/test_serving_gpu.py covers the real thing."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+
+class FakeHGP:
+    live = 0
+
+    def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None, **kw):
+        self.part = np.asarray(part, np.int32).copy()
+        FakeHGP.live += 1
+
+    def partition(self):
+        return self.part
+
+    def objective(self):
+        return 7
+
+    def close(self):
+        FakeHGP.live -= 1
+
+
+class FakeBatch:
+    sizes = []
+
+    def __init__(self, handles, **kw):
+        self.handles = handles
+        FakeBatch.sizes.append(len(handles))
+
+    def refine(self, rounds, stats=True):
+        return np.zeros((len(self.handles), rounds, 7), np.int64)
+
+    def close(self):
+        pass
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1.0
+        return self.t
+
+
+@pytest.fixture()
+def server_cls(monkeypatch):
+    from paper_2010_10272_gb300 import serve
+    monkeypatch.setattr(serve, "HGP", FakeHGP)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (1 << 40, 1 << 40))
+    FakeHGP.live = 0
+    FakeBatch.sizes = []
+    return serve
+
+
+def _req(serve, rid, p, rounds):
+    hg = synth.serving_request(np.random.SeedSequence(rid), p_lo=p, p_hi=p + 1)
+    return serve.Request.from_hypergraph(rid, hg, rounds=rounds)
+
+
+def test_admission_by_budget_and_retirement(server_cls):
+    serve = server_cls
+    reqs = [_req(serve, i, 20_000, 1 + i % 3) for i in range(6)]
+    one = reqs[0].footprint()
+    srv = serve.Server(memory_budget=int(2.5 * one), reserve_bytes=0, clock=Clock())
+    for r in reqs:
+        srv.submit(r)
+    done = []
+    max_active = 0
+    while not srv.idle():
+        done.extend(srv.step())
+        max_active = max(max_active, len(srv.active))
+        assert srv._resident_bytes <= srv.memory_budget
+    assert sorted(r.rid for r in done) == list(range(6))
+    assert max(FakeBatch.sizes) == 2          # at most two requests fit the budget
+    assert FakeHGP.live == 0                   # every handle closed on retirement
+    for r in done:
+        assert r.finished > r.admitted >= r.arrival and r.latency > 0
+        np.testing.assert_array_equal(r.result, r.part)
+        assert r.stats.shape == (r.rounds, 7)      # one statistics row per round
+    srv.close()
+
+
+def test_request_that_never_fits_is_refused(server_cls):
+    serve = server_cls
+    small, big = _req(serve, 1, 20_000, 1), _req(serve, 2, 2_000_000, 1)
+    srv = serve.Server(memory_budget=int(1.5 * small.footprint()), reserve_bytes=0, clock=Clock())
+    srv.submit(big)
+    srv.submit(small)
+    done = srv.run_until_idle()
+    assert [r.rid for r in done] == [1] and [r.rid for r in srv.rejected] == [2]
+
+
+def test_footprint_grows_with_the_instance(server_cls):
+    serve = server_cls
+    a = serve.estimate_device_bytes(1000, 1000, 7000, 8, 20, False, False)
+    b = serve.estimate_device_bytes(2000, 2000, 14000, 8, 20, False, False)
+    c = serve.estimate_device_bytes(3_000_000, 3_000_000, 21_000_000, 8, 20, False, False)
+    d = serve.estimate_device_bytes(3_000_000, 3_000_000, 21_000_000, 64, 20, True, True)
+    assert a < b < c < d
+    # above 2^21 vertices the transpose's pairs (8 bytes per pin) are part of the peak
+    assert c >= 21_000_000 * 8
