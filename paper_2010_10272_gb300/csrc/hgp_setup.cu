@@ -116,23 +116,62 @@ __global__ void k_check_offsets(const int64_t *off64, int32_t *off32, int32_t m,
 }
 
 // warp per net: pins in range and strictly increasing; largest net size
-__global__ void k_check_pins(const int32_t *off, const int32_t *pins, int32_t m, int32_t n,
-                             int32_t *err, int32_t *max_size)
+// Warp-wide: the pins of nets e0 .. e0 + 31 (clipped to e_hi) are contiguous; off33 receives
+// their exclusive offsets inside that run (off33[32] = its length) and the run's first pin index
+// is returned.  Lanes then walk the run flattened, one pin each, with pin_net to find the net.
+__device__ __forceinline__ int32_t net_group(const int32_t *off, int64_t e0, int64_t e_hi, int32_t *off33,
+                                             int32_t &sz_lane)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int32_t local_max = 0;
-    for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
-        const int32_t b = off[e], end = off[e + 1];
-        local_max = max(local_max, end - b);
-        bool bad = false;
-        for (int32_t j = b + lane; j < end; j += 32) {
-            const int32_t v = pins[j];
-            if (v < 0 || v >= n) bad = true;
-            if (j + 1 < end && pins[j + 1] <= v) bad = true;
-        }
-        if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, ERR_INVALID);
+    const int64_t e = e0 + lane;
+    sz_lane = e < e_hi ? off[e + 1] - off[e] : 0;
+    int32_t incl = sz_lane;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
     }
+    off33[lane] = incl - sz_lane;
+    if (lane == 31) off33[32] = incl;
+    __syncwarp();
+    return off[e0];
+}
+
+// slot of the net holding run position i: the largest s with off33[s] <= i (empty nets skipped)
+__device__ __forceinline__ int pin_net(const int32_t *off33, int32_t i)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1)
+        if (off33[lo + step] <= i) lo += step;
+    return lo;
+}
+
+// pins in [0, n) and strictly increasing inside every net; the largest net size.  Offsets
+// were checked before (k_check_offsets).  A warp walks 32 nets' pins at once, coalesced.
+__global__ void __launch_bounds__(256) k_check_pins(const int32_t *off, const int32_t *pins, int32_t m, int32_t n,
+                                                    int32_t *err, int32_t *max_size)
+{
+    __shared__ int32_t off33_w[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *off33 = off33_w[wid];
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    int32_t local_max = 0;
+    bool bad = false;
+    for (int64_t e0 = ((int64_t)blockIdx.x * 8 + wid) * 32; e0 < m; e0 += warps * 32) {
+        int32_t sz;
+        const int32_t base = net_group(off, e0, m, off33, sz);
+        local_max = max(local_max, sz);
+        const int32_t total = off33[32];
+        for (int32_t i = lane; i < total; i += 32) {
+            const int32_t v = pins[base + i];
+            if (v < 0 || v >= n) bad = true;
+            if (i > off33[pin_net(off33, i)] && pins[base + i - 1] >= v) bad = true;
+        }
+        __syncwarp();
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, ERR_INVALID);
+    for (int o = 16; o; o >>= 1) local_max = max(local_max, __shfl_xor_sync(kFull, local_max, o));
     if (lane == 0) atomicMax(max_size, local_max);
 }
 
@@ -233,48 +272,34 @@ __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P,
 }
 
 // CTA per per_cta nets; pass 0 counts its pins per bucket, then one range per bucket is
-// reserved, pass 1 writes the pairs.  A net of at most 32 pins is walked by one lane, a larger
-// one by the whole warp.
+// reserved, pass 1 writes the pairs.  A warp walks the pins of 32 nets at once (coalesced).
 __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m, int bshift,
                                                     int32_t nb, int32_t narrow_max, int32_t per_cta,
                                                     int32_t *bucket_cur, unsigned long long *pairs)
 {
     __shared__ int32_t cur[kTpMaxBuckets];
-    const int lane = threadIdx.x & 31;
+    __shared__ int32_t off33_w[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *off33 = off33_w[wid];
     const int64_t e_lo = (int64_t)blockIdx.x * per_cta;
     const int64_t e_hi = min((int64_t)m, e_lo + per_cta);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
-        for (int64_t e0 = e_lo + (threadIdx.x & ~31); e0 < e_hi; e0 += blockDim.x) {
-            const int64_t e = e0 + lane;
-            int32_t b = 0, sz = 0;
-            if (e < e_hi) {
-                b = off[e];
-                sz = off[e + 1] - b;
-            }
-            const bool small = e < e_hi && sz <= 32;
-            if (small) {
-                const uint32_t ef = (uint32_t)e | (sz > narrow_max ? kWideFlag : 0u);
-                for (int32_t j = b; j < b + sz; ++j) {
-                    const int32_t v = pins[j];
-                    const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
-                    if (pass == 1) pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+        for (int64_t e0 = e_lo + 32 * wid; e0 < e_hi; e0 += 32 * 8) {
+            int32_t sz;
+            const int32_t base = net_group(off, e0, e_hi, off33, sz);
+            const int32_t total = off33[32];
+            for (int32_t i = lane; i < total; i += 32) {
+                const int32_t v = pins[base + i];
+                const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
+                if (pass == 1) {
+                    const int sl = pin_net(off33, i);
+                    const uint32_t ef = (uint32_t)(e0 + sl) | (off33[sl + 1] - off33[sl] > narrow_max ? kWideFlag : 0u);
+                    pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
                 }
             }
-            unsigned big = __ballot_sync(kFull, e < e_hi && !small);
-            while (big) {
-                const int src = __ffs(big) - 1;
-                big &= big - 1;
-                const int64_t ee = e0 + src;
-                const int32_t bb = __shfl_sync(kFull, b, src), s2 = __shfl_sync(kFull, sz, src);
-                const uint32_t ef = (uint32_t)ee | (s2 > narrow_max ? kWideFlag : 0u);
-                for (int32_t j = bb + lane; j < bb + s2; j += 32) {
-                    const int32_t v = pins[j];
-                    const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
-                    if (pass == 1) pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
-                }
-            }
+            __syncwarp();
         }
         __syncthreads();
         if (pass == 0) {
@@ -770,7 +795,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(cudaStreamSynchronize(st));
     if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     if (m > 0) {
-        k_check_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
+        k_check_pins<<<grid_for(m, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
         CKF(cudaGetLastError());
     }
     CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
