@@ -187,11 +187,13 @@ __device__ __forceinline__ void net_done(int64_t e, int32_t kept, unsigned long 
     }
 }
 
-constexpr int kTiny = 8, kMedium = 2048;
+constexpr int kTiny = 8, kMid = 256, kMedium = 2048;
+constexpr int kClasses = 4;   // listed classes: 9..32, 33..kMid, kMid+1..kMedium, larger
 
 // thread per net: nets of at most kTiny pins are sorted in registers (an unrolled sorting
-// network), de-duplicated and fingerprinted; larger nets go to the lists of the warp (9..32
-// pins), CTA shared-memory (..kMedium) and CTA radix (larger) kernels
+// network), de-duplicated and fingerprinted; larger nets go to the lists of the warp-register
+// (9..32 pins), warp shared-memory (..kMid), CTA shared-memory (..kMedium) and chunked (larger)
+// kernels
 __global__ void k_ct_tiny(const int64_t *off, const int32_t *pins, int32_t m, const int32_t *map, int32_t *a,
                           int32_t *size1, unsigned long long *key, int32_t *rep, int32_t *lists, int32_t *counts)
 {
@@ -227,12 +229,12 @@ __global__ void k_ct_tiny(const int64_t *off, const int32_t *pins, int32_t m, co
                 }
                 net_done(e, kept, h, size1, key, rep);
             } else {
-                cls = s <= 32 ? 0 : (s <= kMedium ? 1 : 2);
+                cls = s <= 32 ? 0 : (s <= kMid ? 1 : (s <= kMedium ? 2 : 3));
             }
         }
         // warp-aggregated append of the larger nets to their class lists
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < kClasses; ++c) {
             const unsigned mk = __ballot_sync(kFull, cls == c);
             if (!mk) continue;
             int32_t base = 0;
@@ -275,6 +277,58 @@ __global__ void k_ct_small(const int64_t *off, const int32_t *pins, const int32_
     }
 }
 
+// warp per listed net of 33..kMid pins: bitonic sort in the warp's shared buffer (padded to a
+// power of two), then an order-preserving compaction 32 values at a time, and the fingerprint
+__global__ void __launch_bounds__(256) k_ct_mid(const int64_t *off, const int32_t *pins, const int32_t *map,
+                                                const int32_t *list, const int32_t *count, int32_t *a,
+                                                int32_t *size1, unsigned long long *key, int32_t *rep)
+{
+    __shared__ int32_t buf_w[8][kMid];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *buf = buf_w[wid];
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    const int32_t cnt = *count;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + wid; i < cnt; i += warps) {
+        const int64_t e = list[i];
+        const int64_t b = off[e];
+        const int32_t s = (int32_t)(off[e + 1] - b);
+        int32_t np2 = 64;
+        while (np2 < s) np2 <<= 1;
+        for (int32_t j = lane; j < np2; j += 32) buf[j] = j < s ? map[pins[b + j]] : 0x7fffffff;
+        __syncwarp();
+        for (int32_t k = 2; k <= np2; k <<= 1) {
+            for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int32_t x = lane; x < np2; x += 32) {
+                    const int32_t y = x ^ jj;
+                    if (y > x) {
+                        const bool up = (x & k) == 0;
+                        const int32_t vx = buf[x], vy = buf[y];
+                        if ((vx > vy) == up) { buf[x] = vy; buf[y] = vx; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int32_t kept = 0;
+        unsigned long long h = 0;
+        for (int32_t c = 0; c < s; c += 32) {
+            const int32_t j = c + lane;
+            const bool has = j < s;
+            const int32_t v = has ? buf[j] : 0;
+            const bool keep = has && (j == 0 || v != buf[j - 1]);
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) {
+                a[b + kept + __popc(km & ((1u << lane) - 1))] = v;
+                h += pin_mix(v);
+            }
+            kept += __popc(km);
+        }
+        for (int o = 16; o; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        if (lane == 0) net_done(e, kept, h, size1, key, rep);
+        __syncwarp();
+    }
+}
+
 // block-wide: order-preserving compaction of the first of every run of equal values of the
 // sorted src[0..s) into dst (dst may equal src), fingerprint of the kept values
 __device__ __forceinline__ void compact_runs(const int32_t *src, int32_t *dst, int32_t s, int32_t *wtot,
@@ -311,7 +365,7 @@ __device__ __forceinline__ void compact_runs(const int32_t *src, int32_t *dst, i
     h_out = *hsum;
 }
 
-// CTA per listed net of 33..kMedium pins: bitonic sort of the mapped pins in shared memory
+// CTA per listed net of kMid+1..kMedium pins: bitonic sort of the mapped pins in shared memory
 // (padded to a power of two), then compaction into a and the fingerprint
 __global__ void __launch_bounds__(kSortThreads) k_ct_medium(const int64_t *off, const int32_t *pins,
                                                             const int32_t *map, const int32_t *list,
@@ -327,7 +381,7 @@ __global__ void __launch_bounds__(kSortThreads) k_ct_medium(const int64_t *off, 
         const int64_t e = list[i];
         const int64_t b = off[e];
         const int32_t s = (int32_t)(off[e + 1] - b);
-        int32_t np2 = 64;
+        int32_t np2 = 2 * kMid;
         while (np2 < s) np2 <<= 1;
         for (int32_t j = tid; j < np2; j += kSortThreads) buf[j] = j < s ? map[pins[b + j]] : 0x7fffffff;
         __syncthreads();
@@ -740,20 +794,21 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(cudaMallocAsync(reinterpret_cast<void **>(&size1), sizeof(int32_t) * (size_t)mm, st));
     CT(cudaMallocAsync(reinterpret_cast<void **>(&key), sizeof(unsigned long long) * (size_t)mm, st));
     CT(cudaMallocAsync(reinterpret_cast<void **>(&rep), sizeof(int32_t) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&lists), sizeof(int32_t) * 3 * (size_t)mm + 16, st));
-    counts = lists + 3 * mm;
-    CT(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 3, st));
+    CT(cudaMallocAsync(reinterpret_cast<void **>(&lists), sizeof(int32_t) * kClasses * (size_t)mm + 32, st));
+    counts = lists + kClasses * mm;
+    CT(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (kClasses + 1), st));
     if (m > 0) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         k_ct_tiny<<<grid_of(m, 256), 256, 0, st>>>(net_off, pins, m, c->map, a, size1, key, rep, lists, counts);
         k_ct_small<<<sms * 8, 256, 0, st>>>(net_off, pins, c->map, lists, counts, a, size1, key, rep);
-        k_ct_medium<<<sms * 8, kSortThreads, 0, st>>>(net_off, pins, c->map, lists + mm, counts + 1, a, size1, key, rep);
+        k_ct_mid<<<sms * 8, 256, 0, st>>>(net_off, pins, c->map, lists + mm, counts + 1, a, size1, key, rep);
+        k_ct_medium<<<sms * 8, kSortThreads, 0, st>>>(net_off, pins, c->map, lists + 2 * mm, counts + 2, a, size1, key, rep);
         CT(cudaGetLastError());
         // nets of more than kMedium pins: chunk sorts, merge passes, de-duplication
-        int32_t hcnt[4] = {0, 0, 0, 0};
-        CT(cudaMemcpyAsync(hcnt, counts, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, st));
+        int32_t hcnt[kClasses] = {0, 0, 0, 0};
+        CT(cudaMemcpyAsync(hcnt, counts, sizeof(int32_t) * kClasses, cudaMemcpyDeviceToHost, st));
         CT(cudaStreamSynchronize(st));
-        n_large = hcnt[2];
+        n_large = hcnt[3];
         if (n_large > 0) {
             int32_t *chunks = nullptr;
             int64_t *cpre = nullptr;
@@ -761,23 +816,23 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
             CT(cudaMallocAsync(reinterpret_cast<void **>(&cpre), sizeof(int64_t) * ((size_t)n_large + 1), st));
             lg_scratch[0] = chunks;
             lg_scratch[1] = cpre;
-            CT(cudaMemsetAsync(counts + 3, 0, sizeof(int32_t), st));
-            k_lg_count<<<grid_of(n_large, 256), 256, 0, st>>>(net_off, lists + 2 * mm, counts + 2, chunks, counts + 3);
+            CT(cudaMemsetAsync(counts + kClasses, 0, sizeof(int32_t), st));
+            k_lg_count<<<grid_of(n_large, 256), 256, 0, st>>>(net_off, lists + 3 * mm, counts + 3, chunks, counts + kClasses);
             CT(cudaGetLastError());
             CT(scan_excl<int32_t>(chunks, n_large, cpre, st));
             int64_t tasks = 0;
             int32_t max_size = 0;
             CT(cudaMemcpyAsync(&tasks, cpre + n_large, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            CT(cudaMemcpyAsync(&max_size, counts + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CT(cudaMemcpyAsync(&max_size, counts + kClasses, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             CT(cudaStreamSynchronize(st));
             const int g = (int)(tasks < (int64_t)sms * 2 ? tasks : (int64_t)sms * 2);
-            k_lg_chunk<<<g, kLgThreads, 0, st>>>(net_off, pins, c->map, lists + 2 * mm, counts + 2, cpre, tasks, a);
+            k_lg_chunk<<<g, kLgThreads, 0, st>>>(net_off, pins, c->map, lists + 3 * mm, counts + 3, cpre, tasks, a);
             int32_t *src = a, *dst = b;
             for (int64_t w = kMedium; w < max_size; w *= 2) {
-                k_lg_merge<<<g, kLgThreads, 0, st>>>(net_off, lists + 2 * mm, counts + 2, cpre, tasks, src, dst, (int32_t)w);
+                k_lg_merge<<<g, kLgThreads, 0, st>>>(net_off, lists + 3 * mm, counts + 3, cpre, tasks, src, dst, (int32_t)w);
                 int32_t *t = src; src = dst; dst = t;
             }
-            k_lg_dedupe<<<n_large < sms * 2 ? n_large : sms * 2, kLgThreads, 0, st>>>(net_off, lists + 2 * mm, counts + 2,
+            k_lg_dedupe<<<n_large < sms * 2 ? n_large : sms * 2, kLgThreads, 0, st>>>(net_off, lists + 3 * mm, counts + 3,
                                                                                      src, a, size1, key, rep);
             CT(cudaGetLastError());
         }
@@ -825,7 +880,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     if (m > 0) {
         if (n_large > 0)
             k_lg_emit<<<n_large < sms * 2 ? n_large : sms * 2, kLgThreads, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64,
-                                                                                   lists + 2 * mm, counts + 2, c->pins,
+                                                                                   lists + 3 * mm, counts + 3, c->pins,
                                                                                    c->net_off, c->nw, err);
         k_ct_emit<<<grid_of(m, 256), 256, 0, st>>>(net_off, a, size1, rep, nid, poff, nw64, m,
                                                                  c->pins, c->net_off, c->nw, err);
