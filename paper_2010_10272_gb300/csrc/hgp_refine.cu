@@ -1597,34 +1597,37 @@ __global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr, int32_t
     }
 }
 
-// Rebalancing, source side (KEY_A): warp per range; marks the candidates that may leave their
-// block (bit 24) and adds their weights to the per-target totals of the target-side stage.
+// Rebalancing, source side (KEY_A): persistent, a warp per range item with a grid stride (the
+// per-block thresholds are read once per warp); marks the candidates that may leave their block
+// (bit 24) and adds their weights to the per-target totals of the target-side stage.
 __global__ void __launch_bounds__(kThreads) k_rb_mark(const Dev d)
 {
     __shared__ ApplyInst ai_w[kWarps];
     __shared__ unsigned long long run_w[kWarps][64];
     __shared__ unsigned long long tot_w[kWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t range = blockIdx.x * kWarps + wid;
-    if (range >= d.n_ranges) return;
-    const int32_t ncand = d.cand_cnt[range];
-    if (ncand == 0) return;
     int32_t r;
     const bool any_thr = apply_refresh(d, ai_w[wid], r);
     tot_w[wid][lane] = 0;
     tot_w[wid][lane + 32] = 0;
-    uint64_t *cand = d.cand + (int64_t)range * kRange;
-    range_tie_prefix<KEY_A>(d, range, any_thr, ai_w[wid], run_w[wid], cand, ncand);
-    for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
-        const int idx = c0 + lane;
-        int t, key, ul;
-        int32_t g;
-        unsigned long long cw;
-        const bool sel = approve_slot<KEY_A>(d, range, cand, ncand, idx, ai_w[wid], run_w[wid], t, key, g, ul, cw);
-        if (sel) {
-            cand[idx] |= kSelBit;
-            atomicAdd(&tot_w[wid][t], cw);
+    __syncwarp();
+    for (int32_t range = blockIdx.x * kWarps + wid; range < d.n_ranges; range += gridDim.x * kWarps) {
+        const int32_t ncand = d.cand_cnt[range];
+        if (ncand == 0) continue;
+        uint64_t *cand = d.cand + (int64_t)range * kRange;
+        range_tie_prefix<KEY_A>(d, range, any_thr, ai_w[wid], run_w[wid], cand, ncand);
+        for (int32_t c0 = 0; c0 < ncand; c0 += 32) {
+            const int idx = c0 + lane;
+            int t, key, ul;
+            int32_t g;
+            unsigned long long cw;
+            const bool sel = approve_slot<KEY_A>(d, range, cand, ncand, idx, ai_w[wid], run_w[wid], t, key, g, ul, cw);
+            if (sel) {
+                cand[idx] |= kSelBit;
+                atomicAdd(&tot_w[wid][t], cw);
+            }
         }
+        __syncwarp();
     }
     __syncwarp();
     for (int t = lane; t < 64 && t < d.k; t += 32)
@@ -2128,7 +2131,7 @@ cudaError_t launch_rebalance_pass(const Plan &p, int32_t pass, RbArgs rb, bool l
         k_gain<Rec, false, true><<<p.grid_gain, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, s, pass, rb);
         *p.launches += 1;
         *p.launches += launch_stage<KEY_A>(p, levels);
-        k_rb_mark<<<warp_grid(p.n_ranges), kThreads, 0, p.st>>>(p.d0);
+        k_rb_mark<<<p.grid_apply, kThreads, 0, p.st>>>(p.d0);
         *p.launches += 1;
         *p.launches += launch_stage<KEY_TS>(p, levels);
         k_apply<Rec, false, KEY_TS><<<p.grid_apply, kThreads, 0, p.st>>>(p.d0, p.devs, p.ranges, p.n_ranges, pass, s);
