@@ -67,7 +67,12 @@ typedef struct {
                             Phi table after the call and returns HGP_ERR_INTERNAL if it differs
                             from the incrementally maintained one; bit 1: build the vertex ->
                             nets lists with the bucketed transpose whatever the size (it is
-                            otherwise used above 2^21 vertices) [0] */
+                            otherwise used above 2^21 vertices); bit 2: store the nets in
+                            internal order (by size class, largest first, so that the records
+                            of the largest nets share L2 lines) whatever the size (it is
+                            otherwise used from 2^20 nets on); bit 3: keep the input net order.
+                            Results do not depend on the order; per-net outputs and
+                            checkpoints always use input net ids [0] */
     int32_t graph;       /* 1: hgp_refine captures its launches as a CUDA graph on the first call
                             with a given round count and replays it afterwards [0]; ignored
                             while profiling is on */

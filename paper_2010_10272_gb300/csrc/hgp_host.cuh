@@ -17,12 +17,15 @@ struct hgp_handle {
     int64_t next_round = 0;       // global round counter r
     bool all_eligible = true;     // first round after creation / set_partition
     int32_t n_wide = 0;
+    int32_t m_big = 0;            // internal order: nets [0, m_big) have at least kBigNet pins
+    int32_t m_big32 = 0;          // m_big rounded up to whole 32-net groups (at most m)
     int64_t max_vertex_netweight = 0;   // max_u sum_{e in I(u)} omega(e)
     int64_t total_weight = 0;
     int32_t stats_cap = 0;
     int64_t *h_stats = nullptr;   // pinned host copy of the stats buffer
     // memory owned by the handle
-    void *allocs[40] = {};
+    static constexpr int kMaxAllocs = 64;
+    void *allocs[kMaxAllocs] = {};
     int n_allocs = 0;
     // CUDA-graph cache: one refine() of `graph_rounds` rounds
     cudaGraphExec_t graph_exec = nullptr;

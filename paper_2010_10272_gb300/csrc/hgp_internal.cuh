@@ -83,6 +83,8 @@ struct Dev {
     uint32_t *phi;
     int32_t *phi_wide;
     const int32_t *widx;    // [m] row index in phi_wide (valid where the wide flag is set)
+    const int32_t *net_perm;  // [m] internal id of input net e (nullptr: input order kept);
+                              // every per-net array above is in internal order
     void *rec;              // Rec16[m] (k <= 32) or Rec32[m]
     int64_t *bw;
     int64_t *obj;

@@ -175,6 +175,102 @@ __global__ void __launch_bounds__(256) k_check_pins(const int32_t *off, const in
     if (lane == 0) atomicMax(max_size, local_max);
 }
 
+// ------------------------------------------------------------------ internal net order
+// Nets are relabelled by size class, the largest class first and by input id inside a class.
+// On skewed instances a few large nets take most record gathers (each incidence reads its net's
+// record); stored first, their records and Phi rows share L2 lines and stay resident there.
+// Gains, objective and every move are sums over nets, so results do not depend on the order.
+constexpr int kNrRanks = 32;        // rank 0: the largest size class (2^30 pins and up)
+constexpr int kNrThreads = 256;
+
+__device__ __forceinline__ int nr_rank(int32_t size)
+{
+    return size <= 1 ? kNrRanks - 1 : __clz(size);   // sizes [2^c, 2^(c+1)) -> 31 - c
+}
+
+// per CTA (a contiguous chunk of per_cta nets): nets per rank, written rank-major so that one
+// exclusive scan yields every (rank, CTA) base position
+__global__ void __launch_bounds__(kNrThreads) k_nr_count(const int32_t *off, int32_t m, int32_t per_cta,
+                                                         int32_t *cnt)
+{
+    __shared__ int32_t c[kNrRanks];
+    if (threadIdx.x < kNrRanks) c[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t lo = (int64_t)blockIdx.x * per_cta;
+    const int64_t hi = min((int64_t)m, lo + per_cta);
+    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) atomicAdd(&c[nr_rank(off[e + 1] - off[e])], 1);
+    __syncthreads();
+    if (threadIdx.x < kNrRanks) cnt[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = c[threadIdx.x];
+}
+
+// same chunks: internal id of every net (stable inside a rank) and the sizes in internal order
+__global__ void __launch_bounds__(kNrThreads) k_nr_place(const int32_t *off, int32_t m, int32_t per_cta,
+                                                         const int32_t *base, int32_t *perm, int32_t *size_int)
+{
+    constexpr int W = kNrThreads / 32;
+    __shared__ int32_t run[kNrRanks];
+    __shared__ int32_t wc[W][kNrRanks];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kNrRanks) run[threadIdx.x] = base[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    const int64_t lo = (int64_t)blockIdx.x * per_cta;
+    const int64_t hi = min((int64_t)m, lo + per_cta);
+    for (int64_t c0 = lo; c0 < hi; c0 += kNrThreads) {
+        for (int i = threadIdx.x; i < W * kNrRanks; i += kNrThreads) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t e = c0 + threadIdx.x;
+        const bool valid = e < hi;
+        const int32_t size = valid ? off[e + 1] - off[e] : 0;
+        const int rk = valid ? nr_rank(size) : kNrRanks;
+        const unsigned peers = __match_any_sync(kFull, rk);
+        const int below = __popc(peers & ((1u << lane) - 1));
+        if (valid && below == 0) wc[wid][rk] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int32_t pos = run[rk] + below;
+            for (int w = 0; w < wid; ++w) pos += wc[w][rk];
+            perm[e] = pos;
+            size_int[pos] = size;
+        }
+        __syncthreads();
+        if (threadIdx.x < kNrRanks) {
+            int32_t t = 0;
+            for (int w = 0; w < W; ++w) t += wc[w][threadIdx.x];
+            run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// pins (and net weights) into internal order; a warp copies the pins of 32 consecutive input
+// nets, reading them as one coalesced run
+__global__ void __launch_bounds__(256) k_nr_pins(const int32_t *off, const int32_t *pins, const int32_t *nw,
+                                                 int32_t m, const int32_t *perm, const int32_t *off_int,
+                                                 int32_t *pins_int, int32_t *nw_int)
+{
+    __shared__ int32_t off33_w[8][33];
+    __shared__ int32_t dst_w[8][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *off33 = off33_w[wid];
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t e0 = ((int64_t)blockIdx.x * 8 + wid) * 32; e0 < m; e0 += warps * 32) {
+        int32_t sz;
+        const int32_t src = net_group(off, e0, m, off33, sz);
+        const int64_t e = e0 + lane;
+        if (e < m) {
+            const int32_t q = perm[e];
+            dst_w[wid][lane] = off_int[q];
+            if (nw) nw_int[q] = nw[e];
+        }
+        __syncwarp();
+        const int32_t total = off33[32];
+        for (int32_t i = lane; i < total; i += 32) {
+            const int sl = pin_net(off33, i);
+            pins_int[dst_w[wid][sl] + (i - off33[sl])] = pins[src + i];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_check_vertices(const int32_t *vw, const int32_t *part_in, int32_t n, int32_t k,
                                  int32_t *err)
 {
@@ -221,6 +317,12 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
 // an exclusive scan into vtx_off, then every pin takes the next slot of its vertex (warp per
 // net) and stores the net id with the wide flag.
 constexpr int32_t kTpDirectMaxN = 1 << 21;
+// nets are stored in internal (size class) order from this many nets on: below it their records
+// fit in L2 whatever the order
+constexpr int32_t kReorderMinNets = 1 << 20;
+// in internal order, nets of at least this many pins (a prefix) get their own CTAs at creation
+// and initialisation (a power of two: size classes are powers of two)
+constexpr int32_t kBigNet = 256;
 
 __global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg)
 {
@@ -273,15 +375,15 @@ __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P,
 
 // CTA per per_cta nets; pass 0 counts its pins per bucket, then one range per bucket is
 // reserved, pass 1 writes the pairs.  A warp walks the pins of 32 nets at once (coalesced).
-__global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m, int bshift,
-                                                    int32_t nb, int32_t narrow_max, int32_t per_cta,
-                                                    int32_t *bucket_cur, unsigned long long *pairs)
+__global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m,
+                                                    int32_t e_begin, int bshift, int32_t nb, int32_t narrow_max,
+                                                    int32_t per_cta, int32_t *bucket_cur, unsigned long long *pairs)
 {
     __shared__ int32_t cur[kTpMaxBuckets];
     __shared__ int32_t off33_w[8][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *off33 = off33_w[wid];
-    const int64_t e_lo = (int64_t)blockIdx.x * per_cta;
+    const int64_t e_lo = e_begin + (int64_t)blockIdx.x * per_cta;
     const int64_t e_hi = min((int64_t)m, e_lo + per_cta);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
     __syncthreads();
@@ -300,6 +402,61 @@ __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const in
                 }
             }
             __syncwarp();
+        }
+        __syncthreads();
+        if (pass == 0) {
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+                const int32_t c = cur[i];
+                cur[i] = c ? atomicAdd(&bucket_cur[i], c) : 0;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The pins of the large-net prefix [0, m_big) of the internal order (nets of at least kBigNet
+// pins), split into chunks of kTpBigChunk pins, one CTA each, so that no CTA takes many large
+// nets.  A chunk overlaps at most kTpBigChunk / kBigNet + 2 nets, whose offsets are staged in
+// shared memory.  Same two passes as k_tp_scatter.
+constexpr int kTpBigChunk = 8192;
+constexpr int kTpBigWin = kTpBigChunk / kBigNet + 3;   // offsets of the nets a chunk overlaps, + 1
+
+__global__ void __launch_bounds__(256) k_tp_scatter_big(const int32_t *off, const int32_t *pins, int32_t m_big,
+                                                        int bshift, int32_t nb, int32_t narrow_max,
+                                                        int32_t *bucket_cur, unsigned long long *pairs)
+{
+    __shared__ int32_t cur[kTpMaxBuckets];
+    __shared__ int32_t win[kTpBigWin];
+    __shared__ int32_t first;
+    const int32_t p_end = off[m_big];
+    const int32_t p0 = blockIdx.x * kTpBigChunk;
+    const int32_t p1 = min(p_end, p0 + kTpBigChunk);
+    if (threadIdx.x == 0) {   // the net holding pin p0: the largest e < m_big with off[e] <= p0
+        int32_t lo = 0, hi = m_big - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= p0) lo = mid;
+            else hi = mid - 1;
+        }
+        first = lo;
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = 0;
+    __syncthreads();
+    const int32_t e_f = first;
+    for (int i = threadIdx.x; i < kTpBigWin; i += blockDim.x) win[i] = off[min(m_big, e_f + i)];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int32_t j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
+            const int32_t v = pins[j];
+            const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
+            if (pass == 1) {
+                int sl = 0;   // the largest slot with win[sl] <= j
+#pragma unroll
+                for (int step = 32; step; step >>= 1)
+                    if (sl + step < kTpBigWin && win[sl + step] <= j) sl += step;
+                const uint32_t ef = (uint32_t)(e_f + sl) | (win[sl + 1] - win[sl] > narrow_max ? kWideFlag : 0u);
+                pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+            }
         }
         __syncthreads();
         if (pass == 0) {
@@ -425,7 +582,7 @@ __device__ __forceinline__ void stage_set(uint8_t *blk, int row, int i, int w, i
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d)
+__global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d, int32_t e_begin)
 {
     __shared__ int32_t cnt[kInitWarps][64];
     __shared__ long long part_obj[kInitWarps];
@@ -438,7 +595,7 @@ __global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d)
     uint32_t *stage_w = stage_dyn + wid * blk_words;
     uint8_t *stage = reinterpret_cast<uint8_t *>(stage_w);
     long long obj = 0;
-    for (int64_t e0 = ((int64_t)blockIdx.x * kInitWarps + wid) * 32; e0 < d.m; e0 += warps * 32) {
+    for (int64_t e0 = e_begin + ((int64_t)blockIdx.x * kInitWarps + wid) * 32; e0 < d.m; e0 += warps * 32) {
         const int32_t rows = (int32_t)min((int64_t)32, (int64_t)d.m - e0);
         for (int i = lane; i < blk_words; i += 32) stage_w[i] = 0;
         __syncwarp();
@@ -552,6 +709,57 @@ __global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d)
     }
 }
 
+// The nets of at least kBigNet pins, stored first in internal order (the prefix [0, m_big),
+// rounded up to whole 32-net groups), one CTA per net: k_init_nets would give all of them to
+// the first few warps.  Same results as k_init_nets for these nets (the narrow row of a net in
+// the wide table is written as zeros).
+template <typename Rec>
+__global__ void __launch_bounds__(256) k_init_big(Dev d, int32_t m_big)
+{
+    __shared__ int32_t cnt[64];
+    const int lane = threadIdx.x & 31;
+    const int32_t narrow_max = d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff);
+    const int w = d.phi_w, wb = d.k * d.phi_w;
+    long long obj = 0;
+    for (int64_t e = blockIdx.x; e < m_big; e += gridDim.x) {
+        if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int32_t b = d.net_off[e], sz = d.net_off[e + 1] - b;
+        for (int32_t j0 = 0; j0 < sz; j0 += blockDim.x) {
+            const int32_t j = j0 + threadIdx.x;
+            const bool act = j < sz;
+            const unsigned mask = __ballot_sync(kFull, act);
+            if (act) {
+                const int blk = d.part[d.pins[b + j]];
+                const unsigned peers = __match_any_sync(mask, blk);
+                if (lane == __ffs(peers) - 1) atomicAdd(&cnt[blk], (int)__popc(peers));
+            }
+        }
+        __syncthreads();
+        const bool wide = d.widx != nullptr && sz > narrow_max;
+        uint8_t *row = reinterpret_cast<uint8_t *>(d.phi) + e * (int64_t)wb;
+        for (int i = threadIdx.x; i < d.k; i += blockDim.x) {
+            stage_set(row, 0, i, w, wb, wide ? 0 : cnt[i]);
+            if (wide) d.phi_wide[(int64_t)d.widx[e] * d.k + i] = cnt[i];
+        }
+        if (threadIdx.x < 32) {
+            const unsigned lo_lam = __ballot_sync(kFull, lane < d.k && cnt[lane] > 0);
+            const unsigned lo_s1 = __ballot_sync(kFull, lane < d.k && cnt[lane] == 1);
+            const unsigned hi_lam = __ballot_sync(kFull, lane + 32 < d.k && cnt[lane + 32] > 0);
+            const unsigned hi_s1 = __ballot_sync(kFull, lane + 32 < d.k && cnt[lane + 32] == 1);
+            if (lane == 0) {
+                const int32_t wv = d.nw ? d.nw[e] : 1;
+                write_record<Rec>(d, e, (uint64_t)lo_lam | ((uint64_t)hi_lam << 32),
+                                  (uint64_t)lo_s1 | ((uint64_t)hi_s1 << 32), wv | (wide ? (int32_t)kWideFlag : 0));
+                const int lambda = __popc(lo_lam) + __popc(hi_lam);
+                if (lambda > 0) obj += (long long)(lambda - 1) * wv;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && obj) atomicAdd(reinterpret_cast<unsigned long long *>(d.obj), (unsigned long long)obj);
+}
+
 // ------------------------------------------------------------------ getters
 __global__ void k_obj_from_phi(Dev d, unsigned long long *out)
 {
@@ -569,12 +777,18 @@ __global__ void k_obj_from_phi(Dev d, unsigned long long *out)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, (unsigned long long)s);
 }
 
+// the per-net getters and the checkpoint take nets in input order
+__device__ __forceinline__ int32_t internal_net(const Dev &d, int32_t e)
+{
+    return d.net_perm ? d.net_perm[e] : e;
+}
+
 __global__ void k_widen_phi(Dev d, int32_t *out)
 {
     const int64_t total = (int64_t)d.m * d.k;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = (int32_t)(x / d.k), i = (int32_t)(x % d.k);
+        const int32_t e = internal_net(d, (int32_t)(x / d.k)), i = (int32_t)(x % d.k);
         const int32_t size = d.net_off[e + 1] - d.net_off[e];
         const bool wide = d.widx != nullptr && size > (d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff));
         out[x] = phi_get(d, e, i, wide, wide ? d.widx[e] : 0);
@@ -586,7 +800,7 @@ __global__ void k_get_lambda(Dev d, uint64_t *out)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
          e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = (uint64_t)reinterpret_cast<const Rec *>(d.rec)[e].lam;
+        out[e] = (uint64_t)reinterpret_cast<const Rec *>(d.rec)[internal_net(d, (int32_t)e)].lam;
 }
 
 // move stamps of the records
@@ -596,7 +810,7 @@ __global__ void k_export_moved(Dev d, int32_t r, int32_t first, uint8_t *out)
     const Rec *recs = reinterpret_cast<const Rec *>(d.rec);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
          e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = (!first && moved_in_prev_round(recs[e].mv, r)) ? 1 : 0;
+        out[e] = (!first && moved_in_prev_round(recs[internal_net(d, (int32_t)e)].mv, r)) ? 1 : 0;
 }
 
 template <typename Rec>
@@ -605,7 +819,7 @@ __global__ void k_import_moved(Dev d, int32_t r, const uint8_t *flags)
     Rec *recs = reinterpret_cast<Rec *>(d.rec);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < d.m;
          e += (int64_t)gridDim.x * blockDim.x)
-        if (flags[e]) recs[e].mv = (r - 1) * 2;   // last move in round r-1
+        if (flags[e]) recs[internal_net(d, (int32_t)e)].mv = (r - 1) * 2;   // last move in round r-1
 }
 
 __global__ void k_set_round_state(int32_t *rs, int32_t r, int32_t started)
@@ -637,6 +851,7 @@ cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
 {
     *p = nullptr;
     if (count < 1) count = 1;
+    if (h->n_allocs >= hgp_handle::kMaxAllocs) return cudaErrorMemoryAllocation;
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
     if (e != cudaSuccess) {
@@ -670,14 +885,23 @@ int init_state(hgp_handle *h)
     if (d.phi_wide && h->n_wide > 0) CK(cudaMemsetAsync(d.phi_wide, 0, sizeof(int32_t) * (size_t)h->n_wide * d.k, st));
     k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
     CK(cudaGetLastError());
-    const int g = grid_for(((int64_t)d.m + 31) / 32 * 32, kInitWarps * 32, 152 * 16);
-    const int smem = kInitWarps * (32 * d.k * d.phi_w + 15) / 16 * 16;
-    if (d.k <= 32) {
-        cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d); h->launches++;
-    } else {
-        cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d); h->launches++;
+    const int32_t e_begin = h->m_big32;
+    if (e_begin > 0) {
+        const int gb = e_begin < 152 * 16 ? e_begin : 152 * 16;
+        if (d.k <= 32) k_init_big<Rec16><<<gb, 256, 0, st>>>(d, e_begin);
+        else k_init_big<Rec32><<<gb, 256, 0, st>>>(d, e_begin);
+        h->launches++;
+    }
+    if (d.m > e_begin) {
+        const int g = grid_for(((int64_t)d.m - e_begin + 31) / 32 * 32, kInitWarps * 32, 152 * 16);
+        const int smem = kInitWarps * (32 * d.k * d.phi_w + 15) / 16 * 16;
+        if (d.k <= 32) {
+            cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
+        } else {
+            cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
+        }
     }
     CK(cudaGetLastError());
     h->next_round = 0;
@@ -723,6 +947,13 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     };
     Dev &d = h->d;
     cudaGetDevice(&h->device);
+    auto release = [&](void *ptr) {   // frees one of the handle's allocations before the end
+        for (int i = 0; i < h->n_allocs; ++i)
+            if (h->allocs[i] == ptr) {
+                cudaFree(h->allocs[i]);
+                h->allocs[i] = nullptr;
+            }
+    };
     if (o.cuda_stream) {
         h->stream = (cudaStream_t)o.cuda_stream;
     } else {
@@ -803,15 +1034,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     const int32_t max_size = host_err[1];
 
-    // ---- Phi width chosen by the largest net: 1 byte if every net fits, else 2 bytes; nets
-    // beyond the entry's range keep int32 rows in the wide table
-    int w = o.phi_width;
-    if (w == 0) w = max_size <= 255 ? 1 : 2;
-    d.phi_w = w;
-    const int32_t narrow_max = w == 1 ? 255 : (w == 2 ? 65535 : 0x7fffffff);
-
     // ---- scan scratch (shared by the scans below)
-    const int64_t scan_count = ((int64_t)(n > m ? n : m) + 1);
+    const int64_t nr_ctas = m > 0 ? (m + 2047) / 2048 < 1216 ? (m + 2047) / 2048 : 1216 : 0;
+    const int64_t scan_count = std::max((int64_t)(n > m ? n : m) + 1, kNrRanks * nr_ctas + 1);
     const int64_t nb = (scan_count + kScanChunk - 1) / kScanChunk;
     int32_t *block_sums = nullptr;
     CKF(dalloc(h, &block_sums, nb + 1));
@@ -824,8 +1049,57 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         return cudaGetLastError();
     };
 
-    // ---- wide nets
+    // ---- internal net order (largest size class first); the input-order arrays are released
     CKF(dalloc(h, &tmp, (int64_t)(n > m ? n : m) + 1));
+    const bool reorder = m > 0 && !(o.debug & 8) && (m >= kReorderMinNets || (o.debug & 4));
+    int32_t p_big = 0;   // pins of the large-net prefix
+    if (reorder) {
+        const int32_t per_cta = (int32_t)((m + nr_ctas - 1) / nr_ctas);
+        const int32_t nslots = (int32_t)(kNrRanks * nr_ctas);
+        int32_t *cnt = nullptr, *perm = nullptr, *off_int = nullptr, *pins_int = nullptr, *nw_int = nullptr;
+        CKF(cudaMallocAsync(reinterpret_cast<void **>(&cnt), sizeof(int32_t) * (2 * (size_t)nslots + 1), st));
+        int32_t *base = cnt + nslots;
+        CKF(dalloc(h, &perm, m));
+        CKF(dalloc(h, &off_int, (int64_t)m + 1));
+        if (P) CKF(dalloc(h, &pins_int, P));
+        if (nw_d) CKF(dalloc(h, &nw_int, m));
+        k_nr_count<<<(unsigned)nr_ctas, kNrThreads, 0, st>>>(net_off, m, per_cta, cnt); h->launches++;
+        CKF(scan(cnt, base, nslots));
+        int big_rank = 0;   // first rank of the nets below kBigNet pins
+        while (((int64_t)1 << (31 - big_rank)) >= kBigNet) ++big_rank;
+        int32_t mb = 0;
+        CKF(cudaMemcpyAsync(&mb, base + (int64_t)big_rank * nr_ctas, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CKF(cudaStreamSynchronize(st));
+        k_nr_place<<<(unsigned)nr_ctas, kNrThreads, 0, st>>>(net_off, m, per_cta, base, perm, tmp); h->launches++;
+        CKF(scan(tmp, off_int, m));   // sizes in internal order -> offsets (off_int[m] = P)
+        k_nr_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, nw_d, m, perm, off_int,
+                                                                  pins_int, nw_int); h->launches++;
+        CKF(cudaGetLastError());
+        CKF(cudaFreeAsync(cnt, st));
+        CKF(cudaMemcpyAsync(&p_big, off_int + mb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CKF(cudaStreamSynchronize(st));
+        h->m_big = mb;
+        h->m_big32 = (int32_t)std::min((int64_t)m, ((int64_t)mb + 31) / 32 * 32);
+        release(net_off);
+        release(pins_d);
+        if (nw_d) release(nw_d);
+        net_off = off_int;
+        pins_d = pins_int;
+        nw_d = nw_int;
+        d.net_off = net_off;
+        d.pins = pins_d;
+        d.nw = nw_d;
+        d.net_perm = perm;
+    }
+
+    // ---- Phi width chosen by the largest net: 1 byte if every net fits, else 2 bytes; nets
+    // beyond the entry's range keep int32 rows in the wide table
+    int w = o.phi_width;
+    if (w == 0) w = max_size <= 255 ? 1 : 2;
+    d.phi_w = w;
+    const int32_t narrow_max = w == 1 ? 255 : (w == 2 ? 65535 : 0x7fffffff);
+
+    // ---- wide nets
     if (max_size > narrow_max) {
         int32_t *widx = nullptr;
         CKF(dalloc(h, &widx, (int64_t)m + 1));
@@ -859,7 +1133,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         while (bshift > kTpMinShift && buckets(bshift) < kTpMinCtas) --bshift;
         while (buckets(bshift) > kTpMaxBuckets) ++bshift;
         const int32_t nbk = (int32_t)buckets(bshift);
-        int64_t per_cta = ((int64_t)m + kTpMinCtas - 1) / kTpMinCtas;
+        const int32_t e_begin = h->m_big;   // the large-net prefix goes to k_tp_scatter_big
+        const int64_t m_rest = (int64_t)m - e_begin;
+        int64_t per_cta = (m_rest + kTpMinCtas - 1) / kTpMinCtas;
         per_cta = per_cta < 512 ? 512 : (per_cta > kTpNetsPerCta ? kTpNetsPerCta : per_cta);
         int32_t *bk = nullptr;           // counts [nbk + 1], offsets [nbk + 1], cursors [nbk]
         unsigned long long *pairs = nullptr;
@@ -870,9 +1146,15 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt); h->launches++;
         CKF(scan(bk_cnt, bk_off, nbk));
         CKF(cudaMemcpyAsync(bk_cur, bk_off, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st));
-        const int64_t sc = ((int64_t)m + per_cta - 1) / per_cta;
-        k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, bshift, nbk, narrow_max, (int32_t)per_cta,
-                                                   bk_cur, pairs); h->launches++;
+        const int64_t sc = (m_rest + per_cta - 1) / per_cta;
+        if (e_begin > 0 && p_big > 0) {
+            k_tp_scatter_big<<<(unsigned)((p_big + kTpBigChunk - 1) / kTpBigChunk), 256, 0, st>>>(
+                net_off, pins_d, e_begin, bshift, nbk, narrow_max, bk_cur, pairs); h->launches++;
+        }
+        if (sc > 0) {
+            k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, e_begin, bshift, nbk, narrow_max,
+                                                       (int32_t)per_cta, bk_cur, pairs); h->launches++;
+        }
         if (bshift <= kTpSmemShift) {
             const int smem = (int)(sizeof(int32_t) << bshift);
             cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -30,6 +30,7 @@ _TILE = 2048
 _BINS = 4096
 _ALLOC_SLACK = 64 << 20
 _DIRECT_TRANSPOSE_MAX_N = 1 << 21      # larger instances are transposed through bucketed pairs
+_REORDER_MIN_NETS = 1 << 20            # from this many nets the handle keeps nets in internal order
 
 
 def estimate_device_bytes(n: int, m: int, pins: int, k: int, max_net_size: int,
@@ -48,6 +49,8 @@ def estimate_device_bytes(n: int, m: int, pins: int, k: int, max_net_size: int,
     b += n_ranges * _RANGE * 9 + n_ranges * (subrounds + 1) * 2 + n_ranges * 4   # sub-round lists, candidates
     b += k * _BINS * 8 + k * n_tiles * 8 + 64 * 40             # approval scratch
     b += (max(n, m) + 1) * 4 + n * 4 + (m + 1) * 8            # creation temporaries
+    if m >= _REORDER_MIN_NETS:
+        b += m * 4                                            # internal net order: input -> internal ids
     if n > _DIRECT_TRANSPOSE_MAX_N:
         b += pins * 8 + 3 * 4096 * 4                          # bucketed transpose: (vertex, net) pairs
     # each of the ~32 device allocations is rounded up to the allocator's 2 MiB granularity
