@@ -70,7 +70,8 @@ typedef struct {
                             otherwise used above 2^21 vertices); bit 2: store the nets in
                             internal order (by size class, largest first, so that the records
                             of the largest nets share L2 lines) whatever the size (it is
-                            otherwise used from 2^20 nets on); bit 3: keep the input net order.
+                            otherwise used from 2^20 nets on when the largest net has at least
+                            8 times the average net size); bit 3: keep the input net order.
                             Results do not depend on the order; per-net outputs and
                             checkpoints always use input net ids [0] */
     int32_t graph;       /* 1: hgp_refine captures its launches as a CUDA graph on the first call

@@ -317,9 +317,12 @@ __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, c
 // an exclusive scan into vtx_off, then every pin takes the next slot of its vertex (warp per
 // net) and stores the net id with the wide flag.
 constexpr int32_t kTpDirectMaxN = 1 << 21;
-// nets are stored in internal (size class) order from this many nets on: below it their records
-// fit in L2 whatever the order
+// nets are stored in internal (size class) order from this many nets on, when the largest net
+// has at least kReorderSkew times the average size: below that count their records fit in L2
+// whatever the order, and without large nets no small set of records takes most gathers (on
+// near-uniform sizes the relabelling only adds creation time)
 constexpr int32_t kReorderMinNets = 1 << 20;
+constexpr int64_t kReorderSkew = 8;
 // in internal order, nets of at least this many pins (a prefix) get their own CTAs at creation
 // and initialisation (a power of two: size classes are powers of two)
 constexpr int32_t kBigNet = 256;
@@ -1051,7 +1054,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
 
     // ---- internal net order (largest size class first); the input-order arrays are released
     CKF(dalloc(h, &tmp, (int64_t)(n > m ? n : m) + 1));
-    const bool reorder = m > 0 && !(o.debug & 8) && (m >= kReorderMinNets || (o.debug & 4));
+    const int64_t avg_size = m > 0 ? (P + m - 1) / m : 0;
+    const bool reorder = m > 0 && !(o.debug & 8) &&
+                         ((o.debug & 4) || (m >= kReorderMinNets && max_size >= kReorderSkew * avg_size));
     int32_t p_big = 0;   // pins of the large-net prefix
     if (reorder) {
         const int32_t per_cta = (int32_t)((m + nr_ctas - 1) / nr_ctas);

@@ -49,7 +49,7 @@ def estimate_device_bytes(n: int, m: int, pins: int, k: int, max_net_size: int,
     b += n_ranges * _RANGE * 9 + n_ranges * (subrounds + 1) * 2 + n_ranges * 4   # sub-round lists, candidates
     b += k * _BINS * 8 + k * n_tiles * 8 + 64 * 40             # approval scratch
     b += (max(n, m) + 1) * 4 + n * 4 + (m + 1) * 8            # creation temporaries
-    if m >= _REORDER_MIN_NETS:
+    if m >= _REORDER_MIN_NETS and max_net_size >= 8 * -(-pins // max(m, 1)):
         b += m * 4                                            # internal net order: input -> internal ids
     if n > _DIRECT_TRANSPOSE_MAX_N:
         b += pins * 8 + 3 * 4096 * 4                          # bucketed transpose: (vertex, net) pairs
