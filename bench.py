@@ -174,10 +174,20 @@ def algorithmic_bytes(hg, info, stats, S):
     return {"gain": gain_total / launches, "apply": apply_total / launches}
 
 
+def source_sha256() -> str:
+    """sha256 of the sources the profiled kernels and their data layout come from."""
+    csrc = os.path.join(ROOT, "paper_2010_10272_gb300", "csrc")
+    d = hashlib.sha256()
+    for f in ("hgp_refine.cu", "hgp_setup.cu"):
+        d.update(open(os.path.join(csrc, f), "rb").read())
+    return d.hexdigest()
+
+
 def traffic_from_profile(kernel: str, workload: str, phi_width: int):
     """dram bytes per launch recorded in profiles/ for `kernel` on `workload`, if the kernel
-    source has not changed since the capture (its sha256 is stored with the figure) and the
-    capture used the same Phi entry width."""
+    sources have not changed since the capture (the sha256 of hgp_refine.cu followed by
+    hgp_setup.cu, which decides the data layout, is stored with the figure) and the capture
+    used the same Phi entry width."""
     path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -186,12 +196,10 @@ def traffic_from_profile(kernel: str, workload: str, phi_width: int):
     if not pw or int(pw.group(1)) != phi_width:
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    h = re.search(r"source_sha256[^:\n]*:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    src = os.path.join(ROOT, "paper_2010_10272_gb300", "csrc", "hgp_refine.cu")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if cur != h.group(1):
+    if source_sha256() != h.group(1):
         return None
     return float(m.group(1))
 
