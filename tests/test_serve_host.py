@@ -108,3 +108,16 @@ def test_footprint_grows_with_the_instance(server_cls):
     assert a < b < c < d
     # above 2^21 vertices the transpose's pairs (8 bytes per pin) are part of the peak
     assert c >= 21_000_000 * 8
+
+
+def test_footprint_counts_the_internal_net_order(server_cls):
+    """From 2^20 nets with skewed sizes (largest net >= 8x the average) the handle keeps an
+    input -> internal net map (4 bytes per net); near-uniform sizes or fewer nets do not."""
+    serve = server_cls
+    m = 1 << 20
+    skewed = serve.estimate_device_bytes(m, m, 7 * m, 8, 200, False, False)     # 1-byte Phi in both
+    uniform = serve.estimate_device_bytes(m, m, 7 * m, 8, 50, False, False)
+    assert skewed - uniform >= int(m * 4 * 1.05) - 1
+    below = serve.estimate_device_bytes(m - 1, m - 1, 7 * (m - 1), 8, 200, False, False)
+    below_u = serve.estimate_device_bytes(m - 1, m - 1, 7 * (m - 1), 8, 50, False, False)
+    assert below == below_u
