@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
         return os.environ["HGP_ORACLE_LIB"]
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC,
+                               "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -72,6 +73,8 @@ def _load():
         for name in ("oracle_get_partition", "oracle_get_block_weights", "oracle_get_phi"):
             getattr(lib, name).argtypes = [P, P]
         lib.oracle_set_variant.argtypes = [P, i32, i32]
+        lib.oracle_set_threads.argtypes = [P, i32]
+        lib.oracle_get_phi_rows.argtypes = [P, i32, i32, P]
         lib.oracle_contract.restype = ctypes.c_int
         lib.oracle_contract.argtypes = [i32, i32, P, P, P, P, P, ctypes.POINTER(P)]
         lib.oracle_coarse_destroy.argtypes = [P]
@@ -113,7 +116,7 @@ class Oracle:
 
     def __init__(self, n, m, net_off, pins, k, eps, part, vertex_w=None, net_w=None,
                  subrounds: int = 4, seed: int = 0, balance_moves: bool = False,
-                 revert_negative: bool = False):
+                 revert_negative: bool = False, threads: int = 1):
         lib = _load()
         self._lib = lib
         self.n, self.m, self.k = int(n), int(m), int(k)
@@ -127,6 +130,7 @@ class Oracle:
             raise ValueError("oracle_create rejected the input")
         self._keep = None
         lib.oracle_set_variant(self._h, int(bool(balance_moves)), int(bool(revert_negative)))
+        lib.oracle_set_threads(self._h, int(threads))
 
     @classmethod
     def from_hypergraph(cls, hg, subrounds: int = 4, seed: int = 0, part=None, **variant):
@@ -227,6 +231,15 @@ class Oracle:
     def phi(self) -> np.ndarray:
         out = np.zeros((self.m, self.k), dtype=np.int64)
         self._lib.oracle_get_phi(self._h, _ptr(out))
+        return out
+
+    def phi_rows(self, e0: int, e1: int) -> np.ndarray:
+        """Rows e0 <= e < e1 of Phi as int32 [e1 - e0, k] (for instances too large to copy whole)."""
+        e0, e1 = int(e0), int(e1)
+        if not 0 <= e0 <= e1 <= self.m:
+            raise ValueError("row range outside [0, m]")
+        out = np.zeros((e1 - e0, self.k), dtype=np.int32)
+        self._lib.oracle_get_phi_rows(self._h, e0, e1, _ptr(out))
         return out
 
 

@@ -7,8 +7,17 @@
  * the benchmark may load it.  It shares no code, header, table or helper with the CUDA
  * library, and it never reads anything the CUDA library produced.
  *
- * Everything is integer arithmetic (int64 pin counts, weights and gains), so results are
- * exact and must agree bit for bit with the device path.
+ * Everything is integer arithmetic, so results are exact and must agree bit for bit with the
+ * device path.  Weights, gains and block weights are int64.  Pin counts Phi(e, i) are int32:
+ * 0 <= Phi(e, i) <= |e| <= P < 2^31 (the input bound), so every count is held exactly, and
+ * the table of the largest workloads (m * k entries) takes half the host memory.
+ *
+ * Threads (oracle_set_threads, default 1): three loops whose items are independent may be
+ * split into contiguous slices evaluated by separate threads: the eligibility of each vertex
+ * (a function of the previous round's moved nets), the best move of each vertex (a function
+ * of the state frozen at the start of the sub-round alone, Sec. 6 read synchronously), and
+ * the objective (an integer sum of per-net terms).  Approval and application stay
+ * sequential.  The results do not depend on the thread count.
  *
  * Definitions followed (paper Sec. 2 "Preliminaries"):
  *   H = (V, E, c, omega), positive integer weights; I(v) the incident nets of v.
@@ -40,12 +49,13 @@
  *   to 1 gives exactly this gain).  After the sub-round, every move whose attributed gain is
  *   negative is undone.  A reverted move still counts as a move for eligibility.
  *
- * Build: gcc -O2 -shared -fPIC -o liboracle.so hgp_oracle.c
+ * Build: gcc -O2 -shared -fPIC -pthread -o liboracle.so hgp_oracle.c -lm
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
 
 typedef struct {
     /* hypergraph (copied) */
@@ -62,7 +72,7 @@ typedef struct {
     uint64_t seed;
     /* state */
     int32_t *part;         /* Pi */
-    int64_t *phi;          /* [m*k] Phi(e,i) */
+    int32_t *phi;          /* [m*k] Phi(e,i) */
     int64_t *bw;           /* [k]  block weights c(V_i) */
     int64_t round;         /* global round counter */
     int32_t balance_moves; /* variant: zero-gain moves that improve the balance (Sec. 6) */
@@ -78,6 +88,7 @@ typedef struct {
     int32_t *from;         /* [n]  block an approved vertex left */
     int64_t *attr;         /* [n]  attributed gain of an approved move */
     uint8_t *selected;     /* [n]  rebalancing: passed the source-side selection */
+    int32_t threads;       /* threads for the per-vertex candidate loop (1 = sequential) */
 } oracle_t;
 
 /* Per-round statistics, in this order: objective after the round, number of candidates,
@@ -107,16 +118,68 @@ int32_t oracle_subround_of(uint64_t seed, int64_t round, int32_t u, int32_t S)
     return (int32_t)(z % (uint64_t)S);
 }
 
-static int64_t objective_from_phi(const oracle_t *o)
+/* Runs fn(ctx, lo, hi, &acc) over `threads` contiguous slices of [0, count) and returns the
+ * sum of the slices' acc.  Used only where every item's result is independent of the others
+ * (an integer sum does not depend on how it is split); a slice whose thread cannot be started
+ * runs in the calling thread. */
+typedef void (*slice_fn)(void *ctx, int64_t lo, int64_t hi, int64_t *acc);
+typedef struct {
+    slice_fn fn;
+    void *ctx;
+    int64_t lo, hi, acc;
+} slice_t;
+
+static void *slice_worker(void *arg)
 {
-    int64_t obj = 0;
-    for (int32_t e = 0; e < o->m; ++e) {
+    slice_t *sl = (slice_t *)arg;
+    sl->acc = 0;
+    sl->fn(sl->ctx, sl->lo, sl->hi, &sl->acc);
+    return NULL;
+}
+
+static int64_t for_slices(int32_t threads, int64_t count, slice_fn fn, void *ctx)
+{
+    enum { MAX_THREADS = 256 };
+    const int32_t T = threads < 1 ? 1 : (threads > MAX_THREADS ? MAX_THREADS : threads);
+    if (T == 1 || count < 4096) {
+        int64_t acc = 0;
+        fn(ctx, 0, count, &acc);
+        return acc;
+    }
+    pthread_t th[MAX_THREADS];
+    slice_t sl[MAX_THREADS];
+    int started[MAX_THREADS];
+    for (int32_t t = 0; t < T; ++t) {
+        sl[t].fn = fn;
+        sl[t].ctx = ctx;
+        sl[t].lo = count * t / T;
+        sl[t].hi = count * (t + 1) / T;
+        started[t] = pthread_create(&th[t], NULL, slice_worker, &sl[t]) == 0;
+        if (!started[t]) slice_worker(&sl[t]);
+    }
+    int64_t total = 0;
+    for (int32_t t = 0; t < T; ++t) {
+        if (started[t]) pthread_join(th[t], NULL);
+        total += sl[t].acc;
+    }
+    return total;
+}
+
+/* (lambda(e) - 1) * omega(e) summed over the nets lo <= e < hi (an empty net counts 0). */
+static void objective_slice(void *ctx, int64_t lo, int64_t hi, int64_t *acc)
+{
+    const oracle_t *o = (const oracle_t *)ctx;
+    for (int64_t e = lo; e < hi; ++e) {
         int64_t lambda = 0;
         for (int32_t i = 0; i < o->k; ++i)
-            if (o->phi[(int64_t)e * o->k + i] > 0) lambda++;
-        if (lambda > 0) obj += (lambda - 1) * o->nw[e];
+            if (o->phi[e * o->k + i] > 0) lambda++;
+        if (lambda > 0) *acc += (lambda - 1) * o->nw[e];
     }
-    return obj;
+}
+
+static int64_t objective_from_phi(const oracle_t *o)
+{
+    return for_slices(o->threads, o->m, objective_slice, (void *)o);
 }
 
 void oracle_destroy(oracle_t *o)
@@ -147,7 +210,7 @@ oracle_t *oracle_create(int32_t n, int32_t m, const int64_t *net_off, const int3
     o->vtx_off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     o->inc = (int32_t *)malloc(sizeof(int32_t) * ((size_t)P + 1));
     o->part = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
-    o->phi = (int64_t *)calloc((size_t)m * k + 1, sizeof(int64_t));
+    o->phi = (int32_t *)calloc((size_t)m * k + 1, sizeof(int32_t));
     o->bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
     o->moved_prev = (uint8_t *)calloc((size_t)m + 1, 1);
     o->moved_cur = (uint8_t *)calloc((size_t)m + 1, 1);
@@ -195,6 +258,7 @@ oracle_t *oracle_create(int32_t n, int32_t m, const int64_t *net_off, const int3
     o->lmax = oracle_lmax(total, k, eps);
     o->round = 0;
     o->all_eligible = 1;
+    o->threads = 1;
     return o;
 }
 
@@ -274,6 +338,52 @@ void oracle_candidates(const oracle_t *o, int32_t s, int32_t *target, int64_t *g
     }
 }
 
+/* Best moves (Sec. 6) of the vertices lo <= u < hi that are eligible and active in sub-round s
+ * of round r, against the current (frozen) state; cand_t[u] = -1 for the others. */
+typedef struct {
+    oracle_t *o;
+    const uint8_t *elig;
+    int64_t r;
+    int32_t s;
+} cand_ctx_t;
+
+static void candidates_slice(void *ctx, int64_t lo, int64_t hi, int64_t *acc)
+{
+    cand_ctx_t *c = (cand_ctx_t *)ctx;
+    oracle_t *o = c->o;
+    for (int64_t u = lo; u < hi; ++u) {
+        o->cand_t[u] = -1;
+        o->cand_g[u] = 0;
+        if (!c->elig[u] || oracle_subround_of(o->seed, c->r, (int32_t)u, o->subrounds) != c->s) continue;
+        best_move(o, (int32_t)u, &o->cand_t[u], &o->cand_g[u]);
+        if (o->cand_t[u] >= 0) (*acc)++;
+    }
+}
+
+static void sub_round_candidates(oracle_t *o, const uint8_t *elig, int64_t r, int32_t s)
+{
+    cand_ctx_t c = {o, elig, r, s};
+    for_slices(o->threads, o->n, candidates_slice, &c);
+}
+
+/* elig[u] = eligible(u) for lo <= u < hi; acc counts the eligible vertices. */
+typedef struct {
+    const oracle_t *o;
+    uint8_t *elig;
+} elig_ctx_t;
+
+static void eligible_slice(void *ctx, int64_t lo, int64_t hi, int64_t *acc)
+{
+    elig_ctx_t *c = (elig_ctx_t *)ctx;
+    for (int64_t u = lo; u < hi; ++u) {
+        c->elig[u] = (uint8_t)eligible(c->o, (int32_t)u);
+        *acc += c->elig[u];
+    }
+}
+
+/* Threads used by the candidate step of oracle_refine (1 = sequential; results identical). */
+void oracle_set_threads(oracle_t *o, int32_t threads) { o->threads = threads < 1 ? 1 : threads; }
+
 /* Moves u from its block to t: partition, block weights, Phi, and (mark != 0) the moved-net
  * marks that decide the next LP round's eligibility. */
 static void move_vertex_marked(oracle_t *o, int32_t u, int32_t t, int mark)
@@ -308,18 +418,17 @@ int oracle_refine(oracle_t *o, int32_t rounds, int64_t *stats, int64_t *moves,
         /* eligibility is fixed for the whole round: it depends only on the previous round */
         uint8_t *elig_copy = (uint8_t *)malloc((size_t)n + 1);
         if (!elig_copy) return -1;
-        for (int32_t u = 0; u < n; ++u) { elig_copy[u] = (uint8_t)eligible(o, u); n_elig += elig_copy[u]; }
+        {
+            elig_ctx_t c = {o, elig_copy};
+            n_elig = for_slices(o->threads, n, eligible_slice, &c);
+        }
 
         for (int32_t s = 0; s < S; ++s) {
             /* (1) candidates against the state frozen at the start of the sub-round */
+            sub_round_candidates(o, elig_copy, r, s);
             int32_t cnt = 0;
-            for (int32_t u = 0; u < n; ++u) {
-                o->cand_t[u] = -1;
-                o->cand_g[u] = 0;
-                if (!elig_copy[u] || oracle_subround_of(o->seed, r, u, S) != s) continue;
-                best_move(o, u, &o->cand_t[u], &o->cand_g[u]);
+            for (int32_t u = 0; u < n; ++u)
                 if (o->cand_t[u] >= 0) { o->order[cnt++] = u; n_cand++; }
-            }
             /* (2) approval per target block: (gain desc, id asc), inclusive prefix sums */
             g_sort_ctx = o;
             qsort(o->order, (size_t)cnt, sizeof(int32_t), by_gain_desc_id_asc);
@@ -511,7 +620,14 @@ void oracle_get_block_weights(const oracle_t *o, int64_t *out)
 
 void oracle_get_phi(const oracle_t *o, int64_t *out)
 {
-    memcpy(out, o->phi, sizeof(int64_t) * (size_t)o->m * (size_t)o->k);
+    const int64_t cnt = (int64_t)o->m * o->k;
+    for (int64_t x = 0; x < cnt; ++x) out[x] = o->phi[x];
+}
+
+/* Rows e0 <= e < e1 of Phi into out[(e1 - e0) * k] (for instances too large to copy whole). */
+void oracle_get_phi_rows(const oracle_t *o, int32_t e0, int32_t e1, int32_t *out)
+{
+    memcpy(out, o->phi + (int64_t)e0 * o->k, sizeof(int32_t) * (size_t)(e1 - e0) * (size_t)o->k);
 }
 
 /* Candidates of round 0, sub-round s, for a sample of vertices, straight from the input
@@ -582,11 +698,11 @@ int oracle_sample_candidates(int32_t n, int32_t m, const int64_t *net_off, const
 int oracle_exact_gains(const oracle_t *o, int32_t count, const int32_t *moves, int64_t *gain)
 {
     const int32_t n = o->n, m = o->m, k = o->k;
-    int64_t *phi = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m * k + 1));
+    int32_t *phi = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m * k + 1));
     int32_t *part = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
     uint8_t *seen = (uint8_t *)calloc((size_t)n + 1, 1);
     if (!phi || !part || !seen) { free(phi); free(part); free(seen); return -1; }
-    memcpy(phi, o->phi, sizeof(int64_t) * (size_t)m * k);
+    memcpy(phi, o->phi, sizeof(int32_t) * (size_t)m * k);
     memcpy(part, o->part, sizeof(int32_t) * (size_t)n);
     int rc = 0;
     for (int32_t j = 0; j < count && rc == 0; ++j) {

@@ -98,6 +98,48 @@ class Tiny:
         return out
 
 
+def eligible_after(t: Tiny, moved_prev: Optional[set]) -> set:
+    """Eligible vertices of a round (Sec. 6): every vertex in the first round (moved_prev is
+    None), otherwise the vertices that share a net with a vertex moved in the round before
+    (a moved vertex with at least one net is its own neighbour)."""
+    if moved_prev is None:
+        return set(range(t.n))
+    elig = set()
+    for v in moved_prev:
+        if t.inc[v]:
+            elig |= t.neighbours(v)
+    return elig
+
+
+def candidates(t: Tiny, part, elig, r: int, s: int, S: int, seed: int = 0,
+               balance_moves: bool = False) -> Dict[int, tuple]:
+    """{u: (target, gain)} of sub-round s of round r: every eligible vertex active in s picks
+    the block with the largest objective reduction among those with room for it (block
+    weights of `part`), smallest block on ties, if that reduction is positive."""
+    lmax = t.lmax()
+    w = t.block_weights(part)
+    cands: Dict[int, tuple] = {}
+    for u in sorted(elig):
+        if subround(seed, r, u, S) != s:
+            continue
+        best = None
+        for i in range(t.k):
+            if i == part[u]:
+                continue
+            g = t.gain(part, u, i)
+            if g > 0 and w[i] + t.vw[u] <= lmax and (best is None or g > best[1]):
+                best = (i, g)
+        if best is None and balance_moves:
+            # a zero-gain move to a block it leaves more balanced than a: lightest first
+            zs = [i for i in range(t.k) if i != part[u] and t.gain(part, u, i) == 0
+                  and w[i] + t.vw[u] <= lmax and w[i] + t.vw[u] < w[part[u]]]
+            if zs:
+                best = (min(zs, key=lambda i: (w[i], i)), 0)
+        if best is not None:
+            cands[u] = best
+    return cands
+
+
 def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round: int = 0,
               moved_prev: Optional[set] = None, balance_moves: bool = False,
               revert_negative: bool = False, reverted: Optional[list] = None):
@@ -114,38 +156,12 @@ def lp_rounds(t: Tiny, part, rounds: int, S: int = 4, seed: int = 0, start_round
     all_elig = moved_prev is None
     for rr in range(rounds):
         r = start_round + rr
-        if all_elig:
-            elig = set(range(t.n))
-        else:
-            elig = set()
-            for v in moved_prev:
-                # v and its neighbours (vertices sharing a net with v); a vertex without
-                # nets has no neighbours and no net of it was touched
-                if t.inc[v]:
-                    elig |= t.neighbours(v)
+        elig = eligible_after(t, None if all_elig else moved_prev)
         moved_now = set()
         n_cand = n_appr = n_rev = 0
         for s in range(S):
             w = t.block_weights(part)
-            cands: Dict[int, tuple] = {}
-            for u in sorted(elig):
-                if subround(seed, r, u, S) != s:
-                    continue
-                best = None
-                for i in range(t.k):
-                    if i == part[u]:
-                        continue
-                    g = t.gain(part, u, i)
-                    if g > 0 and w[i] + t.vw[u] <= lmax and (best is None or g > best[1]):
-                        best = (i, g)
-                if best is None and balance_moves:
-                    # a zero-gain move to a block it leaves more balanced than a: lightest first
-                    zs = [i for i in range(t.k) if i != part[u] and t.gain(part, u, i) == 0
-                          and w[i] + t.vw[u] <= lmax and w[i] + t.vw[u] < w[part[u]]]
-                    if zs:
-                        best = (min(zs, key=lambda i: (w[i], i)), 0)
-                if best is not None:
-                    cands[u] = best
+            cands = candidates(t, part, elig, r, s, S, seed, balance_moves)
             n_cand += len(cands)
             approved = []
             for blk in range(t.k):

@@ -19,7 +19,7 @@ SRC = os.path.join(ROOT, "oracle", "hgp_oracle.c")
 
 # the pin suites run against each mutant
 PIN_FILES = ("test_oracle_pins.py", "test_oracle_rebalance.py", "test_oracle_exact_gains.py",
-             "test_oracle_contract.py")
+             "test_oracle_contract.py", "test_oracle_candidates.py")
 
 # (name, exact text in the oracle source, replacement)
 MUTANTS = [
@@ -43,10 +43,10 @@ MUTANTS = [
     ("always eligible", "if (o->all_eligible) return 1;", "return 1;"),
     ("never eligible after round 0", "if (o->moved_prev[o->inc[j]]) return 1;", "(void)j;"),
     ("lmax without ceil", "int64_t avg = (total_weight + k - 1) / k;", "int64_t avg = total_weight / k;"),
-    ("objective counts lambda", "if (lambda > 0) obj += (lambda - 1) * o->nw[e];",
-     "if (lambda > 0) obj += lambda * o->nw[e];"),
-    ("objective drops weight", "if (lambda > 0) obj += (lambda - 1) * o->nw[e];",
-     "if (lambda > 0) obj += (lambda - 1);"),
+    ("objective counts lambda", "if (lambda > 0) *acc += (lambda - 1) * o->nw[e];",
+     "if (lambda > 0) *acc += lambda * o->nw[e];"),
+    ("objective drops weight", "if (lambda > 0) *acc += (lambda - 1) * o->nw[e];",
+     "if (lambda > 0) *acc += (lambda - 1);"),
     ("hash shift", "z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;", "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;"),
     ("hash round/vertex swapped", "seed ^ (((uint64_t)round << 32) | (uint64_t)(uint32_t)u)",
      "seed ^ (((uint64_t)u << 32) | (uint64_t)(uint32_t)round)"),
@@ -76,6 +76,19 @@ MUTANTS = [
     ("identical net weights not summed", "wsum[rep[e]] += net_w ? net_w[e] : 1;",
      "if (rep[e] == e) wsum[e] = net_w ? net_w[e] : 1;"),
     ("cluster ids not remapped in order", "c->map[u] = cid[cluster[u]];", "c->map[u] = c->n - 1 - cid[cluster[u]];"),
+    ("candidates ignore eligibility", "if (!eligible(o, u)) continue;", "(void)eligible;"),
+    ("candidates hash the previous round", "if (oracle_subround_of(o->seed, o->round, u, o->subrounds) != s) continue;",
+     "if (oracle_subround_of(o->seed, o->round ? o->round - 1 : 0, u, o->subrounds) != s) continue;"),
+    ("sample b uses Phi==2", "if (phi_row[part[pins[j]]] == 1) b[q] += w;", "if (phi_row[part[pins[j]]] == 2) b[q] += w;"),
+    ("sample p_i drops net weight", "if (phi_row[i] == 0) p[(int64_t)q * k + i] += w;",
+     "if (phi_row[i] == 0) p[(int64_t)q * k + i] += 1;"),
+    ("sample counts only sampled pins", "for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) phi_row[part[pins[j]]]++;",
+     "for (int64_t j = net_off[e]; j < net_off[e + 1]; ++j) if (slot[pins[j]] >= 0) phi_row[part[pins[j]]]++;"),
+    ("sample hashes round 1", "if (oracle_subround_of(seed, 0, u, subrounds) != s) continue;",
+     "if (oracle_subround_of(seed, 1, u, subrounds) != s) continue;"),
+    ("sample capacity ignores c(u)", "if (g > gain[q] && bw[i] + c <= lmax)", "if (g > gain[q] && bw[i] <= lmax)"),
+    ("threaded slices drop the last item", "sl[t].hi = count * (t + 1) / T;",
+     "sl[t].hi = count * (t + 1) / T - (t == T - 1);"),
     ("moves applied before all approvals", "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = 0;",
      "for (int32_t t = 0; t < k; ++t) {\n                int64_t acc = o->bw[t] > o->lmax ? 0 : 0;"),
 ]
@@ -89,7 +102,7 @@ def _run_mutant(name, old, new, workdir):
     c = os.path.join(d, "m.c")
     so = os.path.join(d, "m.so")
     open(c, "w").write(mutated)
-    subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-o", so, c, "-lm"])
+    subprocess.check_call(["gcc", "-O1", "-shared", "-fPIC", "-pthread", "-o", so, c, "-lm"])
     env = dict(os.environ, HGP_ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
                        [os.path.join(ROOT, "tests", f) for f in PIN_FILES],
