@@ -73,7 +73,10 @@ typedef struct {
                             otherwise used from 2^20 nets on when the largest net has at least
                             8 times the average net size); bit 3: keep the input net order.
                             Results do not depend on the order; per-net outputs and
-                            checkpoints always use input net ids [0] */
+                            checkpoints always use input net ids; bit 4 (fault injection,
+                            for tests of the error path): after each hgp_refine the maintained
+                            objective is lowered by one from the host, so that check mode
+                            reports HGP_ERR_INTERNAL [0] */
     int32_t graph;       /* 1: hgp_refine captures its launches as a CUDA graph on the first call
                             with a given round count and replays it afterwards [0]; ignored
                             while profiling is on */
@@ -267,15 +270,18 @@ int hgp_get_launch_count(hgp_handle *h, int64_t *out);
  * its gain or 0.
  *
  *   All arrays are DEVICE pointers owned by the caller: net_offsets int32[m+1] and pins
- *   int32[P] (net -> pins), vtx_offsets int32[n+1] and inc_nets int32[P] (vertex -> incident
- *   nets, the transpose of the first CSR; the caller must pass a consistent pair), vertex_w
- *   int32[n] / net_w int32[m] or NULL for unit weights, part int32[n]; outputs target
- *   int32[n] and gain int64[n].  Work is queued on cuda_stream (NULL = default stream); the
- *   call synchronises that stream once to validate the inputs, then returns with the
- *   computation queued.
+ *   int32[P] (net -> pins, pins strictly increasing inside each net), vtx_offsets int32[n+1]
+ *   and inc_nets int32[P] (vertex -> incident nets, the transpose of the first CSR: vertex v
+ *   lists exactly the nets that have v as a pin, in increasing net id), vertex_w int32[n] /
+ *   net_w int32[m] or NULL for unit weights, part int32[n]; outputs target int32[n] and gain
+ *   int64[n].  Work is queued on cuda_stream (NULL = default stream); the call synchronises
+ *   that stream to validate the inputs, then returns with the computation queued.  It must
+ *   not be called while that stream is being captured (it then returns HGP_ERR_INVALID).
  *   Limit: m <= 262144 nets (2^18); k <= 64; subrounds <= 64.  Larger m returns
- *   HGP_ERR_UNSUPPORTED.  Out-of-range offsets, pins, incident nets, partition entries or
- *   non-positive weights return HGP_ERR_INVALID before any other kernel runs.
+ *   HGP_ERR_UNSUPPORTED.  Out-of-range offsets, pins, incident nets, partition entries,
+ *   non-positive weights, unsorted or repeated pins or nets, and a vertex -> nets CSR that is
+ *   not the transpose of the net -> pins CSR return HGP_ERR_INVALID before the computation
+ *   runs.
  *   Scratch: a fixed 8 MiB device array inside the library, held on every GPU that loads the
  *   library until the process exits.  Its address is looked up on the first call made on
  *   each device (with that device current), so that first call should come before any

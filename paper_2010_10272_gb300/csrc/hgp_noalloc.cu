@@ -11,8 +11,10 @@
 // The scratch array has room for kNoAllocMaxNets nets.  Every GPU that loads the library holds
 // it until the process exits.  Its device address is looked up once per device, on the first
 // call made with that device current; that first call should therefore come before any
-// stream capture.  All calls share the array and it keeps the last call's contents, so calls
-// whose work overlaps on the GPU (on different streams, or from several host threads) race.
+// stream capture.  No call may be made while its stream is being captured (it reads the
+// validation result back and synchronises the stream); such a call returns HGP_ERR_INVALID.
+// All calls share the array and it keeps the last call's contents, so calls whose work
+// overlaps on the GPU (on different streams, or from several host threads) race.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -96,6 +98,48 @@ __global__ void k_na_check(int32_t n, int32_t m, const int32_t *net_off, const i
     }
     for (int64_t j = i0; j < P; j += stride)
         if (pins[j] < 0 || pins[j] >= n || inc[j] < 0 || inc[j] >= m) bad = true;
+    if (bad) atomicOr(err, 1);
+}
+
+// Order checks, warp per list (run after k_na_check has passed, so every index is in range):
+// pins strictly increasing inside each net (this also excludes a pin listed twice), and net
+// ids strictly increasing inside each vertex's list.
+__global__ void k_na_check_order(int32_t n, int32_t m, const int32_t *net_off, const int32_t *pins,
+                                 const int32_t *vtx_off, const int32_t *inc, int32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    bool bad = false;
+    for (int64_t e = w0; e < m; e += warps)
+        for (int32_t j = net_off[e] + 1 + lane; j < net_off[e + 1]; j += 32)
+            if (pins[j] <= pins[j - 1]) bad = true;
+    for (int64_t v = w0; v < n; v += warps)
+        for (int32_t j = vtx_off[v] + 1 + lane; j < vtx_off[v + 1]; j += 32)
+            if (inc[j] <= inc[j - 1]) bad = true;
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, 1);
+}
+
+// Transpose check, thread per incidence (after the order checks): vertex v's list may name net
+// e only if v is a pin of e (binary search in the sorted pin list).  With distinct entries per
+// list and P entries in total, the two CSRs then describe exactly the same incidences.
+__global__ void k_na_check_transpose(int32_t n, const int32_t *net_off, const int32_t *pins,
+                                     const int32_t *vtx_off, const int32_t *inc, int32_t *err)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+        for (int32_t j = vtx_off[v]; j < vtx_off[v + 1]; ++j) {
+            const int32_t e = inc[j];
+            int32_t lo = net_off[e], hi = net_off[e + 1];
+            while (lo < hi) {
+                const int32_t mid = lo + ((hi - lo) >> 1);
+                if (pins[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= net_off[e + 1] || pins[lo] != (int32_t)v) bad = true;
+        }
+    }
     if (bad) atomicOr(err, 1);
 }
 
@@ -229,10 +273,18 @@ extern "C" int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_o
     if (k < 2 || !(eps > 0.0 && eps < 1.0) || subrounds < 1 || s < 0 || s >= subrounds)
         return HGP_ERR_INVALID;
     if (k > 64 || subrounds > 64 || m > kNoAllocMaxNets) return HGP_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the call reads sizes and the validation result back to the host and synchronises its
+    // stream, which a stream capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HGP_ERR_INVALID;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return HGP_ERR_INVALID;
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != HGP_OK) return rc;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned char *sc = reinterpret_cast<unsigned char *>(base);
     int64_t *bw = reinterpret_cast<int64_t *>(sc);
     int32_t *err = reinterpret_cast<int32_t *>(sc + 512);
@@ -253,6 +305,19 @@ extern "C" int hgp_candidates_noalloc(int32_t n, int32_t m, const int32_t *net_o
     k_na_check<<<152 * 4, 256, 0, st>>>(n, m, net_offsets, pins, vtx_offsets, inc_nets, vertex_w,
                                         net_w, part, k, P, err);
     int32_t bad = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HGP_ERR_CUDA;
+    }
+    if (bad) return HGP_ERR_INVALID;
+    // every index is in range now: the order and transpose checks may follow them
+    if (P > 0) {
+        k_na_check_order<<<152 * 8, 256, 0, st>>>(n, m, net_offsets, pins, vtx_offsets, inc_nets, err);
+        k_na_check_transpose<<<152 * 4, 256, 0, st>>>(n, net_offsets, pins, vtx_offsets, inc_nets, err);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

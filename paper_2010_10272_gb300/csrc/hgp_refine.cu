@@ -2011,6 +2011,20 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
     }
     h->next_round += rounds;
     h->all_eligible = false;
+    if (h->debug & 16) {
+        // fault injection (tests): the maintained objective loses one unit, as if an update
+        // had been dropped; written from the host after the rounds, so no kernel is involved
+        int64_t obj = 0;
+        e = cudaMemcpyAsync(&obj, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        obj -= 1;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.obj, &obj, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return status_of(e);
+        }
+    }
     if (stats || (h->debug & 1)) {
         rc = copy_stats_out(h, rounds, stats);
         if (rc != HGP_OK) return rc;

@@ -97,3 +97,34 @@ def test_launch_shapes_do_not_change_results_and_autotune_restores_state():
     # refining after tuning equals refining a fresh set
     got = Batch(hs).refine(3)
     np.testing.assert_array_equal(got[:, :, :6], ref[:, :, :6])
+
+
+def test_full_batch_workload_equals_oracle():
+    """All 256 instances of the batch workload (n log-uniform 1e3-2e5, |e| = min(2+Zipf(2.5),
+    1000), k in {2,4,8,16}, c(v) in U{1..4}, 5 rounds) in one batch with a tuned launch shape,
+    each member element by element against the oracle."""
+    import os
+    from paper_2010_10272_gb300 import HGP, Batch
+    from paper_2010_10272_gb300.autotune import tune_batch
+    insts = synth.config_batch()
+    assert len(insts) == 256
+    hs = [HGP.from_hypergraph(hg, subrounds=4) for hg in insts]
+    tuned = tune_batch(hs, rounds=1, candidates=[(0, 0), (4, 4), (2, 4)], repeats=1)
+    b = Batch(hs, graph=True, gain_ctas_per_sm=tuned["gain_ctas_per_sm"],
+              apply_ctas_per_sm=tuned["apply_ctas_per_sm"])
+    got = b.refine(insts[0].rounds)
+    threads = max(1, os.cpu_count() or 1)
+    moved = 0
+    for i, hg in enumerate(insts):
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=4, threads=threads)
+        want, _ = o.refine(hg.rounds)
+        np.testing.assert_array_equal(got[i, :, :5], want, err_msg=f"member {i}")
+        np.testing.assert_array_equal(hs[i].partition(), o.partition(), err_msg=f"member {i}")
+        np.testing.assert_array_equal(hs[i].block_weights(), o.block_weights())
+        assert hs[i].objective() == o.objective() == hs[i].objective_from_phi()
+        moved += int(want[:, 2].sum())
+        o.close()
+    assert moved > 100_000
+    b.close()
+    for h in hs:
+        h.close()

@@ -1,13 +1,16 @@
 """Full-size GPU checks in the launch configuration bench.py times (device-resident inputs,
-hgp_create_device, default options, hgp_refine over the workload's rounds).
+hgp_create_device, default options, hgp_refine over the workload's rounds), element by element
+against the oracle.
 
-* row-net workload (2*10^6 x 2*10^6, k=8, 10 rounds): element-by-element parity with the oracle.
-* power-law workload (n = m = 5*10^7, k=64, 5 rounds): the oracle cannot hold this instance's
-  Phi table, so (a) round-0 candidates of sampled vertices are compared with the oracle's
-  sample routine, which counts Phi only for the nets of the sampled vertices, and (b) after all
-  rounds, properties that hold at any size are checked against host recomputation from the
-  returned partition: Lambda(e) of every net, the objective, block weights, balance.
+* row-net workload (2*10^6 x 2*10^6, k=8, 10 rounds).
+* power-law workload (n = m = 5*10^7, P = 3.45*10^8, k=64, 5 rounds): every round's statistics,
+  the final partition, block weights, objective, Lambda of every net and the whole Phi table
+  (compared in row blocks), plus the round-0 candidates of sampled vertices against the oracle's
+  sample routine.  The oracle runs its independent loops on all host cores (identical results
+  for any thread count) so that the five rounds take minutes, not an hour.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +19,8 @@ import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+THREADS = max(1, os.cpu_count() or 1)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,6 +52,13 @@ def _lambda_from_partition(hg, part):
     return lam
 
 
+def _lambda_from_phi_rows(rows):
+    bits = np.zeros(rows.shape[0], dtype=np.uint64)
+    for i in range(rows.shape[1]):
+        bits |= (rows[:, i] > 0).astype(np.uint64) << np.uint64(i)
+    return bits
+
+
 def _objective(hg, lam):
     lam_count = np.bitwise_count(lam).astype(np.int64)
     w = np.ones(hg.m, np.int64) if hg.net_w is None else hg.net_w.astype(np.int64)
@@ -56,7 +68,7 @@ def _objective(hg, lam):
 def test_rownet_full_parity():
     hg = synth.config_rownet()
     h = _device_handle(hg)
-    o = oracle.Oracle.from_hypergraph(hg, subrounds=4)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4, threads=THREADS)
     assert h.info()["lmax"] == o.lmax == 257_500
     got = h.refine(hg.rounds)[:, :5]
     want, _ = o.refine(hg.rounds)
@@ -67,13 +79,13 @@ def test_rownet_full_parity():
     assert h.objective() == o.objective() == h.objective_from_phi()
 
 
-def test_powerlaw_full_sampled_and_properties():
+def test_powerlaw_full_oracle_parity():
     hg = synth.config_powerlaw()
     assert hg.n == 50_000_000 and hg.k == 64
     h = _device_handle(hg)
     info = h.info()
     assert info["lmax"] == 804_687 and info["phi_width"] == 2 and info["wide_nets"] > 0
-    # (a) round 0, sub-round 0: sampled candidates against the oracle's sample routine
+    # round 0, sub-round 0: sampled candidates against the oracle's sample routine
     rng = np.random.default_rng(2024)
     sample = np.sort(rng.choice(hg.n, size=20_000, replace=False)).astype(np.int32)
     want_t, want_g = oracle.sample_candidates(hg, sample, s=0, subrounds=4, seed=0)
@@ -81,23 +93,35 @@ def test_powerlaw_full_sampled_and_properties():
     np.testing.assert_array_equal(t[sample], want_t)
     np.testing.assert_array_equal(g[sample], want_g)
     assert (want_t >= 0).sum() > 1000
-    # initial state against host recomputation
+    del t, g
     lam0 = _lambda_from_partition(hg, hg.part)
     np.testing.assert_array_equal(h.lam(), lam0)
-    assert h.objective() == _objective(hg, lam0)
-    # (b) all rounds, then properties of the result
-    w0 = h.block_weights()
-    stats = h.refine(hg.rounds)
-    part = h.partition()
-    assert part.min() >= 0 and part.max() < hg.k
-    lam = _lambda_from_partition(hg, part)
-    np.testing.assert_array_equal(h.lam(), lam)
-    obj = _objective(hg, lam)
-    assert h.objective() == obj == h.objective_from_phi() == stats[-1, 0]
-    w = np.bincount(part, minlength=hg.k).astype(np.int64)
-    np.testing.assert_array_equal(h.block_weights(), w)
-    assert w.sum() == hg.n
-    assert np.all(w <= np.maximum(w0, info["lmax"]))
-    assert stats[0, 3] == hg.n                      # every vertex eligible in the first round
-    assert np.all(stats[:, 2] <= stats[:, 1])       # approved <= candidates
-    assert stats[-1, 0] < stats[0, 0] < _objective(hg, lam0)
+    obj0 = h.objective()
+    assert obj0 == _objective(hg, lam0)
+    # every round on the GPU, then the whole state read back; the handle is freed before the
+    # oracle is built (host memory)
+    got = h.refine(hg.rounds)
+    part, bw, lam = h.partition(), h.block_weights(), h.lam()
+    obj, obj_phi = h.objective(), h.objective_from_phi()
+    phi = h.phi().reshape(hg.m, hg.k)
+    h.close()
+    del h
+    torch.cuda.empty_cache()
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=4, threads=THREADS)
+    assert o.lmax == info["lmax"] and o.objective() == obj0
+    want, _ = o.refine(hg.rounds)
+    np.testing.assert_array_equal(got[:, :5], want)
+    np.testing.assert_array_equal(part, o.partition())
+    np.testing.assert_array_equal(bw, o.block_weights())
+    assert obj == obj_phi == o.objective() == want[-1, 0]
+    step = 1 << 22
+    for e0 in range(0, hg.m, step):
+        e1 = min(hg.m, e0 + step)
+        rows = o.phi_rows(e0, e1)
+        if not np.array_equal(phi[e0:e1], rows):
+            bad = e0 + int(np.flatnonzero((phi[e0:e1] != rows).any(axis=1))[0])
+            raise AssertionError(f"Phi row of net {bad} differs: {phi[bad]} vs {rows[bad - e0]}")
+        np.testing.assert_array_equal(lam[e0:e1], _lambda_from_phi_rows(rows))
+    assert want[0, 3] == hg.n                       # every vertex eligible in the first round
+    assert want[-1, 0] < want[0, 0] < obj0
+    o.close()

@@ -232,6 +232,43 @@ def test_check_mode():
     h.refine(3)
 
 
+def test_check_mode_reports_an_injected_fault():
+    """Fault injection on the host (debug bit 4: the maintained objective loses one unit after
+    each refine, as a dropped update would): check mode returns HGP_ERR_INTERNAL, the handle
+    still answers (the maintained value is the recomputed one minus one, the partition is the
+    oracle's), a new partition rebuilds the state, and destroying the handle gives back every
+    byte it took on the device (measured on a second identical cycle, after the first one has
+    loaded every kernel it uses)."""
+    import torch
+    from paper_2010_10272_gb300 import HGPError
+    hg = synth.random_small(35, 5000, 4500, 6, max_size=7, weighted=True, rounds=2)
+    o = oracle.Oracle.from_hypergraph(hg, subrounds=3)
+    o.refine(2)
+
+    def cycle():
+        h = HGP.from_hypergraph(hg, subrounds=3, debug=1 | 16)
+        with pytest.raises(HGPError) as ei:
+            h.refine(2)
+        assert ei.value.code == 6
+        np.testing.assert_array_equal(h.partition(), o.partition())
+        assert h.objective_from_phi() == o.objective() == h.objective() + 1
+        h.set_partition(hg.part)
+        assert h.objective() == h.objective_from_phi()
+        # without check mode the injected loss goes unnoticed by refine itself
+        h2 = HGP.from_hypergraph(hg, subrounds=3, debug=16)
+        h2.refine(1)
+        assert h2.objective() == h2.objective_from_phi() - 1
+        h.close()
+        h2.close()
+        torch.cuda.synchronize()
+
+    cycle()
+    free0, _ = torch.cuda.mem_get_info()
+    cycle()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+
+
 # ---------------------------------------------------------------- error codes
 def _err(fn):
     from paper_2010_10272_gb300 import HGPError

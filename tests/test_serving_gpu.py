@@ -77,3 +77,36 @@ def test_footprint_estimate_covers_creation():
     print("device bytes used by one request:", used, "estimate:", req.footprint())
     assert used <= req.footprint()
     h.close()
+
+
+def test_request_sizes_against_oracle():
+    """One serving request per size decade up to the workload's largest (10^4 .. 5*10^6 pins),
+    served together in the mix, each element by element against the oracle as well as against
+    the same request refined alone."""
+    import os
+    import oracle
+    from paper_2010_10272_gb300.serve import Request, Server
+    oracle.build()
+    sizes = [10_000, 100_000, 1_000_000, 5_000_000]
+    reqs = []
+    for i, p in enumerate(sizes):
+        hg = synth.serving_request(np.random.SeedSequence(700 + i), p_lo=p, p_hi=p + 1)
+        reqs.append(Request.from_hypergraph(i, hg, seed=i))
+    assert reqs[-1].num_pins > 4_000_000
+    srv = Server(stream=torch.cuda.Stream(), reserve_bytes=0)
+    for r in reqs:
+        srv.submit(r)
+    done = srv.run_until_idle()
+    srv.close()
+    assert sorted(r.rid for r in done) == list(range(len(sizes)))
+    threads = max(1, os.cpu_count() or 1)
+    for r in done:
+        o = oracle.Oracle(r.n, r.m, r.net_off, r.pins, r.k, r.eps, r.part, r.vertex_w, r.net_w,
+                          r.subrounds, r.seed, threads=threads)
+        want, _ = o.refine(r.rounds)
+        np.testing.assert_array_equal(r.stats[:, :5], want, err_msg=f"request {r.rid}")
+        np.testing.assert_array_equal(r.result, o.partition())
+        assert r.objective == o.objective()
+        part, obj, st = _alone(r)
+        np.testing.assert_array_equal(part, r.result)
+        assert obj == r.objective
