@@ -421,6 +421,19 @@ def run_gpu(args, world, rank, local):
         cv, cstep, sample, _ = oracle_sample(args.workload, 1, 0, variant=args.variant)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
+    # the metric's other parts, on the same GPU after the power-law instance is released:
+    # batched vs plain launches (batch workload) and serving latency (serving workload)
+    extra = {}
+    if args.workload == "powerlaw" and args.variant == "plain":
+        if "h" in locals():
+            del h
+        torch.cuda.empty_cache()
+        if not args.no_batch:
+            b = batch_section(args, stream, world)
+            extra["batched_vs_plain"] = b
+        if not args.no_serving:
+            extra["serving"] = serving_section(args, stream)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -438,23 +451,24 @@ def run_gpu(args, world, rank, local):
                          "reverted": stats[:, 6].tolist()},
         "setup_s": {"generate_or_load": t_gen},
     }
+    line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------------------ batch workload
-def run_batch(args, world, rank, local):
-    """256 planted instances of uneven size refined together (one launch per phase, replayed as
-    a CUDA graph) against the same 256 instances refined one after another with plain
-    per-instance launches on the same stream.  value = the batched throughput."""
+def batch_section(args, stream, world=1):
+    """The 256-instance batch workload (n log-uniform 1e3-2e5, |e| = min(2+Zipf(2.5), 1000),
+    k in {2,4,8,16}, c(v) in U{1..4}, 5 rounds): every phase of a round is one launch over all
+    instances, replayed as a CUDA graph with an autotuned launch shape, against the same
+    instances refined one after another with plain per-instance launches on the same stream.
+    Both from device-resident inputs; a step resets every start partition (untimed) and runs
+    all rounds of every instance."""
     import torch
-    from paper_2010_10272_gb300 import HGP, Batch, build
-    build.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
+    from paper_2010_10272_gb300 import HGP, Batch
+    from paper_2010_10272_gb300.autotune import tune_batch
+    dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
     insts = synth.config_batch(count=args.batch_count)
     t_gen = time.perf_counter() - t0
@@ -464,7 +478,6 @@ def run_batch(args, world, rank, local):
     parts = [to_dev(h.part) for h in insts]
     hs = [HGP(h.n, h.m, to_dev(h.net_off), to_dev(h.pins), h.k, h.eps, parts[i], to_dev(h.vertex_w),
               to_dev(h.net_w), subrounds=S, device=True, stream=stream) for i, h in enumerate(insts)]
-    batch = Batch(hs, graph=True, stream=stream)
 
     def reset():
         for h, p in zip(hs, parts):
@@ -472,12 +485,10 @@ def run_batch(args, world, rank, local):
         torch.cuda.synchronize()
 
     # launch shape of the persistent kernels: tuned on these handles (state restored after)
-    from paper_2010_10272_gb300.autotune import tune_batch
     reset()
     tuned = tune_batch(hs, rounds=R, stream=stream)
     shape = {"gain_ctas_per_sm": tuned["gain_ctas_per_sm"], "apply_ctas_per_sm": tuned["apply_ctas_per_sm"],
              "candidates_ms": {f"{g}x{a}": round(ms, 3) for (g, a), ms in tuned["ms"].items()}}
-    batch.close()
     batch = Batch(hs, graph=True, stream=stream, gain_ctas_per_sm=shape["gain_ctas_per_sm"],
                   apply_ctas_per_sm=shape["apply_ctas_per_sm"])
 
@@ -506,34 +517,57 @@ def run_batch(args, world, rank, local):
             ms.append(ev[0].elapsed_time(ev[1]))
         return ms
 
-    sampler = ClockSampler(local)
-    sampler.start()
     l0 = batch.launch_count()
-    ms_b = timed(batch_step, args.steps, args.warmup)
-    launches = (batch.launch_count() - l0) // (args.steps + args.warmup) * args.steps
-    clocks = sampler.stop()
-    ms_p = timed(plain_step, max(2, args.steps // 2), 1)
+    ms_b = timed(batch_step, args.batch_steps, 3)
+    launches = (batch.launch_count() - l0) // (args.batch_steps + 3) * args.batch_steps
+    ms_p = timed(plain_step, max(2, args.batch_steps // 2), 1)
     total_b = max_over_ranks(sum(ms_b), world)
     value = world * len(ms_b) * P * R / (total_b / 1e3)
     plain = world * len(ms_p) * P * R / (max_over_ranks(sum(ms_p), world) / 1e3)
+    batch.close()
+    for h in hs:
+        h.close()
+    del parts
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"batch of {len(insts)} planted hypergraphs, n log-uniform 1e3-2e5, "
+                    "|e|=min(2+Zipf(2.5),1000), k in {2,4,8,16}, c(v) in U{1..4}",
+        "instances": len(insts), "pins": P, "rounds": R, "subrounds": S,
+        "batched_pins_per_s": value, "plain_pins_per_s": plain, "ratio": value / plain,
+        "batched_ms_per_step": statistics.mean(ms_b), "plain_ms_per_step": statistics.mean(ms_p),
+        "steps": len(ms_b), "plain_steps": len(ms_p),
+        "step": f"reset all partitions (untimed) + {R} rounds of every instance",
+        "launch_shape": shape, "gpu_launches": launches, "generate_s": t_gen,
+    }
+
+
+def run_batch(args, world, rank, local):
+    """The batch workload alone: value = the batched throughput (pins/s per round)."""
+    import torch
+    from paper_2010_10272_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(torch.device("cuda", local))
+    torch.cuda.set_stream(stream)
+    args.batch_steps = args.steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    b = batch_section(args, stream, world)
+    clocks = sampler.stop()
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_b / len(ms_b), "higher_is_better": True,
+        "metric": METRIC, "value": b["batched_pins_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": b["steps"], "warmup": 3, "ms_per_step": b["batched_ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"batch of {len(insts)} planted hypergraphs, n log-uniform 1e3-2e5, "
-                               "|e|=min(2+Zipf(2.5),1000), k in {2,4,8,16}, c(v) in U{1..4}",
-                   "instances": len(insts), "pins": P, "rounds": R, "subrounds": S,
-                   "parallelism": f"replicas x{world}",
-                   "step": f"reset all partitions (untimed) + {R} rounds of every instance",
-                   "l2": "inputs larger than L2"},
-        "batched_vs_plain": {"batched_pins_per_s": value, "plain_pins_per_s": plain,
-                             "ratio": value / plain, "plain_ms_per_step": statistics.mean(ms_p),
-                             "batched_ms_per_step": statistics.mean(ms_b)},
-        "launch_shape": shape, "gpu_launches": launches, "clocks": clocks, "setup_s": {"generate": t_gen},
+        "config": {"workload": b["workload"], "instances": b["instances"], "pins": b["pins"],
+                   "rounds": b["rounds"], "subrounds": b["subrounds"], "parallelism": f"replicas x{world}",
+                   "step": b["step"], "l2": "inputs larger than L2"},
+        "batched_vs_plain": {k: b[k] for k in ("batched_pins_per_s", "plain_pins_per_s", "ratio",
+                                                "batched_ms_per_step", "plain_ms_per_step")},
+        "launch_shape": b["launch_shape"], "gpu_launches": b["gpu_launches"], "clocks": clocks,
+        "setup_s": {"generate": b["generate_s"]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
     return 0
 
 
@@ -770,24 +804,26 @@ def run_contract(args, world, rank, local):
 
 
 # ------------------------------------------------------------------------------ serving workload
-def run_serving(args, world, rank, local):
-    """Poisson arrivals of refinement requests (planted, pins log-uniform 1e4-5e6, k in
-    {2..32}, 3 rounds) served with continuous batching.  First a saturated run (every request
-    queued at t=0) measures the service capacity mu; then arrivals at 0.5 mu and 0.8 mu give
-    p50/p99 latency (arrival -> partition on the host).  value = saturated pin-rounds/s."""
+def serving_section(args, stream):
+    """The serving workload: requests are planted hypergraphs with pins log-uniform in
+    1e4-5e6, |e| = 2+Poisson(4), k in {2,4,8,16,32}, 3 rounds each, every one freshly drawn
+    (seeded, on the GPU; synth.device), served with continuous batching (serve.Server).  A
+    saturated run (every request queued at t = 0) measures the service capacity mu; Poisson
+    arrivals at 0.5 mu and 0.8 mu then give latency percentiles (arrival -> partition on the
+    host) over `serve_requests` requests after `serve_warmup` warm-up requests of the same
+    stream."""
     import torch
-    from paper_2010_10272_gb300 import build
     from paper_2010_10272_gb300.serve import Request, Server, latency_summary
-    build.build()
-    torch.cuda.set_device(local)
-    stream = torch.cuda.Stream(torch.device("cuda", local))
-    torch.cuda.set_stream(stream)
-    t0 = time.perf_counter()
-    pool = [synth.serving_request(np.random.SeedSequence(10_000 + i)) for i in range(args.serve_pool)]
-    t_gen = time.perf_counter() - t0
+    from synth import device as sdev
+    gen_s = 0.0
 
-    def make(count, base):
-        return [Request.from_hypergraph(base + i, pool[i % len(pool)]) for i in range(count)]
+    def make(seed, count, base):
+        nonlocal gen_s
+        t = time.perf_counter()
+        hgs = sdev.serving_requests(seed, count)
+        torch.cuda.empty_cache()
+        gen_s += time.perf_counter() - t
+        return [Request.from_hypergraph(base + i, h) for i, h in enumerate(hgs)]
 
     def run(reqs, arrivals):
         srv = Server(stream=stream)
@@ -804,40 +840,63 @@ def run_serving(args, world, rank, local):
                 continue
             done.extend(srv.step())
         t_total = time.perf_counter() - t_start
+        ticks = srv.ticks
         srv.close()
-        return done, t_total
+        return done, t_total, ticks
 
-    # warm-up (not reported)
-    run(make(min(len(pool), 16), 0), [0.0] * min(len(pool), 16))
-    sampler = ClockSampler(local)
-    sampler.start()
-    sat_reqs = make(args.serve_requests, 100_000)
-    done, t_sat = run(sat_reqs, [0.0] * len(sat_reqs))
-    clocks = sampler.stop()
+    warm = make(args.serve_seed * 1000 + 1, args.serve_warmup, 0)
+    run(warm, [0.0] * len(warm))
+    del warm
+    sat_reqs = make(args.serve_seed * 1000 + 2, args.serve_saturated, 100_000)
+    done, t_sat, ticks = run(sat_reqs, [0.0] * len(sat_reqs))
     work = sum(r.num_pins * r.rounds for r in done)
     mu = len(done) / t_sat
+    sat = {"requests": len(done), "seconds": t_sat, "ticks": ticks, "latency": latency_summary(done),
+           "pin_rounds_per_s": work / t_sat, "pins": sum(r.num_pins for r in done)}
+    del sat_reqs, done
     rng = np.random.default_rng(args.serve_seed)
     rates = {}
-    for frac in (0.5, 0.8):
+    for j, frac in enumerate((0.5, 0.8)):
         lam = frac * mu
-        reqs = make(args.serve_requests, int(1e6 * frac))
-        arr = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs))).tolist()
-        d2, t2 = run(reqs, arr)
-        rates[f"{frac:g}mu"] = dict(latency_summary(d2), arrival_rate_per_s=lam,
+        count = args.serve_warmup + args.serve_requests
+        reqs = make(args.serve_seed * 1000 + 3 + j, count, 1_000_000 * (j + 1))
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=count)).tolist()
+        d2, t2, ticks2 = run(reqs, arr)
+        measured = [r for r in d2 if r.rid - 1_000_000 * (j + 1) >= args.serve_warmup]
+        rates[f"{frac:g}mu"] = dict(latency_summary(measured), arrival_rate_per_s=lam,
+                                    warmup_requests=args.serve_warmup, ticks=ticks2,
                                     pin_rounds_per_s=sum(r.num_pins * r.rounds for r in d2) / t2)
-    value = work / t_sat
+        del reqs, d2, measured
+    return {
+        "workload": "Poisson arrivals of planted hypergraphs, pins log-uniform 1e4-5e6, "
+                    "|e|=2+Poisson(4), k in {2,4,8,16,32}, 3 rounds each, every request distinct",
+        "service_capacity_req_per_s": mu, "saturated_pin_rounds_per_s": sat["pin_rounds_per_s"],
+        "saturated": sat, "poisson": rates, "generate_s": gen_s,
+        "latency": "arrival -> partition on the host",
+    }
+
+
+def run_serving(args, world, rank, local):
+    """The serving workload alone: value = saturated pin-rounds/s."""
+    import torch
+    from paper_2010_10272_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(torch.device("cuda", local))
+    torch.cuda.set_stream(stream)
+    sampler = ClockSampler(local)
+    sampler.start()
+    sv = serving_section(args, stream)
+    clocks = sampler.stop()
+    sat = sv["saturated"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(done),
-        "warmup": 16, "ms_per_step": t_sat * 1e3 / len(done), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals of planted hypergraphs, pins log-uniform "
-                               "1e4-5e6, |e|=2+Poisson(4), k in {2,4,8,16,32}, 3 rounds each",
-                   "requests": len(done), "distinct_instances": len(pool),
+        "metric": METRIC, "value": sv["saturated_pin_rounds_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": sat["requests"], "warmup": args.serve_warmup, "ms_per_step": sat["seconds"] * 1e3 / sat["requests"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serving: " + sv["workload"], "requests": sat["requests"],
                    "step": "one request, arrival to partition on the host",
                    "l2": "request state resident in HBM; saturated run", "parallelism": "replicas x1"},
-        "serving": {"service_capacity_req_per_s": mu, "saturated_pin_rounds_per_s": value,
-                    "saturated_latency": latency_summary(done), "poisson": rates},
-        "clocks": clocks, "setup_s": {"generate": t_gen},
+        "serving": sv, "clocks": clocks, "setup_s": {"generate": sv["generate_s"]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -854,10 +913,18 @@ def main():
                     default="powerlaw")
     ap.add_argument("--skew", type=float, default=0.2,
                     help="rebalance workload: fraction of the vertices moved into block 0")
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="serving: measured requests per arrival rate (after --serve-warmup)")
+    ap.add_argument("--serve-warmup", type=int, default=100)
+    ap.add_argument("--serve-saturated", type=int, default=1000,
+                    help="serving: requests of the saturated run that measures the capacity")
     ap.add_argument("--serve-seed", type=int, default=1)
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: skip the batched-vs-plain section")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: skip the serving section")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--subrounds", type=int, default=4)
     ap.add_argument("--variant", choices=["plain", "balance", "revert", "balance+revert"], default="plain",

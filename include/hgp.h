@@ -216,8 +216,9 @@ int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gai
  * (members with k <= 32 and k > 32 form two groups), and by default the launches of a
  * hgp_batch_refine call are captured once as a CUDA graph and replayed.  The arithmetic of
  * each member is unchanged: refining a handle inside a batch gives exactly the result of
- * refining it alone.  The batch does not own the handles; they must outlive it, must not be
- * used elsewhere while a batch call runs, and their round numbering advances with the batch.
+ * refining it alone.  The batch does not own the handles: they must not be used elsewhere while
+ * a batch call runs, and their round numbering advances with the batch.  A member may be
+ * destroyed before the batch only if the batch is then used for nothing but hgp_batch_destroy.
  */
 typedef struct {
     int32_t graph;              /* 1: capture/replay a CUDA graph per round count [1] */
@@ -230,7 +231,10 @@ typedef struct {
 void hgp_batch_default_options(hgp_batch_options *opt);
 
 /* handles: host array of `count` distinct handles on the current device.  Returns
- * HGP_ERR_UNSUPPORTED for a handle created with the revert variant. */
+ * HGP_ERR_UNSUPPORTED for a handle created with the revert variant.  Members may live on other
+ * streams than the batch: every hgp_batch_refine call then starts, on the device, after the
+ * work already queued on those streams, and work queued on them afterwards (read-backs,
+ * hgp_destroy) runs after the call; no call blocks the host for this. */
 int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_options *opt,
                      hgp_batch **out);
 
@@ -238,6 +242,12 @@ int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_
  * member-major (member i's rounds at [i * rounds, (i + 1) * rounds)); filled on return, and the
  * call then synchronises.  Without stats the call returns with the work queued. */
 int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
+
+/* Statistics of the last hgp_batch_refine call, laid out as that call's `stats` argument;
+ * `rounds` must equal that call's round count (else HGP_ERR_INVALID).  Waits for the batch's
+ * stream.  Lets a caller queue a call without statistics, do host work while it runs, and
+ * read them afterwards. */
+int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
 
 /* Waits for the batch's queued work. */
 int hgp_batch_synchronize(hgp_batch *b);
@@ -372,8 +382,21 @@ int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *moves, int64_t 
  */
 int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *ms_out, double *gathers_per_s);
 
-/* Frees all device memory of the handle (NULL is allowed). */
+/* Frees all device memory of the handle (NULL is allowed).  The releases are queued on the
+ * handle's stream behind its pending work, so the call returns without waiting for the device;
+ * the memory returns to the library's pool (see hgp_set_pool_retention). */
 void hgp_destroy(hgp_handle *h);
+
+/*
+ * Memory pool (no counterpart in the paper).  Handles and batches take their device memory
+ * from a stream-ordered pool the library keeps per device (allocations and releases are
+ * queued on the owner's stream and never synchronise the device, so handles can be created
+ * and destroyed while other handles' kernels run).  By default freed memory goes back to the
+ * system at the next synchronisation; this call lets the pool of the current device keep up
+ * to `bytes` of freed memory for reuse, which a caller that creates and destroys many
+ * handles (a serving loop) may want.  HGP_ERR_INVALID for bytes < 0.
+ */
+int hgp_set_pool_retention(int64_t bytes);
 
 #ifdef __cplusplus
 }

@@ -150,6 +150,7 @@ __global__ void k_eg_degsum(Dev d, const int32_t *moves, int32_t count, unsigned
 extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *moves, int64_t *gains)
 {
     if (!h || count < 0 || (count > 0 && (!moves || !gains))) return HGP_ERR_INVALID;
+    settle(h);
     if (count == 0) return HGP_OK;
     Dev &d = h->d;
     cudaStream_t st = h->stream;

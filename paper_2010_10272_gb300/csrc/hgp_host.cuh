@@ -22,7 +22,7 @@ struct hgp_handle {
     int64_t max_vertex_netweight = 0;   // max_u sum_{e in I(u)} omega(e)
     int64_t total_weight = 0;
     int32_t stats_cap = 0;
-    int64_t *h_stats = nullptr;   // pinned host copy of the stats buffer
+    int64_t *h_stats = nullptr;   // host copy of the stats buffer
     // memory owned by the handle
     static constexpr int kMaxAllocs = 64;
     void *allocs[kMaxAllocs] = {};
@@ -48,6 +48,11 @@ struct hgp_handle {
     int32_t events_used = 0;
     int32_t *event_phase = nullptr; // phase of each event pair
     int32_t *event_count = nullptr; // kernel launches inside each event pair
+    // the end of the last batch call that refined this handle from another stream, which later
+    // work on the handle's own stream must follow (recorded by the batch, owned by the handle;
+    // see settle())
+    cudaEvent_t ev_batch = nullptr;
+    bool after_batch = false;
 };
 
 namespace hgp {
@@ -57,6 +62,27 @@ inline int status_of(cudaError_t e)
     if (e == cudaSuccess) return HGP_OK;
     if (e == cudaErrorMemoryAllocation) return HGP_ERR_OOM;
     return HGP_ERR_CUDA;
+}
+
+// Device memory of handles and batches comes from a library-owned stream-ordered memory pool
+// of the current device (cudaMallocFromPoolAsync / cudaFreeAsync on the owner's stream), so
+// creating or destroying a handle never implies a device-wide synchronisation and can overlap
+// with kernels of other handles (the serving loop relies on this).  Freed memory goes back to
+// the system at the next synchronisation unless hgp_set_pool_retention keeps some of it.
+cudaError_t library_pool(cudaMemPool_t *out);
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+// Orders the handle's stream after the last batch call that refined the handle from another
+// stream.  Every entry point that queues work on, or reads from, the handle calls it first, so
+// a batch call itself never makes the handle's stream wait (work queued there meanwhile, such
+// as creating other handles, is not held back by the batch).
+inline void settle(hgp_handle *h)
+{
+    if (h->after_batch) {
+        if (cudaStreamWaitEvent(h->stream, h->ev_batch, 0) != cudaSuccess) (void)cudaGetLastError();
+        h->after_batch = false;
+    }
 }
 
 // refine-side entry points used by the C ABI layer (hgp_refine.cu)

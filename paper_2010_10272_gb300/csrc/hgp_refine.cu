@@ -1844,7 +1844,7 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
 cudaError_t sync_dev(hgp_handle *h)
 {
     if (!h->d_dev) {
-        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&h->d_dev), sizeof(Dev));
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&h->d_dev), sizeof(Dev), h->stream);
         if (e != cudaSuccess) return e;
         h->dev_dirty = true;
     }
@@ -1914,17 +1914,19 @@ int ensure_stats(hgp_handle *h, int32_t rounds)
     int64_t *dev = nullptr, *host = nullptr;
     // stats rows, then the work counters of the persistent kernels: 64 sub-rounds x (gain, apply)
     // per row
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dev), sizeof(int64_t) * ST_N * (size_t)cap +
-                                                                    sizeof(int32_t) * kWqPerRow * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&host), sizeof(int64_t) * ST_N * (size_t)cap);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&dev), sizeof(int64_t) * ST_N * (size_t)cap +
+                                                                   sizeof(int32_t) * kWqPerRow * (size_t)cap, h->stream);
+    if (e == cudaSuccess) {
+        host = static_cast<int64_t *>(malloc(sizeof(int64_t) * ST_N * (size_t)cap));
+        if (!host) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        if (dev) cudaFree(dev);
+        dev_free(dev, h->stream);
         return status_of(e);
     }
-    if (h->d.stats || h->h_stats) cudaStreamSynchronize(h->stream);
-    if (h->d.stats) cudaFree(h->d.stats);
-    if (h->h_stats) cudaFreeHost(h->h_stats);
+    if (h->d.stats) dev_free(h->d.stats, h->stream);
+    free(h->h_stats);
     h->d.stats = dev;
     h->d.wq = reinterpret_cast<int32_t *>(dev + (size_t)ST_N * cap);
     h->h_stats = host;
@@ -2094,6 +2096,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 extern "C" int hgp_set_launch_shape(hgp_handle *h, int32_t gain_ctas_per_sm, int32_t apply_ctas_per_sm)
 {
     if (!h || gain_ctas_per_sm < 0 || apply_ctas_per_sm < 0) return HGP_ERR_INVALID;
+    settle(h);
     const cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -2162,6 +2165,7 @@ extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats 
                              int32_t *num_passes)
 {
     if (!h || max_passes < 0) return HGP_ERR_INVALID;
+    settle(h);
     if (num_passes) *num_passes = 0;
     if (max_passes == 0) return HGP_OK;
     // phase-2 priorities are gain + W_max in [0, 2 W_max]; they must fit the 31-bit gain field
@@ -2229,6 +2233,11 @@ struct hgp_batch {
     int32_t use_graph = 1;
     int32_t gain_ctas = 0, apply_ctas = 0;     // per-SM CTA overrides (0 = occupancy)
     std::vector<hgp_handle *> hs;
+    // the members' streams other than the batch's: a call waits (on the device) for their
+    // pending work through events[i], and records its end on each such member's own event
+    std::vector<cudaStream_t> member_streams;
+    std::vector<cudaEvent_t> events;
+    int32_t last_rounds = 0;                    // round count of the last hgp_batch_refine
     struct Group {
         Plan plan;
         std::vector<int32_t> members;           // indices into hs
@@ -2250,9 +2259,9 @@ namespace {
 void free_groups(hgp_batch *b)
 {
     for (auto &gr : b->g) {
-        if (gr.d_devs) cudaFree(gr.d_devs);
-        if (gr.d_items) cudaFree(gr.d_items);
-        if (gr.d_wq) cudaFree(gr.d_wq);
+        dev_free(gr.d_devs, b->stream);
+        dev_free(gr.d_items, b->stream);
+        dev_free(gr.d_wq, b->stream);
         gr.d_devs = nullptr;
         gr.d_items = nullptr;
         gr.d_wq = nullptr;
@@ -2267,12 +2276,16 @@ int build_groups(hgp_batch *b, int32_t cap)
 {
     free_groups(b);
     const int32_t count = (int32_t)b->hs.size();
-    if (b->d_stats) cudaFree(b->d_stats);
-    if (b->h_stats) cudaFreeHost(b->h_stats);
+    dev_free(b->d_stats, b->stream);
+    free(b->h_stats);
     b->d_stats = nullptr;
     b->h_stats = nullptr;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_stats), sizeof(int64_t) * ST_N * (size_t)cap * count);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&b->h_stats), sizeof(int64_t) * ST_N * (size_t)cap * count);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b->d_stats), sizeof(int64_t) * ST_N * (size_t)cap * count,
+                              b->stream);
+    if (e == cudaSuccess) {
+        b->h_stats = static_cast<int64_t *>(malloc(sizeof(int64_t) * ST_N * (size_t)cap * count));
+        if (!b->h_stats) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2301,16 +2314,20 @@ int build_groups(hgp_batch *b, int32_t cap)
             levels = levels || h->max_vertex_netweight >= kBins - 1;
         }
         const size_t n_items = ranges.size() + tiles.size() + blocks.size();
-        e = cudaMalloc(reinterpret_cast<void **>(&gr.d_devs), sizeof(Dev) * devs.size());
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&gr.d_items), sizeof(int2) * n_items);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&gr.d_wq), sizeof(int32_t) * kWqPerRow * (size_t)cap);
+        e = dev_alloc(reinterpret_cast<void **>(&gr.d_devs), sizeof(Dev) * devs.size(), b->stream);
+        if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&gr.d_items), sizeof(int2) * n_items, b->stream);
+        if (e == cudaSuccess)
+            e = dev_alloc(reinterpret_cast<void **>(&gr.d_wq), sizeof(int32_t) * kWqPerRow * (size_t)cap, b->stream);
         std::vector<int2> all;
         all.reserve(n_items);
         all.insert(all.end(), ranges.begin(), ranges.end());
         all.insert(all.end(), tiles.begin(), tiles.end());
         all.insert(all.end(), blocks.begin(), blocks.end());
-        if (e == cudaSuccess) e = cudaMemcpy(gr.d_devs, devs.data(), sizeof(Dev) * devs.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(gr.d_items, all.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice);
+        // pageable sources: each call returns once its source has been staged
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(gr.d_devs, devs.data(), sizeof(Dev) * devs.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(gr.d_items, all.data(), sizeof(int2) * n_items, cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
@@ -2354,6 +2371,32 @@ cudaError_t enqueue_batch(hgp_batch *b, int32_t rounds, int64_t *launch_counter)
 
 }  // namespace
 
+// waits for the batch's stream and unpacks the per-member statistics of its last call
+static int batch_stats_out(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
+{
+    const int32_t count = (int32_t)b->hs.size();
+    cudaError_t e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    for (int32_t i = 0; i < count; ++i)
+        for (int32_t rr = 0; rr < rounds; ++rr) {
+            const int64_t *row = b->h_stats + ((int64_t)i * b->stats_cap + rr) * ST_N;
+            hgp_round_stats &o = stats[(int64_t)i * rounds + rr];
+            o.objective = row[ST_OBJ];
+            o.candidates = row[ST_CAND];
+            o.approved = row[ST_APPR];
+            o.eligible = row[ST_ELIG];
+            o.max_block_weight = row[ST_MAXW];
+            o.moved_pins = row[ST_MOVED];
+            o.reverted = row[ST_REV];
+        }
+    return HGP_OK;
+}
+
 extern "C" {
 
 void hgp_batch_default_options(hgp_batch_options *opt)
@@ -2395,7 +2438,29 @@ int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_
     } else {
         b->own_stream = true;
     }
-    for (hgp_handle *h : b->hs) cudaStreamSynchronize(h->stream);
+    for (hgp_handle *h : b->hs) {
+        if (h->stream == b->stream) continue;
+        bool seen = false;
+        for (cudaStream_t s2 : b->member_streams) seen = seen || s2 == h->stream;
+        if (!seen) b->member_streams.push_back(h->stream);
+    }
+    for (size_t i = 0; i < b->member_streams.size(); ++i) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            hgp_batch_destroy(b);
+            return HGP_ERR_CUDA;
+        }
+        b->events.push_back(ev);
+    }
+    for (hgp_handle *h : b->hs)
+        if (h->stream != b->stream && !h->ev_batch &&
+            cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->ev_batch = nullptr;
+            hgp_batch_destroy(b);
+            return HGP_ERR_CUDA;
+        }
     const int rc = build_groups(b, 8);
     if (rc != HGP_OK) {
         hgp_batch_destroy(b);
@@ -2409,12 +2474,15 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
 {
     if (!b || rounds < 0) return HGP_ERR_INVALID;
     if (rounds == 0) return HGP_OK;
-    for (hgp_handle *h : b->hs) {
+    for (hgp_handle *h : b->hs)
         if (h->next_round + rounds >= ((int64_t)1 << 30)) return HGP_ERR_UNSUPPORTED;
-        // the batch reads the handles' state from its own stream
-        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    // the batch reads the handles' state on its own stream: after their streams' pending work
+    for (size_t i = 0; i < b->member_streams.size(); ++i) {
+        cudaError_t e = cudaEventRecord(b->events[i], b->member_streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[i], 0);
+        if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            return HGP_ERR_CUDA;
+            return status_of(e);
         }
     }
     if (rounds > b->stats_cap) {
@@ -2458,29 +2526,26 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
         h->next_round += rounds;
         h->all_eligible = false;
     }
-    const int32_t count = (int32_t)b->hs.size();
-    if (stats) {
-        e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
-                            cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    b->last_rounds = rounds;
+    // later work on the members' own streams (read-backs, releases) must come after this call:
+    // the call's end is recorded on each such member's event, which its next entry point waits on
+    for (hgp_handle *h : b->hs) {
+        if (h->stream == b->stream) continue;
+        e = cudaEventRecord(h->ev_batch, b->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
         }
-        for (int32_t i = 0; i < count; ++i)
-            for (int32_t rr = 0; rr < rounds; ++rr) {
-                const int64_t *row = b->h_stats + ((int64_t)i * b->stats_cap + rr) * ST_N;
-                hgp_round_stats &o = stats[(int64_t)i * rounds + rr];
-                o.objective = row[ST_OBJ];
-                o.candidates = row[ST_CAND];
-                o.approved = row[ST_APPR];
-                o.eligible = row[ST_ELIG];
-                o.max_block_weight = row[ST_MAXW];
-                o.moved_pins = row[ST_MOVED];
-                o.reverted = row[ST_REV];
-            }
+        h->after_batch = true;
     }
+    if (stats) return batch_stats_out(b, rounds, stats);
     return HGP_OK;
+}
+
+int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
+{
+    if (!b || !stats || rounds < 1 || rounds != b->last_rounds) return HGP_ERR_INVALID;
+    return batch_stats_out(b, rounds, stats);
 }
 
 int hgp_batch_synchronize(hgp_batch *b)
@@ -2504,10 +2569,10 @@ int hgp_batch_get_launch_count(hgp_batch *b, int64_t *out)
 void hgp_batch_destroy(hgp_batch *b)
 {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    free_groups(b);
-    if (b->d_stats) cudaFree(b->d_stats);
-    if (b->h_stats) cudaFreeHost(b->h_stats);
+    free_groups(b);   // touches no member handle: members may already be destroyed
+    dev_free(b->d_stats, b->stream);
+    free(b->h_stats);
+    for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     (void)cudaGetLastError();
     delete b;

@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "hgp_host.cuh"
@@ -849,6 +850,61 @@ int grid_for(int64_t work, int threads, int cap = 152 * 32)
     return (int)g;
 }
 
+}  // namespace
+
+namespace hgp {
+
+static constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[kMaxPoolDevices];
+
+// the library's pool on the current device, created on first use
+cudaError_t library_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&g_pool[dev], &props);
+        if (e != cudaSuccess) {
+            g_pool[dev] = nullptr;
+            return e;
+        }
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
+}
+
+void dev_free(void *p, cudaStream_t st)
+{
+    if (p && cudaFreeAsync(p, st) != cudaSuccess) (void)cudaGetLastError();
+}
+
+}  // namespace hgp
+
+namespace {
+
 template <typename T>
 cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
 {
@@ -856,7 +912,7 @@ cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
     if (count < 1) count = 1;
     if (h->n_allocs >= hgp_handle::kMaxAllocs) return cudaErrorMemoryAllocation;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+    cudaError_t e = dev_alloc(&q, (size_t)count * sizeof(T), h->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return e;
@@ -897,12 +953,17 @@ int init_state(hgp_handle *h)
     }
     if (d.m > e_begin) {
         const int g = grid_for(((int64_t)d.m - e_begin + 31) / 32 * 32, kInitWarps * 32, 152 * 16);
-        const int smem = kInitWarps * (32 * d.k * d.phi_w + 15) / 16 * 16;
+        auto init_smem = [](int k, int w) { return kInitWarps * (32 * k * w + 15) / 16 * 16; };
+        const int smem = init_smem(d.k, d.phi_w);
+        // the attribute is the kernel's largest need over every k and entry width (the same
+        // value from every caller), so concurrent creations cannot lower it under each other
         if (d.k <= 32) {
-            cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 init_smem(32, 4));
             k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
         } else {
-            cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 init_smem(64, 4));
             k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
         }
     }
@@ -953,7 +1014,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     auto release = [&](void *ptr) {   // frees one of the handle's allocations before the end
         for (int i = 0; i < h->n_allocs; ++i)
             if (h->allocs[i] == ptr) {
-                cudaFree(h->allocs[i]);
+                dev_free(h->allocs[i], h->stream);
                 h->allocs[i] = nullptr;
             }
     };
@@ -1162,7 +1223,8 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         }
         if (bshift <= kTpSmemShift) {
             const int smem = (int)(sizeof(int32_t) << bshift);
-            cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(int32_t) << kTpSmemShift));   // largest need, as above
             k_tp_place<true><<<nbk, 1024, smem, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
         } else {
             k_tp_place<false><<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
@@ -1273,7 +1335,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     for (int i = 0; i < h->n_allocs; ++i) {
         if (h->allocs[i] == off64 || h->allocs[i] == part_in || h->allocs[i] == block_sums ||
             h->allocs[i] == tmp) {
-            cudaFree(h->allocs[i]);
+            dev_free(h->allocs[i], st);
             h->allocs[i] = nullptr;
         }
     }
@@ -1294,6 +1356,20 @@ void hgp_default_options(hgp_options *opt)
     if (!opt) return;
     memset(opt, 0, sizeof(*opt));
     opt->subrounds = 4;
+}
+
+int hgp_set_pool_retention(int64_t bytes)
+{
+    if (bytes < 0) return HGP_ERR_INVALID;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = hgp::library_pool(&pool);
+    uint64_t v = (uint64_t)bytes;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &v);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return HGP_OK;
 }
 
 const char *hgp_strerror(int code)
@@ -1324,20 +1400,23 @@ int hgp_create_device(int32_t n, int32_t m, const int64_t *net_offsets, const in
     return create_impl(n, m, net_offsets, pins, vertex_w, net_w, k, eps, initial_part, opt, out, true);
 }
 
+// Releases are queued on the handle's stream behind its pending work (and behind the batch
+// work that hgp_batch_refine ordered before it), so the call does not wait for the device.
 void hgp_destroy(hgp_handle *h)
 {
     if (!h) return;
-    if (h->stream) cudaStreamSynchronize(h->stream);
+    settle(h);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (int i = 0; i < h->n_allocs; ++i)
-        if (h->allocs[i]) cudaFree(h->allocs[i]);
+        if (h->allocs[i]) dev_free(h->allocs[i], h->stream);
     for (int32_t i = 0; i < h->n_events; ++i) cudaEventDestroy(h->events[i]);
+    if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     delete[] h->events;
     delete[] h->event_phase;
     delete[] h->event_count;
-    if (h->d.stats) cudaFree(h->d.stats);
-    if (h->d_dev) cudaFree(h->d_dev);
-    if (h->h_stats) cudaFreeHost(h->h_stats);
+    if (h->d.stats) dev_free(h->d.stats, h->stream);
+    if (h->d_dev) dev_free(h->d_dev, h->stream);
+    free(h->h_stats);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     (void)cudaGetLastError();
     delete h;
@@ -1346,6 +1425,7 @@ void hgp_destroy(hgp_handle *h)
 int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
 {
     if (!h || !part) return HGP_ERR_INVALID;
+    settle(h);
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     int32_t *tmp = nullptr;
@@ -1378,6 +1458,7 @@ int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t 
                      int32_t *first_round)
 {
     if (!h) return HGP_ERR_INVALID;
+    settle(h);
     if (part) {
         const int rc = hgp_get_partition(h, part, 0);
         if (rc != HGP_OK) return rc;
@@ -1408,6 +1489,7 @@ int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_ne
                      int64_t next_round, int32_t first_round)
 {
     if (!h || !part || next_round < 0 || next_round >= ((int64_t)1 << 30)) return HGP_ERR_INVALID;
+    settle(h);
     if (!first_round && !moved_nets && h->d.m > 0) return HGP_ERR_INVALID;
     int rc = hgp_set_partition(h, part, 0);
     if (rc != HGP_OK) return rc;
@@ -1439,6 +1521,7 @@ int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_ne
 int hgp_objective(hgp_handle *h, int64_t *out)
 {
     if (!h || !out) return HGP_ERR_INVALID;
+    settle(h);
     CK(cudaMemcpyAsync(out, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return HGP_OK;
@@ -1447,6 +1530,7 @@ int hgp_objective(hgp_handle *h, int64_t *out)
 int hgp_objective_from_phi(hgp_handle *h, int64_t *out)
 {
     if (!h || !out) return HGP_ERR_INVALID;
+    settle(h);
     unsigned long long *tmp = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(*tmp), h->stream));
     cudaError_t e = objective_from_phi(h, reinterpret_cast<int64_t *>(tmp));
@@ -1460,6 +1544,7 @@ int hgp_objective_from_phi(hgp_handle *h, int64_t *out)
 int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
 {
     if (!h || !part) return HGP_ERR_INVALID;
+    settle(h);
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     if (on_device) {
@@ -1482,6 +1567,7 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
 int hgp_get_block_weights(hgp_handle *h, int64_t *w)
 {
     if (!h || !w) return HGP_ERR_INVALID;
+    settle(h);
     CK(cudaMemcpyAsync(w, h->d.bw, sizeof(int64_t) * h->d.k, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return HGP_OK;
@@ -1490,6 +1576,7 @@ int hgp_get_block_weights(hgp_handle *h, int64_t *w)
 int hgp_get_phi(hgp_handle *h, int32_t *phi)
 {
     if (!h || !phi) return HGP_ERR_INVALID;
+    settle(h);
     Dev &d = h->d;
     const int64_t total = (int64_t)d.m * d.k;
     if (total == 0) return HGP_OK;
@@ -1507,6 +1594,7 @@ int hgp_get_phi(hgp_handle *h, int32_t *phi)
 int hgp_get_lambda(hgp_handle *h, uint64_t *lam)
 {
     if (!h || !lam) return HGP_ERR_INVALID;
+    settle(h);
     Dev &d = h->d;
     if (d.m == 0) return HGP_OK;
     uint64_t *tmp = nullptr;
@@ -1539,12 +1627,14 @@ int hgp_get_info(hgp_handle *h, int32_t *n, int32_t *m, int32_t *k, int64_t *pin
 int hgp_refine(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
 {
     if (!h || rounds < 0) return HGP_ERR_INVALID;
+    settle(h);
     return refine_rounds(h, rounds, stats);
 }
 
 int hgp_debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
 {
     if (!h || !target || !gain || s < 0 || s >= h->d.S) return HGP_ERR_INVALID;
+    settle(h);
     return debug_candidates(h, s, target, gain);
 }
 

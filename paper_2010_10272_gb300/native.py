@@ -119,9 +119,12 @@ def load_library():
         lib.hgp_batch_refine.argtypes = [P, i32, P]
         lib.hgp_batch_synchronize.argtypes = [P]
         lib.hgp_batch_get_launch_count.argtypes = [P, P]
+        lib.hgp_batch_get_stats.argtypes = [P, i32, P]
         for name in ("hgp_batch_create", "hgp_batch_refine", "hgp_batch_synchronize",
-                     "hgp_batch_get_launch_count"):
+                     "hgp_batch_get_launch_count", "hgp_batch_get_stats"):
             getattr(lib, name).restype = ctypes.c_int
+        lib.hgp_set_pool_retention.argtypes = [i64]
+        lib.hgp_set_pool_retention.restype = ctypes.c_int
         lib.hgp_batch_destroy.argtypes = [P]
         lib.hgp_batch_destroy.restype = None
         lib.hgp_probe_gather.argtypes = [i64, i64, P, P]
@@ -391,16 +394,23 @@ class Batch:
                                           ctypes.byref(self._b)), "hgp_batch_create")
 
     def refine(self, rounds: int, stats: bool = True):
-        """Runs `rounds` rounds on every member; returns int64 [count x rounds x 7] or None."""
+        """Runs `rounds` rounds on every member; returns int64 [count x rounds x 7] or None
+        (then the call returns with the work queued; see stats())."""
         n = len(self.handles)
         if stats:
             buf = (RoundStats * max(1, n * rounds))()
             _check(self._lib.hgp_batch_refine(self._b, int(rounds), buf), "hgp_batch_refine")
-            out = np.array([[getattr(buf[i], f) for f in STAT_FIELDS] for i in range(n * rounds)],
-                           dtype=np.int64)
-            return out.reshape(n, rounds, len(STAT_FIELDS))
+            return _stats_array(buf, n * rounds).reshape(n, rounds, len(STAT_FIELDS))
         _check(self._lib.hgp_batch_refine(self._b, int(rounds), None), "hgp_batch_refine")
         return None
+
+    def stats(self, rounds: int):
+        """Statistics of the last refine call (of `rounds` rounds), waiting for it:
+        int64 [count x rounds x 7]."""
+        n = len(self.handles)
+        buf = (RoundStats * max(1, n * rounds))()
+        _check(self._lib.hgp_batch_get_stats(self._b, int(rounds), buf), "hgp_batch_get_stats")
+        return _stats_array(buf, n * rounds).reshape(n, rounds, len(STAT_FIELDS))
 
     def synchronize(self):
         _check(self._lib.hgp_batch_synchronize(self._b), "hgp_batch_synchronize")
@@ -420,6 +430,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _stats_array(buf, count: int) -> np.ndarray:
+    raw = np.frombuffer(buf, dtype=np.int64, count=count * len(STAT_FIELDS))
+    return raw.reshape(count, len(STAT_FIELDS)).copy()
+
+
+def set_pool_retention(nbytes: int):
+    """hgp_set_pool_retention: freed device memory the library's pool of the current device
+    keeps for reuse (0 = give it back at the next synchronisation)."""
+    _check(load_library().hgp_set_pool_retention(int(nbytes)), "hgp_set_pool_retention")
 
 
 def probe_gather(array_bytes: int = 1600 << 20, n_gathers: int = 86_000_000):

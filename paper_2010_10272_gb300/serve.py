@@ -1,21 +1,28 @@
 """Serving loop: continuous batching of refinement requests on one GPU.
 
-Requests (a hypergraph, a start partition, a round count) are queued as they arrive.  Every
-tick the server
-  1. admits queued requests while the device has room for them: a request's state is created
-     on the device (hgp_create) only if the free HBM minus a reserve covers its footprint
-     estimate, so memory decides how many requests run at once;
-  2. runs one LP round for every resident request in a single batch (hgp_batch_*: one launch
-     per phase over all requests' work items), so requests that arrived while others were on
-     the GPU share their kernels from the next round on;
-  3. retires requests whose rounds are done: their partition is read back to the host, their
-     device state is freed, and their latency (arrival -> result on the host) is recorded.
-Each request's arithmetic is the same as refining it alone: batching changes only which
-kernel launch does the work (see tests/test_serving_gpu.py).
+Requests (a hypergraph, a start partition, a round count) are queued as they arrive.  Each
+tick of the server
+  1. queues, on the batch stream, the next rounds of every resident request as one batch
+     (hgp_batch_*: one launch per phase over all requests' work items): as many rounds as the
+     request closest to completion still needs, so no request runs past its round count;
+  2. while those rounds run on the GPU, admits queued requests: a request's state is created
+     on the device (hgp_create, by a small pool of creator threads, each on its own upload
+     stream, so creations overlap each other and the batch) if the memory budget minus what
+     resident, staged and in-creation requests take covers its footprint estimate, so memory
+     decides how many requests run at once; the new handles are staged and join the batch at
+     the next tick (a round boundary);
+  3. waits for the rounds, then retires the requests that are done, on the creator threads
+     too: each partition is read back to the host and its device state released (queued behind
+     the batch's rounds on the request's own stream, without synchronising the device), and the
+     latency (arrival -> result on the host) is recorded.
+Device memory comes from the library's stream-ordered pool, so creating and releasing request
+state never synchronises the device.  Each request's arithmetic is the same as refining it
+alone: batching changes only which kernel launch does the work (see tests/test_serving_gpu.py).
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import threading
 import time
@@ -102,21 +109,33 @@ class Request:
 
 
 class Server:
-    """Continuous-batching refinement server for one GPU (see the module docstring)."""
+    """Continuous-batching refinement server for one GPU (see the module docstring).
+
+    memory_budget: device bytes the server may hold for requests (default: the free device
+    memory when the server starts, minus reserve_bytes).  max_active: requests refined at once;
+    max_staged: requests created (or being created) ahead of the batch they will join;
+    creators: threads that create and retire request state (0: the serving thread itself)."""
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
-                 memory_budget: Optional[int] = None, max_active: int = 1024, graph: bool = False,
-                 clock=time.perf_counter):
+                 memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
+                 graph: bool = False, creators: int = 4, clock=time.perf_counter):
         import torch
         self._torch = torch
         self.stream = stream
         self.reserve = int(reserve_bytes)
-        self.memory_budget = memory_budget
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            memory_budget = max(0, int(free) - self.reserve)
+        self.memory_budget = int(memory_budget)
         self.max_active = int(max_active)
+        self.max_staged = int(max_staged)
         self.graph = graph
         self.clock = clock
         self.queue: Deque[Request] = collections.deque()
+        self.staged: Deque[Request] = collections.deque()
         self.active: List[Request] = []
+        self._creating: Deque[tuple] = collections.deque()    # (request, future), FIFO
+        self._retiring: Deque[tuple] = collections.deque()    # (request, future), FIFO
         self._handles: Dict[int, HGP] = {}
         self._done_rounds: Dict[int, int] = {}
         self._stats: Dict[int, list] = {}
@@ -124,6 +143,9 @@ class Server:
         self._batch_key: tuple = ()
         self._resident_bytes = 0
         self._lock = threading.Lock()
+        self._tls = threading.local()
+        self._device = torch.cuda.current_device() if stream is not None else None
+        self._pool = concurrent.futures.ThreadPoolExecutor(max_workers=creators) if creators > 0 else None
         self.ticks = 0
         self.rejected: List[Request] = []
 
@@ -135,48 +157,75 @@ class Server:
 
     def idle(self) -> bool:
         with self._lock:
-            return not self.queue and not self.active
+            return (not self.queue and not self.active and not self.staged and not self._creating
+                    and not self._retiring)
 
-    # -- admission by free HBM
+    # -- admission by the memory budget
     def _free_bytes(self) -> int:
-        free, _ = self._torch.cuda.mem_get_info()
-        if self.memory_budget is not None:
-            free = min(free, self.memory_budget - self._resident_bytes)
-        return free
+        return self.memory_budget - self._resident_bytes
+
+    def _create(self, req: Request) -> HGP:
+        """The request's device state, on the calling thread's upload stream."""
+        stream = None
+        if self.stream is not None:
+            stream = getattr(self._tls, "stream", None)
+            if stream is None:
+                self._torch.cuda.set_device(self._device)
+                stream = self._tls.stream = self._torch.cuda.Stream()
+        return HGP(req.n, req.m, req.net_off, req.pins, req.k, req.eps, req.part, req.vertex_w,
+                   req.net_w, subrounds=req.subrounds, seed=req.seed, stream=stream)
+
+    def _retire(self, req: Request, h: HGP) -> Request:
+        """Result to the host, device state released (on the request's own stream)."""
+        req.result = h.partition()
+        req.objective = h.objective()
+        h.close()
+        req.finished = self.clock()
+        return req
+
+    def _install(self, req: Request, h: HGP):
+        req.admitted = self.clock()
+        self._handles[req.rid] = h
+        self._done_rounds[req.rid] = 0
+        self._stats[req.rid] = []
+        self.staged.append(req)
 
     def _admit(self):
-        while True:
+        while len(self.staged) + len(self._creating) < self.max_staged:
             with self._lock:
-                if not self.queue or len(self.active) >= self.max_active:
+                if not self.queue:
                     return
                 req = self.queue[0]
             need = req.footprint()
-            if need + self.reserve > self._free_bytes():
-                if self.active:
+            if need > self._free_bytes():
+                if self.active or self.staged or self._creating:
                     return                      # wait for a resident request to finish
-                if self.memory_budget is not None and need > self.memory_budget:
+                if need > self.memory_budget:
                     with self._lock:            # can never fit: refuse it
                         self.queue.popleft()
                     self.rejected.append(req)
                     continue
             with self._lock:
                 self.queue.popleft()
-            h = HGP(req.n, req.m, req.net_off, req.pins, req.k, req.eps, req.part, req.vertex_w,
-                    req.net_w, subrounds=req.subrounds, seed=req.seed, stream=self.stream)
-            req.admitted = self.clock()
-            self._handles[req.rid] = h
-            self._done_rounds[req.rid] = 0
-            self._stats[req.rid] = []
             self._resident_bytes += need
             req._bytes = need
-            self.active.append(req)
+            if self._pool is not None:
+                self._creating.append((req, self._pool.submit(self._create, req)))
+            else:
+                self._install(req, self._create(req))
 
-    # -- one tick
-    def step(self) -> List[Request]:
-        """Admit what fits, run one round for every resident request, retire finished ones."""
-        self._admit()
-        if not self.active:
-            return []
+    def _collect(self, block: bool):
+        """Stages the created requests, in admission order; with `block`, waits for the first."""
+        while self._creating and (block or self._creating[0][1].done()):
+            req, fut = self._creating.popleft()
+            self._install(req, fut.result())
+            block = False
+
+    def _promote(self):
+        while self.staged and len(self.active) < self.max_active:
+            self.active.append(self.staged.popleft())
+
+    def _ensure_batch(self):
         key = tuple(r.rid for r in self.active)
         if key != self._batch_key:
             if self._batch is not None:
@@ -184,31 +233,60 @@ class Server:
             self._batch = Batch([self._handles[rid] for rid in key], graph=self.graph,
                                 stream=self.stream)
             self._batch_key = key
-        st = self._batch.refine(1)
-        self.ticks += 1
+
+    # -- one tick
+    def step(self) -> List[Request]:
+        """Queue the next rounds of the resident requests, admit arrivals while they run,
+        retire the requests that are done, and let the staged ones join."""
+        rounds = 0
+        if self.active:
+            self._ensure_batch()
+            rounds = min(r.rounds - self._done_rounds[r.rid] for r in self.active)
+            self._batch.refine(rounds, stats=False)
+            self.ticks += 1
+        self._admit()
         finished = []
-        for i, req in enumerate(self.active):
-            self._stats[req.rid].append(st[i, 0])
-            self._done_rounds[req.rid] += 1
-            if self._done_rounds[req.rid] >= req.rounds:
-                finished.append(req)
+        if rounds:
+            st = self._batch.stats(rounds)
+            for i, req in enumerate(self.active):
+                self._stats[req.rid].extend(st[i])
+                self._done_rounds[req.rid] += rounds
+                if self._done_rounds[req.rid] >= req.rounds:
+                    finished.append(req)
         if finished:
             done_ids = {r.rid for r in finished}
-            keep = []
-            for req in self.active:
-                if req.rid in done_ids:
-                    h = self._handles.pop(req.rid)
-                    req.result = h.partition()
-                    req.objective = h.objective()
-                    req.stats = np.array(self._stats.pop(req.rid), dtype=np.int64)
-                    req.finished = self.clock()
-                    h.close()
-                    self._done_rounds.pop(req.rid)
-                    self._resident_bytes -= req._bytes
+            for req in finished:
+                h = self._handles.pop(req.rid)
+                req.stats = np.array(self._stats.pop(req.rid), dtype=np.int64)
+                self._done_rounds.pop(req.rid)
+                if self._pool is not None:
+                    self._retiring.append((req, self._pool.submit(self._retire, req, h)))
                 else:
-                    keep.append(req)
-            self.active = keep
-        return finished
+                    self._retiring.append((req, None))
+                    self._retire(req, h)
+            self.active = [r for r in self.active if r.rid not in done_ids]
+        out = self._collect_retired(block=False)
+        if out:
+            self._admit()
+        self._collect(block=not self.active and not self.staged)
+        if not self.active and not self.staged and not self._creating and self._retiring:
+            out.extend(self._collect_retired(block=True))
+            self._admit()
+            self._collect(block=not self.staged)
+        self._promote()
+        return out
+
+    def _collect_retired(self, block: bool) -> List[Request]:
+        """Requests whose results reached the host (their memory is free again), in order."""
+        out = []
+        while self._retiring and (block or self._retiring[0][1] is None or self._retiring[0][1].done()):
+            req, fut = self._retiring.popleft()
+            if fut is not None:
+                fut.result()
+            self._resident_bytes -= req._bytes
+            out.append(req)
+            block = False
+        return out
 
     def run_until_idle(self) -> List[Request]:
         out = []
@@ -217,6 +295,15 @@ class Server:
         return out
 
     def close(self):
+        while self._creating:
+            req, fut = self._creating.popleft()
+            try:
+                fut.result().close()
+            except Exception:
+                pass
+        if self._pool is not None:
+            self._pool.shutdown(wait=True)
+        self._retiring.clear()
         if self._batch is not None:
             self._batch.close()
             self._batch = None

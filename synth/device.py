@@ -23,22 +23,48 @@ _KS = (2, 4, 8, 16, 32)
 
 def serving_requests(seed: int, count: int, p_lo: int = 10_000, p_hi: int = 5_000_000,
                      device="cuda", pin_memory: bool = True):
-    """`count` planted requests (``synth.Hypergraph``, 3 rounds each) drawn from one seed."""
+    """`count` planted requests (``synth.Hypergraph``, 3 rounds each) drawn from one seed.
+
+    All requests are drawn on the device first; their arrays are then copied into one host
+    buffer (page-locked unless pin_memory is False) and returned as views into it, so the
+    whole set costs one host allocation."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     hgen = np.random.Generator(np.random.PCG64(np.random.SeedSequence(int(seed))))
-    out = []
+    drawn = []
     for i in range(count):
         P_target = math.exp(hgen.uniform(math.log(p_lo), math.log(p_hi)))
         n = int(math.ceil(P_target / 6.0))
         k = int(hgen.choice(_KS))
-        out.append(_planted(gen, n, k, device, pin_memory, f"request[{i}] n=m={n} k={k}"))
+        drawn.append((n, k, f"request[{i}] n=m={n} k={k}", _planted(gen, n, k, device)))
+    # one host buffer for every array, each slice 8-byte aligned
+    sizes = [[t.numel() * t.element_size() for t in arrs] for _, _, _, arrs in drawn]
+    total = sum((b + 7) // 8 * 8 for row in sizes for b in row)
+    buf = torch.empty(max(8, total), dtype=torch.uint8, pin_memory=pin_memory)
+    out, off = [], 0
+    views = []
+    for (n, k, name, arrs), row in zip(drawn, sizes):
+        host = []
+        for t, b in zip(arrs, row):
+            dst = buf[off:off + b]
+            dst.copy_(t.view(torch.uint8).reshape(-1), non_blocking=True)
+            host.append((off, b, t.dtype))
+            off += (b + 7) // 8 * 8
+        views.append((n, k, name, host))
+    torch.cuda.synchronize() if str(device).startswith("cuda") else None
+    base = buf.numpy()
+    np_types = {torch.int64: np.int64, torch.int32: np.int32}
+    for n, k, name, host in views:
+        a = [base[o:o + b].view(np_types[dt]) for o, b, dt in host]
+        out.append(Hypergraph(name, n, n, k, 0.03, a[0], a[1], a[2], None, None, 3))
+    del drawn
     return out
 
 
-def _planted(gen, n: int, k: int, device, pin_memory: bool, name: str,
-             p_in: float = 0.8, f: float = 0.3, rate: float = 4.0) -> Hypergraph:
+def _planted(gen, n: int, k: int, device, p_in: float = 0.8, f: float = 0.3, rate: float = 4.0):
+    """Device arrays (net_off int64[m+1], pins int32[P], part int32[n]) of one planted
+    request with m = n nets of size 2 + Poisson(rate) before de-duplication."""
     import torch
     m = n
     i64 = torch.int64
@@ -65,10 +91,4 @@ def _planted(gen, n: int, k: int, device, pin_memory: bool, name: str,
     part = group.clone()
     sel = torch.randperm(n, generator=gen, device=device)[: int(round(f * n))]
     part[sel] = torch.randint(0, k, (sel.numel(),), generator=gen, device=device)
-    part = part.to(torch.int32)
-
-    def host(t):
-        h = torch.empty(t.shape, dtype=t.dtype, pin_memory=pin_memory)
-        h.copy_(t)
-        return h.numpy()
-    return Hypergraph(name, n, m, k, 0.03, host(off), host(pins), host(part), None, None, 3)
+    return off, pins, part.to(torch.int32)

@@ -110,3 +110,39 @@ def test_request_sizes_against_oracle():
         part, obj, st = _alone(r)
         np.testing.assert_array_equal(part, r.result)
         assert obj == r.objective
+
+
+def test_concurrent_creation_from_threads():
+    """Handles created at the same time from several host threads (each on its own stream, as
+    the server's creator threads do), with k and Phi widths differing from thread to thread,
+    equal handles created one after another."""
+    import concurrent.futures
+    import threading
+    from paper_2010_10272_gb300 import HGP
+    specs = [(2 + (i % 5) * 7, 3000 + 500 * (i % 7)) for i in range(48)]
+    hgs = [synth.random_small(880 + i, n, n, k, max_size=7 + (i % 3) * 150, weighted=i % 2 == 0, rounds=2)
+           for i, (k, n) in enumerate(specs)]
+    tls = threading.local()
+    dev = torch.cuda.current_device()
+
+    def make(hg):
+        s = getattr(tls, "s", None)
+        if s is None:
+            torch.cuda.set_device(dev)
+            s = tls.s = torch.cuda.Stream()
+        h = HGP.from_hypergraph(hg, stream=s)
+        st = h.refine(2)
+        out = (h.partition(), st[:, :5].copy(), h.info()["phi_width"])
+        h.close()
+        return out
+
+    for _ in range(2):
+        with concurrent.futures.ThreadPoolExecutor(8) as ex:
+            got = list(ex.map(make, hgs))
+        for hg, (part, st, w) in zip(hgs, got):
+            h = HGP.from_hypergraph(hg)
+            np.testing.assert_array_equal(h.refine(2)[:, :5], st)
+            np.testing.assert_array_equal(h.partition(), part)
+            assert h.info()["phi_width"] == w
+            h.close()
+    assert len({w for _, _, w in got}) == 2          # both entry widths were created concurrently
