@@ -826,7 +826,7 @@ def serving_section(args, stream):
         return [Request.from_hypergraph(base + i, h) for i, h in enumerate(hgs)]
 
     def run(reqs, arrivals):
-        srv = Server(stream=stream)
+        srv = Server(stream=stream, creators=args.serve_creators, ctas_per_sm=args.serve_ctas)
         order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
         t_start = time.perf_counter()
         nxt, done = 0, []
@@ -872,6 +872,7 @@ def serving_section(args, stream):
                     "|e|=2+Poisson(4), k in {2,4,8,16,32}, 3 rounds each, every request distinct",
         "service_capacity_req_per_s": mu, "saturated_pin_rounds_per_s": sat["pin_rounds_per_s"],
         "saturated": sat, "poisson": rates, "generate_s": gen_s,
+        "server": {"creators": args.serve_creators, "ctas_per_sm": args.serve_ctas},
         "latency": "arrival -> partition on the host",
     }
 
@@ -919,6 +920,10 @@ def main():
     ap.add_argument("--serve-saturated", type=int, default=1000,
                     help="serving: requests of the saturated run that measures the capacity")
     ap.add_argument("--serve-seed", type=int, default=1)
+    ap.add_argument("--serve-creators", type=int, default=8,
+                    help="serving: threads creating and retiring request state")
+    ap.add_argument("--serve-ctas", type=int, default=0,
+                    help="serving: CTAs per SM of the batch's persistent kernels (0 = occupancy)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true",

@@ -148,14 +148,18 @@ __device__ __forceinline__ int pin_net(const int32_t *off33, int32_t i)
     return lo;
 }
 
-// pins in [0, n) and strictly increasing inside every net; the largest net size.  Offsets
-// were checked before (k_check_offsets).  A warp walks 32 nets' pins at once, coalesced.
+// pins in [0, n) and strictly increasing inside every net; the largest net size.  Runs after
+// k_check_offsets and does nothing if that found an error.  A warp walks 32 nets' pins at once,
+// coalesced.
 __global__ void __launch_bounds__(256) k_check_pins(const int32_t *off, const int32_t *pins, int32_t m, int32_t n,
                                                     int32_t *err, int32_t *max_size)
 {
     __shared__ int32_t off33_w[8][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *off33 = off33_w[wid];
+    // the offsets may only be trusted when the checks before found nothing (they ran to
+    // completion earlier on the same stream, so their flag is final)
+    if (*reinterpret_cast<volatile int32_t *>(err) & ERR_INVALID) return;
     const int64_t warps = (int64_t)gridDim.x * 8;
     int32_t local_max = 0;
     bool bad = false;
@@ -1086,9 +1090,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     if (nw_d) { k_check_nets<<<grid_for(m, 256), 256, 0, st>>>(nw_d, m, d.err); h->launches++; }
     CKF(cudaGetLastError());
     int32_t host_err[2] = {0, 0};
-    CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CKF(cudaStreamSynchronize(st));
-    if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
+    // one read-back for both checks: the pin check does nothing when the offsets were bad
     if (m > 0) {
         k_check_pins<<<grid_for(m, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
         CKF(cudaGetLastError());
@@ -1241,14 +1243,10 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
 
     unsigned long long *maxw_d = reinterpret_cast<unsigned long long *>(misc32 + 2);
     CKF(cudaMemsetAsync(maxw_d, 0, sizeof(unsigned long long), st));
+    // the result of this check is read with the block weights at the end (nothing in between
+    // depends on it)
     k_vertex_netweight<<<grid_for(n, 256), 256, 0, st>>>(vtx_off, inc, nw_d, n, d.err, maxw_d); h->launches++;
     CKF(cudaGetLastError());
-    unsigned long long maxw = 0;
-    CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CKF(cudaMemcpyAsync(&maxw, maxw_d, sizeof(maxw), cudaMemcpyDeviceToHost, st));
-    CKF(cudaStreamSynchronize(st));
-    if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
-    h->max_vertex_netweight = (int64_t)maxw;
 
     // ---- state
     uint8_t *part = nullptr;
@@ -1321,10 +1319,15 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     rc = init_state(h);
     if (rc != HGP_OK) return fail(rc);
 
-    // ---- L_max = floor((1 + eps) * ceil(c(V) / k))  (Sec. 2)
+    // ---- L_max = floor((1 + eps) * ceil(c(V) / k))  (Sec. 2); the incident-weight check
     int64_t bw[64];
+    unsigned long long maxw = 0;
     CKF(cudaMemcpyAsync(bw, d.bw, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(&maxw, maxw_d, sizeof(maxw), cudaMemcpyDeviceToHost, st));
     CKF(cudaStreamSynchronize(st));
+    if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
+    h->max_vertex_netweight = (int64_t)maxw;
     int64_t total = 0;
     for (int i = 0; i < k; ++i) total += bw[i];
     h->total_weight = total;

@@ -114,11 +114,14 @@ class Server:
     memory_budget: device bytes the server may hold for requests (default: the free device
     memory when the server starts, minus reserve_bytes).  max_active: requests refined at once;
     max_staged: requests created (or being created) ahead of the batch they will join;
-    creators: threads that create and retire request state (0: the serving thread itself)."""
+    creators: threads that create and retire request state (0: the serving thread itself);
+    ctas_per_sm: persistent grid of the batch's gain and apply kernels (0: by occupancy; fewer
+    leave room on each SM for the creations' kernels)."""
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
                  memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
-                 graph: bool = False, creators: int = 4, clock=time.perf_counter):
+                 graph: bool = False, creators: int = 8, ctas_per_sm: int = 0,
+                 clock=time.perf_counter):
         import torch
         self._torch = torch
         self.stream = stream
@@ -130,6 +133,7 @@ class Server:
         self.max_active = int(max_active)
         self.max_staged = int(max_staged)
         self.graph = graph
+        self.ctas_per_sm = int(ctas_per_sm)
         self.clock = clock
         self.queue: Deque[Request] = collections.deque()
         self.staged: Deque[Request] = collections.deque()
@@ -170,8 +174,9 @@ class Server:
         if self.stream is not None:
             stream = getattr(self._tls, "stream", None)
             if stream is None:
+                # high priority: a creation's short kernels go ahead of queued batch kernels
                 self._torch.cuda.set_device(self._device)
-                stream = self._tls.stream = self._torch.cuda.Stream()
+                stream = self._tls.stream = self._torch.cuda.Stream(priority=-1)
         return HGP(req.n, req.m, req.net_off, req.pins, req.k, req.eps, req.part, req.vertex_w,
                    req.net_w, subrounds=req.subrounds, seed=req.seed, stream=stream)
 
@@ -231,7 +236,8 @@ class Server:
             if self._batch is not None:
                 self._batch.close()
             self._batch = Batch([self._handles[rid] for rid in key], graph=self.graph,
-                                stream=self.stream)
+                                stream=self.stream, gain_ctas_per_sm=self.ctas_per_sm,
+                                apply_ctas_per_sm=self.ctas_per_sm)
             self._batch_key = key
 
     # -- one tick
