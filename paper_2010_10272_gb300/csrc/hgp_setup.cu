@@ -1344,6 +1344,8 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     }
     rc = ensure_stats(h, 16);
     if (rc != HGP_OK) return fail(rc);
+    // the event a batch records its end on (see settle); made here, on the creating thread
+    CKF(cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
     *out = h;
     return HGP_OK;
 #undef CKF

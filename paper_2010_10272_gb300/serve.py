@@ -79,6 +79,7 @@ class Request:
     net_w: Optional[np.ndarray] = None
     subrounds: int = 4
     seed: int = 0
+    max_net_size: Optional[int] = None    # largest net, if the producer knows it (else computed once)
     arrival: float = 0.0
     # filled by the server
     admitted: float = 0.0
@@ -89,6 +90,7 @@ class Request:
 
     @classmethod
     def from_hypergraph(cls, rid, hg, rounds=None, **kw):
+        kw.setdefault("max_net_size", getattr(hg, "max_net_size", None))
         return cls(rid, hg.n, hg.m, hg.net_off, hg.pins, hg.k, hg.eps, hg.part,
                    hg.rounds if rounds is None else rounds, hg.vertex_w, hg.net_w, **kw)
 
@@ -97,11 +99,16 @@ class Request:
         return int(self.net_off[-1])
 
     def footprint(self) -> int:
-        sizes = np.diff(self.net_off)
-        return estimate_device_bytes(self.n, self.m, self.num_pins, self.k,
-                                     int(sizes.max()) if sizes.size else 0,
-                                     self.vertex_w is not None, self.net_w is not None,
-                                     self.subrounds)
+        """Device bytes the request's state needs (computed once; admission asks repeatedly)."""
+        fp = getattr(self, "_footprint", None)
+        if fp is None:
+            if self.max_net_size is None:
+                sizes = np.diff(self.net_off)
+                self.max_net_size = int(sizes.max()) if sizes.size else 0
+            fp = self._footprint = estimate_device_bytes(
+                self.n, self.m, self.num_pins, self.k, self.max_net_size, self.vertex_w is not None,
+                self.net_w is not None, self.subrounds)
+        return fp
 
     @property
     def latency(self) -> float:

@@ -37,8 +37,11 @@ def serving_requests(seed: int, count: int, p_lo: int = 10_000, p_hi: int = 5_00
         P_target = math.exp(hgen.uniform(math.log(p_lo), math.log(p_hi)))
         n = int(math.ceil(P_target / 6.0))
         k = int(hgen.choice(_KS))
-        drawn.append((n, k, f"request[{i}] n=m={n} k={k}", _planted(gen, n, k, device)))
+        arrs = _planted(gen, n, k, device)
+        drawn.append((n, k, f"request[{i}] n=m={n} k={k}", arrs))
     # one host buffer for every array, each slice 8-byte aligned
+    # largest net of each request (one device reduction per request, read back together)
+    maxes = torch.stack([(a[0][1:] - a[0][:-1]).max() for _, _, _, a in drawn]).cpu().tolist() if drawn else []
     sizes = [[t.numel() * t.element_size() for t in arrs] for _, _, _, arrs in drawn]
     total = sum((b + 7) // 8 * 8 for row in sizes for b in row)
     buf = torch.empty(max(8, total), dtype=torch.uint8, pin_memory=pin_memory)
@@ -55,9 +58,11 @@ def serving_requests(seed: int, count: int, p_lo: int = 10_000, p_hi: int = 5_00
     torch.cuda.synchronize() if str(device).startswith("cuda") else None
     base = buf.numpy()
     np_types = {torch.int64: np.int64, torch.int32: np.int32}
-    for n, k, name, host in views:
+    for (n, k, name, host), mx in zip(views, maxes):
         a = [base[o:o + b].view(np_types[dt]) for o, b, dt in host]
-        out.append(Hypergraph(name, n, n, k, 0.03, a[0], a[1], a[2], None, None, 3))
+        hg = Hypergraph(name, n, n, k, 0.03, a[0], a[1], a[2], None, None, 3)
+        hg.max_net_size = int(mx)      # known from the draw; spares consumers a pass over net_off
+        out.append(hg)
     del drawn
     return out
 
