@@ -45,6 +45,9 @@ def test_host_only_functions(lib):
     assert p.strerror(99) == "unknown status"
     o = p.default_options()
     assert o.subrounds == 4 and o.phi_width == 0 and o.seed == 0 and not o.cuda_stream
+    # argument checks that return before any CUDA call
+    assert lib.hgp_set_pool_retention(-1) == 1
+    assert lib.hgp_batch_get_stats(None, 1, None) == 1
 
 
 def test_struct_layout_matches_header(lib):

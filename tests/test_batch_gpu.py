@@ -128,3 +128,52 @@ def test_full_batch_workload_equals_oracle():
     b.close()
     for h in hs:
         h.close()
+
+
+def test_batch_statistics_read_later_and_members_on_other_streams():
+    """A batch call queued without statistics, whose statistics are read afterwards
+    (hgp_batch_get_stats), equals a call that returns them; members created on their own
+    streams are ordered after the batch (read-backs on their streams see its result); a member
+    may be destroyed before the batch if the batch is then only destroyed."""
+    from paper_2010_10272_gb300 import HGP, Batch, HGPError
+    members = _members()[:6]
+    streams = [torch.cuda.Stream() for _ in members]
+    hs = [HGP.from_hypergraph(hg, subrounds=S, phi_width=pw, seed=3, stream=st)
+          for (hg, S, pw), st in zip(members, streams)]
+    b = Batch(hs, graph=False, stream=torch.cuda.Stream())
+    assert b.refine(3, stats=False) is None
+    got = b.stats(3)
+    with pytest.raises(HGPError) as ei:
+        b.stats(2)                                   # not the last call's round count
+    assert ei.value.code == 1
+    for i, (hg, S, pw) in enumerate(members):
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=3)
+        want, _ = o.refine(3)
+        np.testing.assert_array_equal(got[i, :, :5], want)
+        np.testing.assert_array_equal(hs[i].partition(), o.partition())
+    hs[0].close()                                    # before the batch
+    b.close()
+    np.testing.assert_array_equal(hs[1].refine(1)[:, :5],
+                                  oracle.Oracle.from_hypergraph(members[1][0], subrounds=members[1][1], seed=3)
+                                  .refine(4)[0][3:])
+    for h in hs[1:]:
+        h.close()
+
+
+def test_pool_retention_keeps_results():
+    """With the library's pool keeping freed memory (hgp_set_pool_retention), handles created
+    and destroyed in a loop give the same results as without."""
+    from paper_2010_10272_gb300 import HGP
+    from paper_2010_10272_gb300.native import set_pool_retention
+    hg = synth.random_small(71, 20000, 18000, 8, max_size=9, weighted=True, rounds=3)
+    ref = HGP.from_hypergraph(hg, subrounds=4)
+    want = ref.refine(3)
+    ref.close()
+    try:
+        set_pool_retention(1 << 30)
+        for _ in range(3):
+            h = HGP.from_hypergraph(hg, subrounds=4)
+            np.testing.assert_array_equal(h.refine(3), want)
+            h.close()
+    finally:
+        set_pool_retention(0)
