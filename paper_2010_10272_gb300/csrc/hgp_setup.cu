@@ -168,10 +168,21 @@ __global__ void __launch_bounds__(256) k_check_pins(const int32_t *off, const in
         const int32_t base = net_group(off, e0, m, off33, sz);
         local_max = max(local_max, sz);
         const int32_t total = off33[32];
-        for (int32_t i = lane; i < total; i += 32) {
-            const int32_t v = pins[base + i];
-            if (v < 0 || v >= n) bad = true;
-            if (i > off33[pin_net(off33, i)] && pins[base + i - 1] >= v) bad = true;
+        for (int32_t i0 = lane; i0 < total; i0 += 128) {   // four pins (and predecessors) per lane
+            int32_t vq[4], pq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t i = i0 + 32 * q;
+                vq[q] = i < total ? pins[base + i] : 0;
+                pq[q] = i < total && i > 0 ? pins[base + i - 1] : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t i = i0 + 32 * q;
+                if (i >= total) continue;
+                if (vq[q] < 0 || vq[q] >= n) bad = true;
+                if (i > off33[pin_net(off33, i)] && pq[q] >= vq[q]) bad = true;
+            }
         }
         __syncwarp();
     }
@@ -268,9 +279,17 @@ __global__ void __launch_bounds__(256) k_nr_pins(const int32_t *off, const int32
         }
         __syncwarp();
         const int32_t total = off33[32];
-        for (int32_t i = lane; i < total; i += 32) {
-            const int sl = pin_net(off33, i);
-            pins_int[dst_w[wid][sl] + (i - off33[sl])] = pins[src + i];
+        for (int32_t i0 = lane; i0 < total; i0 += 128) {   // four loads in flight per lane
+            int32_t vq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vq[q] = i0 + 32 * q < total ? pins[src + i0 + 32 * q] : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t i = i0 + 32 * q;
+                if (i >= total) continue;
+                const int sl = pin_net(off33, i);
+                pins_int[dst_w[wid][sl] + (i - off33[sl])] = vq[q];
+            }
         }
         __syncwarp();
     }
@@ -400,13 +419,21 @@ __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const in
             int32_t sz;
             const int32_t base = net_group(off, e0, e_hi, off33, sz);
             const int32_t total = off33[32];
-            for (int32_t i = lane; i < total; i += 32) {
-                const int32_t v = pins[base + i];
-                const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
-                if (pass == 1) {
-                    const int sl = pin_net(off33, i);
-                    const uint32_t ef = (uint32_t)(e0 + sl) | (off33[sl + 1] - off33[sl] > narrow_max ? kWideFlag : 0u);
-                    pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+            // four pins per lane are loaded before any is used (their latencies overlap)
+            for (int32_t i0 = lane; i0 < total; i0 += 128) {
+                int32_t vq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vq[q] = i0 + 32 * q < total ? pins[base + i0 + 32 * q] : -1;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (vq[q] < 0) continue;
+                    const int32_t i = i0 + 32 * q, v = vq[q];
+                    const int32_t pos = atomicAdd(&cur[v >> bshift], 1);
+                    if (pass == 1) {
+                        const int sl = pin_net(off33, i);
+                        const uint32_t ef = (uint32_t)(e0 + sl) | (off33[sl + 1] - off33[sl] > narrow_max ? kWideFlag : 0u);
+                        pairs[pos] = ((unsigned long long)(uint32_t)v << 32) | ef;
+                    }
                 }
             }
             __syncwarp();
@@ -481,6 +508,8 @@ __global__ void __launch_bounds__(256) k_tp_scatter_big(const int32_t *off, cons
 // vtx_off, then the nets of the bucket's pairs into inc.  SMEM: the bucket's counters live in
 // shared memory (buckets of at most 2^kTpSmemShift vertices); otherwise in cursor (zeroed
 // int32[n], global).
+constexpr int kTpPlaceBatch = 8;
+
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pairs, const int32_t *bucket_off,
                                                    int bshift, int32_t n, int32_t nb, int32_t *cursor,
@@ -497,8 +526,19 @@ __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pai
     if (SMEM)
         for (int64_t i = threadIdx.x; i < v1 - v0; i += blockDim.x) sc[i] = 0;
     __syncthreads();
-    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x)
-        atomicAdd(&cnt[(int32_t)(pairs[i] >> 32) - v0], 1);
+    // kTpPlaceBatch pairs per thread are loaded before any is used (the loads' latencies overlap)
+    const int32_t step = (int32_t)blockDim.x * kTpPlaceBatch;
+    for (int32_t i0 = p0 + threadIdx.x; i0 < p1; i0 += step) {
+        unsigned long long pr[kTpPlaceBatch];
+#pragma unroll
+        for (int q = 0; q < kTpPlaceBatch; ++q) {
+            const int32_t i = i0 + q * (int32_t)blockDim.x;
+            pr[q] = i < p1 ? pairs[i] : ~0ull;            // read again below: keep in L2
+        }
+#pragma unroll
+        for (int q = 0; q < kTpPlaceBatch; ++q)
+            if (pr[q] != ~0ull) atomicAdd(&cnt[(int32_t)(pr[q] >> 32) - v0], 1);
+    }
     __syncthreads();
     int32_t carry = p0;
     for (int64_t base = v0; base < v1; base += blockDim.x) {
@@ -513,10 +553,19 @@ __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pai
     }
     if (bkt == nb - 1 && threadIdx.x == 0) vtx_off[n] = p1;
     __syncthreads();
-    for (int32_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-        const unsigned long long pr = pairs[i];
-        const int32_t pos = atomicAdd(&cnt[(int32_t)(pr >> 32) - v0], 1);
-        inc[pos] = (int32_t)(uint32_t)pr;
+    for (int32_t i0 = p0 + threadIdx.x; i0 < p1; i0 += step) {
+        unsigned long long pr[kTpPlaceBatch];
+#pragma unroll
+        for (int q = 0; q < kTpPlaceBatch; ++q) {
+            const int32_t i = i0 + q * (int32_t)blockDim.x;
+            pr[q] = i < p1 ? __ldcs(&pairs[i]) : ~0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < kTpPlaceBatch; ++q) {
+            if (pr[q] == ~0ull) continue;
+            const int32_t pos = atomicAdd(&cnt[(int32_t)(pr[q] >> 32) - v0], 1);
+            inc[pos] = (int32_t)(uint32_t)pr[q];
+        }
     }
 }
 
