@@ -380,6 +380,16 @@ def run_gpu(args, world, rank, local):
                           "peak_gathers_per_s": g_rate,
                           "frac": gathers_per_launch / (gain_ms / 1e3) / g_rate,
                           "peak_kind": "measured random 32-byte gathers from a 1.6 GB array (hgp_probe_gather)"}
+    # the apply step's ceiling: two pin-count atomics with results per moved incidence, against
+    # the device's measured rate of random atomics with results on an array of the Phi table's size
+    from paper_2010_10272_gb300.native import probe_atomic
+    a_ms_probe, a_rate = probe_atomic(6400 << 20, 50_000_000)
+    apply_ms = prof["apply"][0] / max(1, prof["apply"][1])
+    atomics_per_launch = 2.0 * float(stats[:, 5].sum()) / (R * S)
+    roofline["atomic"] = {"kernel": "k_apply", "achieved_atomics_per_s": atomics_per_launch / (apply_ms / 1e3),
+                          "peak_atomics_per_s": a_rate,
+                          "frac": atomics_per_launch / (apply_ms / 1e3) / a_rate,
+                          "peak_kind": "measured random 32-bit atomics with results on a 6.4 GB array (hgp_probe_atomic)"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
               for k, v in prof.items()}
     other = "apply" if kern == "gain" else "gain"

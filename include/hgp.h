@@ -382,6 +382,14 @@ int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *moves, int64_t 
  */
 int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *ms_out, double *gathers_per_s);
 
+/*
+ * Measurement helper (no counterpart in the paper): times n_atomics 32-bit atomic additions,
+ * each at a random word of a freshly allocated array of array_bytes bytes and each returning
+ * the old value that the thread then uses (the form of the apply step's pin-count updates), and
+ * returns the time and the rate.  Allocates and frees its own buffers.
+ */
+int hgp_probe_atomic(int64_t array_bytes, int64_t n_atomics, double *ms_out, double *atomics_per_s);
+
 /* Frees all device memory of the handle (NULL is allowed).  The releases are queued on the
  * handle's stream behind its pending work, so the call returns without waiting for the device;
  * the memory returns to the library's pool (see hgp_set_pool_retention). */

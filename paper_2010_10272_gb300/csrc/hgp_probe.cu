@@ -1,4 +1,4 @@
-// libhgp: measurement of the device's random-gather rate.
+// libhgp: measurement of the device's random-gather and random-atomic rates.
 //
 // The gain and apply steps are bound by random accesses to per-net data (one record per
 // incidence, Phi entries per moved pin), not by streaming bandwidth: on an array much larger
@@ -27,12 +27,24 @@ __global__ void k_probe_gather(const uint4 *__restrict__ rec, int64_t count, int
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
-}  // namespace
-
-extern "C" int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *ms_out,
-                                double *gathers_per_s)
+// each thread adds 1 at pseudo-random 32-bit words in [0, count) with atomics whose old value
+// it consumes (the form of the apply step's pin-count updates)
+__global__ void k_probe_atomic(uint32_t *__restrict__ words, int64_t count, int64_t n_ops, uint32_t *out)
 {
-    if (array_bytes < 64 || n_gathers < 1 || !ms_out || !gathers_per_s) return HGP_ERR_INVALID;
+    uint32_t acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_ops;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = (int64_t)(splitmix64_output((uint64_t)i ^ 0x5bd1e995ull) % (uint64_t)count);
+        acc ^= atomicAdd(words + idx, 1u);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+enum { PROBE_GATHER = 0, PROBE_ATOMIC = 1 };
+
+int probe(int kind, int64_t array_bytes, int64_t n_ops, double *ms_out, double *ops_per_s)
+{
+    if (array_bytes < 64 || n_ops < 1 || !ms_out || !ops_per_s) return HGP_ERR_INVALID;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -51,7 +63,10 @@ extern "C" int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *
     float best = 0.f;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         cudaEventRecord(a, st);
-        k_probe_gather<<<grid, block, 0, st>>>(reinterpret_cast<const uint4 *>(buf), count, n_gathers, out);
+        if (kind == PROBE_GATHER)
+            k_probe_gather<<<grid, block, 0, st>>>(reinterpret_cast<const uint4 *>(buf), count, n_ops, out);
+        else
+            k_probe_atomic<<<grid, block, 0, st>>>(reinterpret_cast<uint32_t *>(buf), count * 8, n_ops, out);
         cudaEventRecord(b, st);
         e = cudaEventSynchronize(b);
         float ms = 0.f;
@@ -68,6 +83,19 @@ extern "C" int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *
         return e == cudaErrorMemoryAllocation ? HGP_ERR_OOM : HGP_ERR_CUDA;
     }
     *ms_out = best;
-    *gathers_per_s = (double)n_gathers / (best / 1e3);
+    *ops_per_s = (double)n_ops / (best / 1e3);
     return HGP_OK;
+}
+
+}  // namespace
+
+extern "C" int hgp_probe_atomic(int64_t array_bytes, int64_t n_atomics, double *ms_out, double *atomics_per_s)
+{
+    return probe(PROBE_ATOMIC, array_bytes, n_atomics, ms_out, atomics_per_s);
+}
+
+extern "C" int hgp_probe_gather(int64_t array_bytes, int64_t n_gathers, double *ms_out,
+                                double *gathers_per_s)
+{
+    return probe(PROBE_GATHER, array_bytes, n_gathers, ms_out, gathers_per_s);
 }

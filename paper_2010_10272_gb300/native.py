@@ -129,6 +129,8 @@ def load_library():
         lib.hgp_batch_destroy.restype = None
         lib.hgp_probe_gather.argtypes = [i64, i64, P, P]
         lib.hgp_probe_gather.restype = ctypes.c_int
+        lib.hgp_probe_atomic.argtypes = [i64, i64, P, P]
+        lib.hgp_probe_atomic.restype = ctypes.c_int
         lib.hgp_destroy.argtypes = [P]
         lib.hgp_destroy.restype = None
         _lib = lib
@@ -449,6 +451,16 @@ def probe_gather(array_bytes: int = 1600 << 20, n_gathers: int = 86_000_000):
     ms, rate = ctypes.c_double(), ctypes.c_double()
     _check(lib.hgp_probe_gather(int(array_bytes), int(n_gathers), ctypes.byref(ms), ctypes.byref(rate)),
            "hgp_probe_gather")
+    return ms.value, rate.value
+
+
+def probe_atomic(array_bytes: int = 6400 << 20, n_atomics: int = 50_000_000):
+    """Random 32-bit atomic-add rate (old value consumed) of the current device: (ms, atomics
+    per second)."""
+    lib = load_library()
+    ms, rate = ctypes.c_double(), ctypes.c_double()
+    _check(lib.hgp_probe_atomic(int(array_bytes), int(n_atomics), ctypes.byref(ms), ctypes.byref(rate)),
+           "hgp_probe_atomic")
     return ms.value, rate.value
 
 
