@@ -127,7 +127,7 @@ class Server:
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
                  memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
-                 graph: bool = False, creators: int = 8, ctas_per_sm: int = 0,
+                 graph: bool = False, creators: int = 8, ctas_per_sm: int = 0, join_at: int = 0,
                  clock=time.perf_counter):
         import torch
         self._torch = torch
@@ -141,6 +141,7 @@ class Server:
         self.max_staged = int(max_staged)
         self.graph = graph
         self.ctas_per_sm = int(ctas_per_sm)
+        self.join_at = int(join_at)
         self.clock = clock
         self.queue: Deque[Request] = collections.deque()
         self.staged: Deque[Request] = collections.deque()
@@ -234,6 +235,10 @@ class Server:
             block = False
 
     def _promote(self):
+        # join_at: 0 = staged requests join at every round boundary; otherwise they join only
+        # when at most join_at requests are still running (fewer, larger ticks)
+        if self.join_at and len(self.active) > self.join_at:
+            return
         while self.staged and len(self.active) < self.max_active:
             self.active.append(self.staged.popleft())
 
