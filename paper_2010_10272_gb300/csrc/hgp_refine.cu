@@ -608,9 +608,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
     __shared__ long long slack_w[kWarps][64];
     __shared__ unsigned long long tot_w[kWarps][64];
     __shared__ Dev dsm[B ? kWarps : 1];
+    __shared__ unsigned long long cnt_s[2];
+    __shared__ int warps_done;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     tot_w[wid][lane] = 0;
     tot_w[wid][lane + 32] = 0;
+    if (tid == 0) { cnt_s[0] = 0; cnt_s[1] = 0; warps_done = 0; }
+    __syncthreads();   // before any warp can add into another warp's slots (at its end)
     GainInst<Lam> gi;
     int32_t nelig = 0, ncand = 0;
     int inst_prev = -1;
@@ -661,10 +665,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_gain(const Dev d0, const Dev *d
         // one instance: the warps add their partial sums into warp 0's slots as they finish and
         // the last warp of the CTA flushes them with one atomic per block (no barrier, so warps
         // that finish early do not wait for the slowest one)
-        __shared__ unsigned long long cnt_s[2];
-        __shared__ int warps_done;
-        if (tid == 0) { cnt_s[0] = 0; cnt_s[1] = 0; warps_done = 0; }
-        __syncthreads();
         if (wid != 0) {
             for (int t = lane; t < 64; t += 32)
                 if (tot_w[wid][t]) atomicAdd(&tot_w[0][t], tot_w[wid][t]);
@@ -1231,9 +1231,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
     __shared__ unsigned long long bwd_w[kWarps][64];
     __shared__ ApplyWarp aw[kWarps];
     __shared__ Dev dsm[B ? kWarps : 1];
+    __shared__ unsigned long long objd, napp, mpins;
+    __shared__ int warps_done;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     bwd_w[wid][lane] = 0;
     bwd_w[wid][lane + 32] = 0;
+    if (tid == 0) { objd = 0; napp = 0; mpins = 0; warps_done = 0; }
+    __syncthreads();   // before any warp can add into another warp's slots (at its end)
     long long dobj = 0;
     int32_t nappr = 0, npins = 0, r = 0, nshared = 0;
     int inst_prev = -1;
@@ -1296,15 +1300,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply(const Dev d0, const Dev *
     }
     if (!B) {
         // as in k_gain: partial sums into warp 0's slots, the last warp to finish flushes
-        __shared__ unsigned long long objd, napp, mpins;
-        __shared__ int warps_done;
         for (int o = 16; o; o >>= 1) {
             dobj += __shfl_xor_sync(kFull, dobj, o);
             nappr += __shfl_xor_sync(kFull, nappr, o);
             npins += __shfl_xor_sync(kFull, npins, o);
         }
-        if (tid == 0) { objd = 0; napp = 0; mpins = 0; warps_done = 0; }
-        __syncthreads();
         if (wid != 0) {
             for (int t = lane; t < 64; t += 32)
                 if (bwd_w[wid][t]) atomicAdd(&bwd_w[0][t], bwd_w[wid][t]);
