@@ -234,7 +234,9 @@ void hgp_batch_default_options(hgp_batch_options *opt);
  * HGP_ERR_UNSUPPORTED for a handle created with the revert variant.  Members may live on other
  * streams than the batch: every hgp_batch_refine call then starts, on the device, after the
  * work already queued on those streams, and work queued on them afterwards (read-backs,
- * hgp_destroy) runs after the call; no call blocks the host for this. */
+ * hgp_destroy) runs after the call; no call blocks the host for this.  A handle may be a member
+ * of several batches on different streams: a call also starts after the last call of another
+ * batch that refined one of its members. */
 int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_options *opt,
                      hgp_batch **out);
 
@@ -244,10 +246,15 @@ int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_
 int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
 
 /* Statistics of the last hgp_batch_refine call, laid out as that call's `stats` argument;
- * `rounds` must equal that call's round count (else HGP_ERR_INVALID).  Waits for the batch's
- * stream.  Lets a caller queue a call without statistics, do host work while it runs, and
- * read them afterwards. */
+ * `rounds` must equal that call's round count (else HGP_ERR_INVALID).  Waits for that call
+ * only, not for work queued on the batch's stream after it.  Lets a caller queue a call without
+ * statistics, do host work (and queue further work, for example the next call of another
+ * batch) while it runs, and read them afterwards. */
 int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
+
+/* done: 1 if the last hgp_batch_refine call has finished on the device (or there was none),
+ * else 0.  Does not block. */
+int hgp_batch_query(hgp_batch *b, int32_t *done);
 
 /* Waits for the batch's queued work. */
 int hgp_batch_synchronize(hgp_batch *b);

@@ -2238,6 +2238,8 @@ struct hgp_batch {
     std::vector<cudaStream_t> member_streams;
     std::vector<cudaEvent_t> events;
     int32_t last_rounds = 0;                    // round count of the last hgp_batch_refine
+    cudaEvent_t ev_end = nullptr;               // recorded at the end of each hgp_batch_refine
+    cudaStream_t aux = nullptr;                 // statistics read-back of a call, after ev_end only
     struct Group {
         Plan plan;
         std::vector<int32_t> members;           // indices into hs
@@ -2372,16 +2374,9 @@ cudaError_t enqueue_batch(hgp_batch *b, int32_t rounds, int64_t *launch_counter)
 }  // namespace
 
 // waits for the batch's stream and unpacks the per-member statistics of its last call
-static int batch_stats_out(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
+static int batch_stats_unpack(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
 {
     const int32_t count = (int32_t)b->hs.size();
-    cudaError_t e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
-                                    cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return status_of(e);
-    }
     for (int32_t i = 0; i < count; ++i)
         for (int32_t rr = 0; rr < rounds; ++rr) {
             const int64_t *row = b->h_stats + ((int64_t)i * b->stats_cap + rr) * ST_N;
@@ -2395,6 +2390,19 @@ static int batch_stats_out(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
             o.reverted = row[ST_REV];
         }
     return HGP_OK;
+}
+
+static int batch_stats_out(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
+{
+    const int32_t count = (int32_t)b->hs.size();
+    cudaError_t e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return batch_stats_unpack(b, rounds, stats);
 }
 
 extern "C" {
@@ -2461,6 +2469,12 @@ int hgp_batch_create(hgp_handle *const *handles, int32_t count, const hgp_batch_
             hgp_batch_destroy(b);
             return HGP_ERR_CUDA;
         }
+    if (cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        b->ev_end = nullptr;
+        hgp_batch_destroy(b);
+        return HGP_ERR_CUDA;
+    }
     const int rc = build_groups(b, 8);
     if (rc != HGP_OK) {
         hgp_batch_destroy(b);
@@ -2476,10 +2490,19 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
     if (rounds == 0) return HGP_OK;
     for (hgp_handle *h : b->hs)
         if (h->next_round + rounds >= ((int64_t)1 << 30)) return HGP_ERR_UNSUPPORTED;
-    // the batch reads the handles' state on its own stream: after their streams' pending work
+    // the batch reads the handles' state on its own stream: after their streams' pending work,
+    // and after the last call of another batch that refined them (on another stream)
     for (size_t i = 0; i < b->member_streams.size(); ++i) {
         cudaError_t e = cudaEventRecord(b->events[i], b->member_streams[i]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[i], 0);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return status_of(e);
+        }
+    }
+    for (hgp_handle *h : b->hs) {
+        if (!h->after_batch) continue;
+        const cudaError_t e = cudaStreamWaitEvent(b->stream, h->ev_batch, 0);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
@@ -2527,6 +2550,11 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
         h->all_eligible = false;
     }
     b->last_rounds = rounds;
+    e = cudaEventRecord(b->ev_end, b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
     // later work on the members' own streams (read-backs, releases) must come after this call:
     // the call's end is recorded on each such member's event, which its next entry point waits on
     for (hgp_handle *h : b->hs) {
@@ -2545,7 +2573,42 @@ int hgp_batch_refine(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
 int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
 {
     if (!b || !stats || rounds < 1 || rounds != b->last_rounds) return HGP_ERR_INVALID;
-    return batch_stats_out(b, rounds, stats);
+    // waits for the last call only, not for work queued on the batch's stream after it (the
+    // next tick of a pipelined caller): the copy runs on a private stream after ev_end
+    cudaError_t e = cudaSuccess;
+    if (!b->aux) {
+        e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+        if (e != cudaSuccess) b->aux = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_end, 0);
+    if (e == cudaSuccess) {
+        const int32_t count = (int32_t)b->hs.size();
+        e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
+                            cudaMemcpyDeviceToHost, b->aux);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->aux);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    return batch_stats_unpack(b, rounds, stats);
+}
+
+int hgp_batch_query(hgp_batch *b, int32_t *done)
+{
+    if (!b || !done) return HGP_ERR_INVALID;
+    const cudaError_t e = cudaEventQuery(b->ev_end);
+    if (e == cudaErrorNotReady) {
+        (void)cudaGetLastError();
+        *done = 0;
+        return HGP_OK;
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    *done = 1;
+    return HGP_OK;
 }
 
 int hgp_batch_synchronize(hgp_batch *b)
@@ -2573,6 +2636,8 @@ void hgp_batch_destroy(hgp_batch *b)
     dev_free(b->d_stats, b->stream);
     free(b->h_stats);
     for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
+    if (b->ev_end) cudaEventDestroy(b->ev_end);
+    if (b->aux) cudaStreamDestroy(b->aux);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     (void)cudaGetLastError();
     delete b;

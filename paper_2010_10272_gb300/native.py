@@ -120,8 +120,9 @@ def load_library():
         lib.hgp_batch_synchronize.argtypes = [P]
         lib.hgp_batch_get_launch_count.argtypes = [P, P]
         lib.hgp_batch_get_stats.argtypes = [P, i32, P]
+        lib.hgp_batch_query.argtypes = [P, P]
         for name in ("hgp_batch_create", "hgp_batch_refine", "hgp_batch_synchronize",
-                     "hgp_batch_get_launch_count", "hgp_batch_get_stats"):
+                     "hgp_batch_get_launch_count", "hgp_batch_get_stats", "hgp_batch_query"):
             getattr(lib, name).restype = ctypes.c_int
         lib.hgp_set_pool_retention.argtypes = [i64]
         lib.hgp_set_pool_retention.restype = ctypes.c_int
@@ -406,9 +407,15 @@ class Batch:
         _check(self._lib.hgp_batch_refine(self._b, int(rounds), None), "hgp_batch_refine")
         return None
 
+    def done(self) -> bool:
+        """Whether the last refine call has finished on the device (does not block)."""
+        d = ctypes.c_int32(0)
+        _check(self._lib.hgp_batch_query(self._b, ctypes.byref(d)), "hgp_batch_query")
+        return bool(d.value)
+
     def stats(self, rounds: int):
-        """Statistics of the last refine call (of `rounds` rounds), waiting for it:
-        int64 [count x rounds x 7]."""
+        """Statistics of the last refine call (of `rounds` rounds), waiting for that call
+        only: int64 [count x rounds x 7]."""
         n = len(self.handles)
         buf = (RoundStats * max(1, n * rounds))()
         _check(self._lib.hgp_batch_get_stats(self._b, int(rounds), buf), "hgp_batch_get_stats")

@@ -160,6 +160,45 @@ def test_batch_statistics_read_later_and_members_on_other_streams():
         h.close()
 
 
+def test_batches_on_different_streams_share_members():
+    """Two batches on two streams over overlapping members, called alternately without reading
+    anything in between: each call starts after the other batch's last call on its members, and
+    a pipelined reader gets each call's statistics while the next call is already queued."""
+    from paper_2010_10272_gb300 import HGP, Batch
+    members = _members()[:6]
+    hs = [HGP.from_hypergraph(hg, subrounds=S, phi_width=pw, seed=5) for hg, S, pw in members]
+    b1 = Batch(hs[:4], graph=False, stream=torch.cuda.Stream())
+    b2 = Batch(hs[2:], graph=False, stream=torch.cuda.Stream())
+    calls = [(b1, 2), (b2, 1), (b1, 1), (b2, 2), (b1, 2)]
+    rounds = [0] * len(hs)
+    got = {i: [] for i in range(len(hs))}
+    prev = None
+    for b, r in calls:
+        b.refine(r, stats=False)
+        if prev is not None:                         # the previous call, read after this one is queued
+            pb, pr = prev
+            st = pb.stats(pr)
+            for j, h in enumerate(pb.handles):
+                got[hs.index(h)].append(st[j, :, :5])
+        prev = (b, r)
+        for h in b.handles:
+            rounds[hs.index(h)] += r
+    pb, pr = prev
+    st = pb.stats(pr)
+    for j, h in enumerate(pb.handles):
+        got[hs.index(h)].append(st[j, :, :5])
+    for i, (hg, S, pw) in enumerate(members):
+        o = oracle.Oracle.from_hypergraph(hg, subrounds=S, seed=5)
+        want, _ = o.refine(rounds[i])
+        np.testing.assert_array_equal(np.concatenate(got[i]), want)
+        np.testing.assert_array_equal(hs[i].partition(), o.partition())
+        assert hs[i].objective() == o.objective()
+    b1.close()
+    b2.close()
+    for h in hs:
+        h.close()
+
+
 def test_pool_retention_keeps_results():
     """With the library's pool keeping freed memory (hgp_set_pool_retention), handles created
     and destroyed in a loop give the same results as without."""
