@@ -4,17 +4,21 @@ Requests (a hypergraph, a start partition, a round count) are queued as they arr
 tick of the server
   1. queues, on the batch stream, the next rounds of every resident request as one batch
      (hgp_batch_*: one launch per phase over all requests' work items): as many rounds as the
-     request closest to completion still needs, so no request runs past its round count;
+     request closest to completion still needs, so no request runs past its round count.  Up to
+     `depth` ticks are queued on the device at once: the next tick's membership follows from
+     the round counts alone, so it is queued before the previous tick's results are read, and
+     the GPU does not wait for the host between ticks;
   2. while those rounds run on the GPU, admits queued requests: a request's state is created
      on the device (hgp_create, by a small pool of creator threads, each on its own upload
      stream, so creations overlap each other and the batch) if the memory budget minus what
      resident, staged and in-creation requests take covers its footprint estimate, so memory
      decides how many requests run at once; the new handles are staged and join the batch at
      the next tick (a round boundary);
-  3. waits for the rounds, then retires the requests that are done, on the creator threads
-     too: each partition is read back to the host and its device state released (queued behind
-     the batch's rounds on the request's own stream, without synchronising the device), and the
-     latency (arrival -> result on the host) is recorded.
+  3. once the oldest queued tick has finished, reads its statistics (waiting for that tick
+     only) and retires the requests it completed, on the creator threads too: each partition is
+     read back to the host and its device state released (queued behind the batch's rounds on
+     the request's own stream, without synchronising the device), and the latency (arrival ->
+     result on the host) is recorded.
 Device memory comes from the library's stream-ordered pool, so creating and releasing request
 state never synchronises the device.  Each request's arithmetic is the same as refining it
 alone: batching changes only which kernel launch does the work (see tests/test_serving_gpu.py).
@@ -123,12 +127,13 @@ class Server:
     max_staged: requests created (or being created) ahead of the batch they will join;
     creators: threads that create and retire request state (0: the serving thread itself);
     ctas_per_sm: persistent grid of the batch's gain and apply kernels (0: by occupancy; fewer
-    leave room on each SM for the creations' kernels)."""
+    leave room on each SM for the creations' kernels); depth: ticks queued on the device at once
+    (1: each tick's results are read before the next is queued)."""
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
                  memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
                  graph: bool = False, creators: int = 8, ctas_per_sm: int = 0, join_at: int = 0,
-                 clock=time.perf_counter):
+                 depth: int = 1, clock=time.perf_counter):
         import torch
         self._torch = torch
         self.stream = stream
@@ -142,6 +147,9 @@ class Server:
         self.graph = graph
         self.ctas_per_sm = int(ctas_per_sm)
         self.join_at = int(join_at)
+        if depth < 1:
+            raise ValueError("depth must be at least 1")
+        self.depth = int(depth)
         self.clock = clock
         self.queue: Deque[Request] = collections.deque()
         self.staged: Deque[Request] = collections.deque()
@@ -149,10 +157,10 @@ class Server:
         self._creating: Deque[tuple] = collections.deque()    # (request, future), FIFO
         self._retiring: Deque[tuple] = collections.deque()    # (request, future), FIFO
         self._handles: Dict[int, HGP] = {}
-        self._done_rounds: Dict[int, int] = {}
+        self._planned: Dict[int, int] = {}                      # rounds queued per request
         self._stats: Dict[int, list] = {}
-        self._batch: Optional[Batch] = None
-        self._batch_key: tuple = ()
+        # queued ticks, oldest first: (batch, members, rounds, members it completes)
+        self._inflight: Deque[tuple] = collections.deque()
         self._resident_bytes = 0
         self._lock = threading.Lock()
         self._tls = threading.local()
@@ -170,7 +178,7 @@ class Server:
     def idle(self) -> bool:
         with self._lock:
             return (not self.queue and not self.active and not self.staged and not self._creating
-                    and not self._retiring)
+                    and not self._retiring and not self._inflight)
 
     # -- admission by the memory budget
     def _free_bytes(self) -> int:
@@ -199,7 +207,7 @@ class Server:
     def _install(self, req: Request, h: HGP):
         req.admitted = self.clock()
         self._handles[req.rid] = h
-        self._done_rounds[req.rid] = 0
+        self._planned[req.rid] = 0
         self._stats[req.rid] = []
         self.staged.append(req)
 
@@ -211,13 +219,12 @@ class Server:
                 req = self.queue[0]
             need = req.footprint()
             if need > self._free_bytes():
-                if self.active or self.staged or self._creating:
-                    return                      # wait for a resident request to finish
-                if need > self.memory_budget:
-                    with self._lock:            # can never fit: refuse it
-                        self.queue.popleft()
-                    self.rejected.append(req)
-                    continue
+                if self._resident_bytes > 0:
+                    return                      # wait for resident requests to finish
+                with self._lock:                # larger than the whole budget: refuse it
+                    self.queue.popleft()
+                self.rejected.append(req)
+                continue
             with self._lock:
                 self.queue.popleft()
             self._resident_bytes += need
@@ -242,56 +249,66 @@ class Server:
         while self.staged and len(self.active) < self.max_active:
             self.active.append(self.staged.popleft())
 
-    def _ensure_batch(self):
-        key = tuple(r.rid for r in self.active)
-        if key != self._batch_key:
-            if self._batch is not None:
-                self._batch.close()
-            self._batch = Batch([self._handles[rid] for rid in key], graph=self.graph,
-                                stream=self.stream, gain_ctas_per_sm=self.ctas_per_sm,
-                                apply_ctas_per_sm=self.ctas_per_sm)
-            self._batch_key = key
+    def _can_launch(self) -> bool:
+        return bool(self.active or self.staged) and len(self._inflight) < self.depth
+
+    def _launch(self):
+        """Queues the next rounds of the active requests as one batch call (no host wait)."""
+        members = list(self.active)
+        batch = Batch([self._handles[r.rid] for r in members], graph=self.graph, stream=self.stream,
+                      gain_ctas_per_sm=self.ctas_per_sm, apply_ctas_per_sm=self.ctas_per_sm)
+        rounds = min(r.rounds - self._planned[r.rid] for r in members)
+        if rounds:
+            batch.refine(rounds, stats=False)
+        self.ticks += 1
+        finishing = []
+        for r in members:
+            self._planned[r.rid] += rounds
+            if self._planned[r.rid] >= r.rounds:
+                finishing.append(r)
+        done_ids = {r.rid for r in finishing}
+        self.active = [r for r in members if r.rid not in done_ids]
+        self._inflight.append((batch, members, rounds, finishing))
+
+    def _complete(self, tick):
+        """Statistics of a finished (or the oldest) tick; its completed requests retire."""
+        batch, members, rounds, finishing = tick
+        if rounds:
+            st = batch.stats(rounds)            # waits for this tick only
+            for i, req in enumerate(members):
+                self._stats[req.rid].extend(st[i])
+        batch.close()
+        for req in finishing:
+            h = self._handles.pop(req.rid)
+            req.stats = np.array(self._stats.pop(req.rid), dtype=np.int64)
+            self._planned.pop(req.rid)
+            if self._pool is not None:
+                self._retiring.append((req, self._pool.submit(self._retire, req, h)))
+            else:
+                self._retiring.append((req, None))
+                self._retire(req, h)
 
     # -- one tick
     def step(self) -> List[Request]:
-        """Queue the next rounds of the resident requests, admit arrivals while they run,
-        retire the requests that are done, and let the staged ones join."""
-        rounds = 0
-        if self.active:
-            self._ensure_batch()
-            rounds = min(r.rounds - self._done_rounds[r.rid] for r in self.active)
-            self._batch.refine(rounds, stats=False)
-            self.ticks += 1
+        """Let the staged requests join, queue the next rounds of the resident requests, admit
+        arrivals while they run, and retire the requests of the oldest queued tick once it is
+        done (or wait for it when no further tick can be queued)."""
+        self._collect(block=False)
+        self._promote()
+        if self.active and len(self._inflight) < self.depth:
+            self._launch()
         self._admit()
-        finished = []
-        if rounds:
-            st = self._batch.stats(rounds)
-            for i, req in enumerate(self.active):
-                self._stats[req.rid].extend(st[i])
-                self._done_rounds[req.rid] += rounds
-                if self._done_rounds[req.rid] >= req.rounds:
-                    finished.append(req)
-        if finished:
-            done_ids = {r.rid for r in finished}
-            for req in finished:
-                h = self._handles.pop(req.rid)
-                req.stats = np.array(self._stats.pop(req.rid), dtype=np.int64)
-                self._done_rounds.pop(req.rid)
-                if self._pool is not None:
-                    self._retiring.append((req, self._pool.submit(self._retire, req, h)))
-                else:
-                    self._retiring.append((req, None))
-                    self._retire(req, h)
-            self.active = [r for r in self.active if r.rid not in done_ids]
+        if self._inflight and (not self._can_launch() or self._inflight[0][0].done()):
+            self._complete(self._inflight.popleft())
         out = self._collect_retired(block=False)
         if out:
             self._admit()
-        self._collect(block=not self.active and not self.staged)
-        if not self.active and not self.staged and not self._creating and self._retiring:
-            out.extend(self._collect_retired(block=True))
-            self._admit()
-            self._collect(block=not self.staged)
-        self._promote()
+        if not self._inflight and not self.active and not self.staged:
+            if self._creating:
+                self._collect(block=True)
+            elif self._retiring:
+                out.extend(self._collect_retired(block=True))
+                self._admit()
         return out
 
     def _collect_retired(self, block: bool) -> List[Request]:
@@ -322,9 +339,10 @@ class Server:
         if self._pool is not None:
             self._pool.shutdown(wait=True)
         self._retiring.clear()
-        if self._batch is not None:
-            self._batch.close()
-            self._batch = None
+        while self._inflight:
+            batch = self._inflight.popleft()[0]
+            batch.synchronize()
+            batch.close()
         for h in self._handles.values():
             h.close()
         self._handles.clear()

@@ -42,6 +42,12 @@ class FakeBatch:
         assert rounds == self.last
         return np.zeros((len(self.handles), rounds, 7), np.int64)
 
+    def done(self):
+        return True
+
+    def synchronize(self):
+        pass
+
     def close(self):
         pass
 
@@ -71,12 +77,14 @@ def _req(serve, rid, p, rounds):
     return serve.Request.from_hypergraph(rid, hg, rounds=rounds)
 
 
+@pytest.mark.parametrize("depth", [1, 2])
 @pytest.mark.parametrize("creators", [0, 3])
-def test_admission_by_budget_and_retirement(server_cls, creators):
+def test_admission_by_budget_and_retirement(server_cls, creators, depth):
     serve = server_cls
     reqs = [_req(serve, i, 20_000, 1 + i % 3) for i in range(6)]
     one = reqs[0].footprint()
-    srv = serve.Server(memory_budget=int(2.5 * one), reserve_bytes=0, clock=Clock(), creators=creators)
+    srv = serve.Server(memory_budget=int(2.5 * one), reserve_bytes=0, clock=Clock(), creators=creators,
+                       depth=depth)
     for r in reqs:
         srv.submit(r)
     done = []
@@ -129,3 +137,58 @@ def test_footprint_counts_the_internal_net_order(server_cls):
     below = serve.estimate_device_bytes(m - 1, m - 1, 7 * (m - 1), 8, 200, False, False)
     below_u = serve.estimate_device_bytes(m - 1, m - 1, 7 * (m - 1), 8, 50, False, False)
     assert below == below_u
+
+
+class RecordingBatch(FakeBatch):
+    """Records the queue of ticks: which requests each tick holds, and how many ticks are
+    queued (refined but not yet read) when a new one is queued."""
+    queued = []
+    log = []
+
+    def refine(self, rounds, stats=True):
+        RecordingBatch.log.append((len(RecordingBatch.queued), [h.rid for h in self.handles], rounds))
+        RecordingBatch.queued.append(self)
+        return super().refine(rounds, stats)
+
+    def done(self):
+        return False
+
+    def stats(self, rounds):
+        RecordingBatch.queued.remove(self)
+        return super().stats(rounds)
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_pipelined_ticks(server_cls, monkeypatch, depth):
+    """Ticks are queued up to `depth` deep before the oldest one is read; every request still
+    runs exactly its rounds, one tick after another, and retires once."""
+    serve = server_cls
+    monkeypatch.setattr(serve, "Batch", RecordingBatch)
+    RecordingBatch.queued, RecordingBatch.log = [], []
+    orig = FakeHGP.__init__
+
+    def init(self, *a, **kw):
+        orig(self, *a, **kw)
+        self.rid = kw.get("seed")
+    monkeypatch.setattr(FakeHGP, "__init__", init)
+    want = {0: 2, 1: 3, 2: 5, 3: 5}            # ticks of 2, 1 and 2 rounds
+    reqs = [_req(serve, i, 20_000, want[i]) for i in range(4)]
+    for i, r in enumerate(reqs):
+        r.seed = i
+    srv = serve.Server(memory_budget=1 << 40, reserve_bytes=0, clock=Clock(), creators=0, depth=depth)
+    for r in reqs:
+        srv.submit(r)
+    done = srv.run_until_idle()
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3]
+    assert max(q for q, _, _ in RecordingBatch.log) == min(depth, 3) - 1   # never more than depth queued
+    rounds = {i: 0 for i in range(4)}
+    for _, rids, rr in RecordingBatch.log:
+        for rid in rids:
+            rounds[rid] += rr
+    assert rounds == want
+    assert [rr for _, _, rr in RecordingBatch.log] == [2, 1, 2]
+    for r in done:
+        assert r.stats.shape == (want[r.rid], 7)
+    assert FakeHGP.live == 0
+    srv.close()
+

@@ -37,12 +37,16 @@ def _alone(req):
     return out
 
 
-@pytest.mark.parametrize("budget", [None, 96 << 20])
-def test_mix_equals_alone(budget):
+@pytest.mark.parametrize("budget,depth,own_streams", [(None, 2, False), (96 << 20, 2, False),
+                                                      (None, 1, False), (96 << 20, 3, False),
+                                                      (None, 2, True)])
+def test_mix_equals_alone(budget, depth, own_streams):
+    """own_streams: no server stream, so every tick's batch runs on a stream of its own and the
+    requests that continue from one tick to the next are ordered across batches."""
     from paper_2010_10272_gb300.serve import Server
     reqs = _requests()
-    s = torch.cuda.Stream()
-    srv = Server(stream=s, memory_budget=budget, reserve_bytes=0)
+    s = None if own_streams else torch.cuda.Stream()
+    srv = Server(stream=s, memory_budget=budget, reserve_bytes=0, depth=depth)
     done = []
     pending = list(reqs)
     # arrivals in waves while earlier requests are still running
