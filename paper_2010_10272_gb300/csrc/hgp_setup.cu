@@ -319,11 +319,22 @@ __global__ void k_check_nets(const int32_t *nw, int32_t m, int32_t *err)
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
 }
 
+// Creation queues its kernels behind the input checks without waiting for their verdict (for
+// instances whose net sizes the host reads itself, see create_impl): every kernel that indexes
+// by a pin, a vertex id or a block then returns at once when the checks flagged the input, and
+// the creation reports HGP_ERR_INVALID at its one read-back.  guard: the creation's error flag,
+// or nullptr outside creation.
+__device__ __forceinline__ bool input_invalid(const int32_t *guard)
+{
+    return guard && (*reinterpret_cast<const volatile int32_t *>(guard) & ERR_INVALID) != 0;
+}
+
 // ------------------------------------------------------------------ per-vertex net weight
 // W(u) = sum of incident net weights must stay below 2^31 (int32 gain arithmetic)
 __global__ void k_vertex_netweight(const int32_t *vtx_off, const int32_t *inc, const int32_t *nw,
                                    int32_t n, int32_t *err, unsigned long long *max_w)
 {
+    if (input_invalid(err)) return;
     unsigned long long local = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -347,20 +358,24 @@ constexpr int32_t kTpDirectMaxN = 1 << 21;
 // near-uniform sizes the relabelling only adds creation time)
 constexpr int32_t kReorderMinNets = 1 << 20;
 constexpr int64_t kReorderSkew = 8;
+// host inputs with fewer nets than this: the host reads the net sizes (see create_impl)
+constexpr int32_t kHostSizesMaxNets = 1 << 20;
 // in internal order, nets of at least this many pins (a prefix) get their own CTAs at creation
 // and initialisation (a power of two: size classes are powers of two)
 constexpr int32_t kBigNet = 256;
 
-__global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg)
+__global__ void k_degrees(const int32_t *pins, int64_t P, int32_t *deg, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
          j += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&deg[pins[j]], 1);
 }
 
 __global__ void k_scatter(const int32_t *off, const int32_t *pins, int32_t m, int32_t narrow_max, int32_t *fill,
-                          int32_t *inc)
+                          int32_t *inc, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e < m; e += warps) {
@@ -388,8 +403,9 @@ constexpr int kTpNetsPerCta = 16384;     // at most; fewer when the instance has
 constexpr int kTpMinCtas = 608;          // target CTAs per launch (4 per SM)
 
 __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P, int bshift, int32_t nb,
-                                                 int32_t *bucket_cnt)
+                                                 int32_t *bucket_cnt, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t h[kTpMaxBuckets];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
     __syncthreads();
@@ -404,8 +420,10 @@ __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P,
 // reserved, pass 1 writes the pairs.  A warp walks the pins of 32 nets at once (coalesced).
 __global__ void __launch_bounds__(256) k_tp_scatter(const int32_t *off, const int32_t *pins, int32_t m,
                                                     int32_t e_begin, int bshift, int32_t nb, int32_t narrow_max,
-                                                    int32_t per_cta, int32_t *bucket_cur, unsigned long long *pairs)
+                                                    int32_t per_cta, int32_t *bucket_cur, unsigned long long *pairs,
+                                                    const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t cur[kTpMaxBuckets];
     __shared__ int32_t off33_w[8][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -458,8 +476,10 @@ constexpr int kTpBigWin = kTpBigChunk / kBigNet + 3;   // offsets of the nets a 
 
 __global__ void __launch_bounds__(256) k_tp_scatter_big(const int32_t *off, const int32_t *pins, int32_t m_big,
                                                         int bshift, int32_t nb, int32_t narrow_max,
-                                                        int32_t *bucket_cur, unsigned long long *pairs)
+                                                        int32_t *bucket_cur, unsigned long long *pairs,
+                                                        const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t cur[kTpMaxBuckets];
     __shared__ int32_t win[kTpBigWin];
     __shared__ int32_t first;
@@ -513,8 +533,9 @@ constexpr int kTpPlaceBatch = 8;
 template <bool SMEM>
 __global__ void __launch_bounds__(1024) k_tp_place(const unsigned long long *pairs, const int32_t *bucket_off,
                                                    int bshift, int32_t n, int32_t nb, int32_t *cursor,
-                                                   int32_t *vtx_off, int32_t *inc)
+                                                   int32_t *vtx_off, int32_t *inc, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t wt[32];
     __shared__ int32_t tot;
     extern __shared__ int32_t sc[];
@@ -584,8 +605,9 @@ __global__ void k_copy_part(const int32_t *in, uint8_t *part, int32_t n)
         part[v] = (uint8_t)in[v];
 }
 
-__global__ void k_block_weights(Dev d)
+__global__ void k_block_weights(Dev d, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ unsigned long long w[64];
     if (threadIdx.x < 64) w[threadIdx.x] = 0;
     __syncthreads();
@@ -639,8 +661,9 @@ __device__ __forceinline__ void stage_set(uint8_t *blk, int row, int i, int w, i
 }
 
 template <typename Rec>
-__global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d, int32_t e_begin)
+__global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d, int32_t e_begin, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t cnt[kInitWarps][64];
     __shared__ long long part_obj[kInitWarps];
     extern __shared__ __align__(16) uint32_t stage_dyn[];   // kInitWarps blocks of 32 rows
@@ -771,8 +794,9 @@ __global__ void __launch_bounds__(kInitWarps * 32) k_init_nets(Dev d, int32_t e_
 // the first few warps.  Same results as k_init_nets for these nets (the narrow row of a net in
 // the wide table is written as zeros).
 template <typename Rec>
-__global__ void __launch_bounds__(256) k_init_big(Dev d, int32_t m_big)
+__global__ void __launch_bounds__(256) k_init_big(Dev d, int32_t m_big, const int32_t *guard)
 {
+    if (input_invalid(guard)) return;
     __shared__ int32_t cnt[64];
     const int lane = threadIdx.x & 31;
     const int32_t narrow_max = d.phi_w == 1 ? 255 : (d.phi_w == 2 ? 65535 : 0x7fffffff);
@@ -984,7 +1008,8 @@ cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
         }                                          \
     } while (0)
 
-int init_state(hgp_handle *h)
+// guard: the creation's error flag while creating (kernels skip flagged input), else nullptr
+int init_state(hgp_handle *h, const int32_t *guard)
 {
     Dev &d = h->d;
     cudaStream_t st = h->stream;
@@ -995,13 +1020,13 @@ int init_state(hgp_handle *h)
     // the net kernel writes every narrow Phi row (zeros included); the wide table's rows are
     // written by their nets, but a row of a net with zero pins in range stays as zeroed here
     if (d.phi_wide && h->n_wide > 0) CK(cudaMemsetAsync(d.phi_wide, 0, sizeof(int32_t) * (size_t)h->n_wide * d.k, st));
-    k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d); h->launches++;
+    k_block_weights<<<grid_for(d.n, 256), 256, 0, st>>>(d, guard); h->launches++;
     CK(cudaGetLastError());
     const int32_t e_begin = h->m_big32;
     if (e_begin > 0) {
         const int gb = e_begin < 152 * 16 ? e_begin : 152 * 16;
-        if (d.k <= 32) k_init_big<Rec16><<<gb, 256, 0, st>>>(d, e_begin);
-        else k_init_big<Rec32><<<gb, 256, 0, st>>>(d, e_begin);
+        if (d.k <= 32) k_init_big<Rec16><<<gb, 256, 0, st>>>(d, e_begin, guard);
+        else k_init_big<Rec32><<<gb, 256, 0, st>>>(d, e_begin, guard);
         h->launches++;
     }
     if (d.m > e_begin) {
@@ -1013,11 +1038,11 @@ int init_state(hgp_handle *h)
         if (d.k <= 32) {
             cudaFuncSetAttribute(k_init_nets<Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  init_smem(32, 4));
-            k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
+            k_init_nets<Rec16><<<g, kInitWarps * 32, smem, st>>>(d, e_begin, guard); h->launches++;
         } else {
             cudaFuncSetAttribute(k_init_nets<Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  init_smem(64, 4));
-            k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d, e_begin); h->launches++;
+            k_init_nets<Rec32><<<g, kInitWarps * 32, smem, st>>>(d, e_begin, guard); h->launches++;
         }
     }
     CK(cudaGetLastError());
@@ -1144,10 +1169,27 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         k_check_pins<<<grid_for(m, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
         CKF(cudaGetLastError());
     }
-    CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CKF(cudaStreamSynchronize(st));
-    if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
-    const int32_t max_size = host_err[1];
+    // Small host inputs: the host checks the offsets and finds the largest net itself (cheaper
+    // than a round trip to the device, which waits behind other work on a busy GPU), so the
+    // creation is queued to its end without waiting for the device checks: the kernels after
+    // them skip flagged input (guard) and the verdict comes with the final read-back.
+    const bool host_sizes = !on_device && m < kHostSizesMaxNets;
+    int32_t max_size = 0;
+    const int32_t *guard = nullptr;
+    if (host_sizes) {
+        if (net_offsets[0] != 0) return fail(HGP_ERR_INVALID);
+        for (int32_t e = 0; e < m; ++e) {
+            const int64_t sz = net_offsets[e + 1] - net_offsets[e];
+            if (sz < 0) return fail(HGP_ERR_INVALID);
+            if (sz > max_size) max_size = (int32_t)sz;
+        }
+        guard = d.err;
+    } else {
+        CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CKF(cudaStreamSynchronize(st));
+        if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
+        max_size = host_err[1];
+    }
 
     // ---- scan scratch (shared by the scans below)
     const int64_t nr_ctas = m > 0 ? (m + 2047) / 2048 < 1216 ? (m + 2047) / 2048 : 1216 : 0;
@@ -1239,10 +1281,11 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(dalloc(h, &inc, P));
     CKF(cudaMemsetAsync(tmp, 0, sizeof(int32_t) * ((size_t)n + 1), st));
     if (P > 0 && n <= kTpDirectMaxN && !(o.debug & 2)) {
-        k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp); h->launches++;
+        k_degrees<<<grid_for(P, 256), 256, 0, st>>>(pins_d, P, tmp, guard); h->launches++;
         CKF(scan(tmp, vtx_off, n));
         CKF(cudaMemcpyAsync(tmp, vtx_off, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, narrow_max, tmp, inc); h->launches++;
+        k_scatter<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, m, narrow_max, tmp, inc, guard);
+        h->launches++;
         CKF(cudaGetLastError());
     } else if (P > 0) {
         auto buckets = [&](int sh) { return (((int64_t)n + ((int64_t)1 << sh) - 1) >> sh); };
@@ -1260,25 +1303,25 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         CKF(cudaMallocAsync(reinterpret_cast<void **>(&pairs), sizeof(unsigned long long) * (size_t)P, st));
         int32_t *bk_cnt = bk, *bk_off = bk + nbk + 1, *bk_cur = bk + 2 * nbk + 2;
         CKF(cudaMemsetAsync(bk_cnt, 0, sizeof(int32_t) * ((size_t)nbk + 1), st));
-        k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt); h->launches++;
+        k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt, guard); h->launches++;
         CKF(scan(bk_cnt, bk_off, nbk));
         CKF(cudaMemcpyAsync(bk_cur, bk_off, sizeof(int32_t) * (size_t)nbk, cudaMemcpyDeviceToDevice, st));
         const int64_t sc = (m_rest + per_cta - 1) / per_cta;
         if (e_begin > 0 && p_big > 0) {
             k_tp_scatter_big<<<(unsigned)((p_big + kTpBigChunk - 1) / kTpBigChunk), 256, 0, st>>>(
-                net_off, pins_d, e_begin, bshift, nbk, narrow_max, bk_cur, pairs); h->launches++;
+                net_off, pins_d, e_begin, bshift, nbk, narrow_max, bk_cur, pairs, guard); h->launches++;
         }
         if (sc > 0) {
             k_tp_scatter<<<(unsigned)sc, 256, 0, st>>>(net_off, pins_d, m, e_begin, bshift, nbk, narrow_max,
-                                                       (int32_t)per_cta, bk_cur, pairs); h->launches++;
+                                                       (int32_t)per_cta, bk_cur, pairs, guard); h->launches++;
         }
         if (bshift <= kTpSmemShift) {
             const int smem = (int)(sizeof(int32_t) << bshift);
             cudaFuncSetAttribute(k_tp_place<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(int32_t) << kTpSmemShift));   // largest need, as above
-            k_tp_place<true><<<nbk, 1024, smem, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
+            k_tp_place<true><<<nbk, 1024, smem, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc, guard);
         } else {
-            k_tp_place<false><<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc);
+            k_tp_place<false><<<nbk, 1024, 0, st>>>(pairs, bk_off, bshift, n, nbk, tmp, vtx_off, inc, guard);
         }
         h->launches++;
         CKF(cudaGetLastError());
@@ -1365,7 +1408,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.seed = o.seed;
     d.variant = (o.balance_moves ? 1 : 0) | (o.revert_negative ? 2 : 0);
 
-    rc = init_state(h);
+    rc = init_state(h, guard);
     if (rc != HGP_OK) return fail(rc);
 
     // ---- L_max = floor((1 + eps) * ceil(c(V) / k))  (Sec. 2); the incident-weight check
@@ -1375,6 +1418,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CKF(cudaMemcpyAsync(&maxw, maxw_d, sizeof(maxw), cudaMemcpyDeviceToHost, st));
     CKF(cudaStreamSynchronize(st));
+    if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
     h->max_vertex_netweight = (int64_t)maxw;
     int64_t total = 0;
@@ -1505,7 +1549,7 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
         return status_of(e);
     }
     if (rc != HGP_OK) return rc;
-    return init_state(h);
+    return init_state(h, nullptr);
 }
 
 int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t *next_round,

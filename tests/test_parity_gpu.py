@@ -308,6 +308,56 @@ def test_error_codes():
                    net_off=np.array([0, 2, 4], np.int64))) == 3
 
 
+@pytest.mark.parametrize("debug,device", [(0, True), (2, False), (4, False), (2 | 4, True)],
+                         ids=["device", "bucketed", "reordered", "bucketed-reordered-device"])
+def test_invalid_inputs_every_creation_path(debug, device):
+    """Host inputs of small instances are checked while the creation is already queued (the
+    kernels after the checks skip flagged input; the verdict comes with the final read-back);
+    device inputs wait for the checks first.  Both reject the same inputs, whatever the
+    transpose and net order, including pins far outside [0, n) that the bucketed transpose would
+    otherwise use as bucket indices."""
+    import torch
+    from paper_2010_10272_gb300 import HGP
+    rng = np.random.default_rng(8)
+    n, m = 5000, 4000
+    sizes = rng.integers(1, 7, size=m)
+    off = np.zeros(m + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    pins = np.concatenate([np.sort(rng.choice(n, size=int(s), replace=False)) for s in sizes]).astype(np.int32)
+    part = rng.integers(0, 4, size=n).astype(np.int32)
+    vw = rng.integers(1, 4, size=n).astype(np.int32)
+    nw = rng.integers(1, 4, size=m).astype(np.int32)
+
+    def make(pins_=pins, part_=part, vw_=vw, nw_=nw):
+        if device:
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            return HGP(n, m, t(off), t(pins_), 4, 0.05, t(part_), t(vw_), t(nw_), debug=debug, device=True)
+        return HGP(n, m, off, pins_, 4, 0.05, part_, vw_, nw_, debug=debug)
+
+    h = make()
+    o = oracle.Oracle(n, m, off, pins, 4, 0.05, part, vw, nw, 4, 0)
+    compare_state(h, o)
+    h.close()
+    far = pins.copy()
+    far[len(far) // 2] = (1 << 30) + 7
+    neg = pins.copy()
+    neg[3] = -(1 << 29)
+    bad_part = part.copy()
+    bad_part[17] = 200
+    bad_vw = vw.copy()
+    bad_vw[5] = 0
+    bad_nw = nw.copy()
+    bad_nw[9] = -1
+    assert _err(lambda: make(pins_=far)) == 1
+    assert _err(lambda: make(pins_=neg)) == 1
+    assert _err(lambda: make(part_=bad_part)) == 1
+    assert _err(lambda: make(vw_=bad_vw)) == 1
+    assert _err(lambda: make(nw_=bad_nw)) == 1
+    h = make()                                     # the device is fine afterwards
+    compare_state(h, o)
+    h.close()
+
+
 def test_moved_pins_and_profile():
     """moved_pins = sum of degrees of the vertices the oracle moved; profiling accounts for
     every kernel the rounds launch."""
