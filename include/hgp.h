@@ -413,6 +413,13 @@ void hgp_destroy(hgp_handle *h);
  */
 int hgp_set_pool_retention(int64_t bytes);
 
+/* Host waits inside the library (read-backs, the end of hgp_create, statistics): on = 0
+ * (default) spins in cudaStreamSynchronize; on = 1 sleeps on a blocking-sync event recorded on
+ * the stream, which frees the CPU core while the device works (for callers where many threads
+ * wait at once, such as a serving loop's creator threads) at the cost of a wake-up latency.
+ * Process-wide; results do not depend on it. */
+int hgp_set_blocking_waits(int32_t on);
+
 #ifdef __cplusplus
 }
 #endif

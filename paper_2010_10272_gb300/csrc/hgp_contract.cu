@@ -757,7 +757,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     int32_t herr = 0;
     const int64_t mm = m > 0 ? m : 1;
     CT(cudaMemcpyAsync(&P, net_off + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CT(cudaStreamSynchronize(st));
+    CT(stream_wait(st));
     if (P < 0 || (m == 0 && P != 0)) { rc = HGP_ERR_INVALID; goto done; }
     if (P >= ((int64_t)1 << 31)) { rc = HGP_ERR_UNSUPPORTED; goto done; }
     CT(cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int32_t) * 2, st));
@@ -766,7 +766,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     k_ct_check<<<grid_of(P > n ? P : n, 256), 256, 0, st>>>(net_off, pins, vertex_w, net_w, n, m, P, err);
     CT(cudaGetLastError());
     CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CT(cudaStreamSynchronize(st));
+    CT(stream_wait(st));
     if (herr) { rc = HGP_ERR_INVALID; goto done; }
     // (1) remap the used cluster ids
     CT(cudaMallocAsync(reinterpret_cast<void **>(&used), sizeof(int32_t) * (size_t)n, st));
@@ -777,7 +777,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(scan_excl<int32_t>(used, n, cid, st));
     CT(cudaMemcpyAsync(&n2, cid + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CT(cudaStreamSynchronize(st));
+    CT(stream_wait(st));
     if (herr) { rc = HGP_ERR_INVALID; goto done; }
     c->n = (int32_t)n2;
     // (2) map and cluster weights
@@ -807,7 +807,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
         // nets of more than kMedium pins: chunk sorts, merge passes, de-duplication
         int32_t hcnt[kClasses] = {0, 0, 0, 0};
         CT(cudaMemcpyAsync(hcnt, counts, sizeof(int32_t) * kClasses, cudaMemcpyDeviceToHost, st));
-        CT(cudaStreamSynchronize(st));
+        CT(stream_wait(st));
         n_large = hcnt[3];
         if (n_large > 0) {
             int32_t *chunks = nullptr;
@@ -824,7 +824,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
             int32_t max_size = 0;
             CT(cudaMemcpyAsync(&tasks, cpre + n_large, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             CT(cudaMemcpyAsync(&max_size, counts + kClasses, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            CT(cudaStreamSynchronize(st));
+            CT(stream_wait(st));
             const int g = (int)(tasks < (int64_t)sms * 2 ? tasks : (int64_t)sms * 2);
             k_lg_chunk<<<g, kLgThreads, 0, st>>>(net_off, pins, c->map, lists + 3 * mm, counts + 3, cpre, tasks, a);
             int32_t *src = a, *dst = b;
@@ -851,7 +851,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
             k_ct_resolve<<<grid_of(m, 256), 256, 0, st>>>(net_off, a, size1, key, rep, m, tab, size - 1, left);
             CT(cudaGetLastError());
             CT(cudaMemcpyAsync(&hleft, left, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            CT(cudaStreamSynchronize(st));
+            CT(stream_wait(st));
             if (hleft == 0) break;
         }
     }
@@ -870,7 +870,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(scan_excl<int32_t>(rep_size, m, poff, st));
     CT(cudaMemcpyAsync(&m2, nid + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CT(cudaMemcpyAsync(&P2, poff + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CT(cudaStreamSynchronize(st));
+    CT(stream_wait(st));
     c->m = (int32_t)m2;
     c->P = P2;
     CT(cudaMalloc(reinterpret_cast<void **>(&c->net_off), sizeof(int64_t) * ((size_t)m2 + 1)));
@@ -887,7 +887,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
         CT(cudaGetLastError());
     }
     CT(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CT(cudaStreamSynchronize(st));
+    CT(stream_wait(st));
     if (herr & ERR_UNSUPPORTED) rc = HGP_ERR_UNSUPPORTED;
     else if (herr) rc = HGP_ERR_INTERNAL;
 done:
@@ -910,7 +910,7 @@ done:
     if (poff) cudaFreeAsync(poff, st);
     if (nw64) cudaFreeAsync(nw64, st);
     {
-        const cudaError_t e2 = cudaStreamSynchronize(st);
+        const cudaError_t e2 = stream_wait(st);
         if (e == cudaSuccess) e = e2;
     }
     if (e != cudaSuccess) {
@@ -960,7 +960,7 @@ extern "C" int hgp_coarse_copy_to_host(const hgp_coarse *c, int64_t *net_off, in
         e = cudaMemcpyAsync(net_w, c->nw, sizeof(int32_t) * (size_t)c->m, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && map)
         e = cudaMemcpyAsync(map, c->map, sizeof(int32_t) * (size_t)c->fine_n, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = stream_wait(c->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -973,7 +973,7 @@ extern "C" int hgp_coarse_project(const hgp_coarse *c, const int32_t *coarse_par
     if (!c || !coarse_part || !fine_part) return HGP_ERR_INVALID;
     k_ct_project<<<grid_of(c->fine_n, 256), 256, 0, c->stream>>>(c->map, c->fine_n, coarse_part, fine_part);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = stream_wait(c->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -983,6 +983,6 @@ extern "C" int hgp_coarse_project(const hgp_coarse *c, const int32_t *coarse_par
 
 extern "C" void hgp_coarse_destroy(hgp_coarse *c)
 {
-    if (c) cudaStreamSynchronize(c->stream);
+    if (c) stream_wait(c->stream);
     coarse_free(c);
 }

@@ -177,7 +177,7 @@ extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *move
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hdeg, degsum, sizeof(hdeg), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = stream_wait(st);
     if (e == cudaSuccess && herr) rc = HGP_ERR_INVALID;
     // at most 2 keys per incident net of a moved vertex; keep the table at most half full
     uint64_t size = 64;
@@ -199,7 +199,7 @@ extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *move
     if (degsum) cudaFreeAsync(degsum, st);
     if (table) cudaFreeAsync(table, st);
     if (g_d) cudaFreeAsync(g_d, st);
-    const cudaError_t e2 = cudaStreamSynchronize(st);
+    const cudaError_t e2 = stream_wait(st);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

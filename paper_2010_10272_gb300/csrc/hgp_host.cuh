@@ -27,6 +27,10 @@ struct hgp_handle {
     static constexpr int kMaxAllocs = 64;
     void *allocs[kMaxAllocs] = {};
     int n_allocs = 0;
+    // one allocation (also in allocs) that small handles' buffers are carved from, so that a
+    // creation makes one pool call instead of ~25 (pool calls from many threads contend)
+    char *arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
     // CUDA-graph cache: one refine() of `graph_rounds` rounds
     cudaGraphExec_t graph_exec = nullptr;
     int32_t graph_rounds = 0;
@@ -70,8 +74,27 @@ inline int status_of(cudaError_t e)
 // with kernels of other handles (the serving loop relies on this).  Freed memory goes back to
 // the system at the next synchronisation unless hgp_set_pool_retention keeps some of it.
 cudaError_t library_pool(cudaMemPool_t *out);
+// Waits on the host for the work queued on st: spinning in cudaStreamSynchronize, or, after
+// hgp_set_blocking_waits(1), sleeping on a blocking-sync event recorded on st.
+cudaError_t stream_wait(cudaStream_t st);
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
 void dev_free(void *p, cudaStream_t st);
+
+// Carves `bytes` (rounded up to 256) from the handle's arena; nullptr when it has no room left.
+inline void *arena_take(hgp_handle *h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (!h->arena || h->arena_used + bytes > h->arena_size) return nullptr;
+    void *p = h->arena + h->arena_used;
+    h->arena_used += bytes;
+    return p;
+}
+
+inline bool in_arena(const hgp_handle *h, const void *p)
+{
+    const char *c = static_cast<const char *>(p);
+    return h->arena && c >= h->arena && c < h->arena + h->arena_size;
+}
 
 // Orders the handle's stream after the last batch call that refined the handle from another
 // stream.  Every entry point that queues work on, or reads from, the handle calls it first, so

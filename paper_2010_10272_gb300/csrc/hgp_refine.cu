@@ -1739,7 +1739,7 @@ cudaError_t phase_end(hgp_handle *h, int phase, int32_t launches)
 cudaError_t collect_profile(hgp_handle *h)
 {
     if (!h->profiling || h->events_used == 0) return cudaSuccess;
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    cudaError_t e = stream_wait(h->stream);
     for (int32_t i = 0; i + 1 < h->events_used && e == cudaSuccess; i += 2) {
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]);
@@ -1844,13 +1844,16 @@ cudaError_t launch_round(const Plan &p, int32_t rr)
 cudaError_t sync_dev(hgp_handle *h)
 {
     if (!h->d_dev) {
-        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&h->d_dev), sizeof(Dev), h->stream);
-        if (e != cudaSuccess) return e;
+        h->d_dev = static_cast<Dev *>(arena_take(h, sizeof(Dev)));
+        if (!h->d_dev) {
+            cudaError_t e = dev_alloc(reinterpret_cast<void **>(&h->d_dev), sizeof(Dev), h->stream);
+            if (e != cudaSuccess) return e;
+        }
         h->dev_dirty = true;
     }
     if (!h->dev_dirty) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(h->d_dev, &h->d, sizeof(Dev), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = stream_wait(h->stream);
     if (e == cudaSuccess) h->dev_dirty = false;
     return e;
 }
@@ -1914,18 +1917,20 @@ int ensure_stats(hgp_handle *h, int32_t rounds)
     int64_t *dev = nullptr, *host = nullptr;
     // stats rows, then the work counters of the persistent kernels: 64 sub-rounds x (gain, apply)
     // per row
-    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&dev), sizeof(int64_t) * ST_N * (size_t)cap +
-                                                                   sizeof(int32_t) * kWqPerRow * (size_t)cap, h->stream);
+    const size_t bytes = sizeof(int64_t) * ST_N * (size_t)cap + sizeof(int32_t) * kWqPerRow * (size_t)cap;
+    cudaError_t e = cudaSuccess;
+    dev = static_cast<int64_t *>(arena_take(h, bytes));
+    if (!dev) e = dev_alloc(reinterpret_cast<void **>(&dev), bytes, h->stream);
     if (e == cudaSuccess) {
         host = static_cast<int64_t *>(malloc(sizeof(int64_t) * ST_N * (size_t)cap));
         if (!host) e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        dev_free(dev, h->stream);
+        if (!in_arena(h, dev)) dev_free(dev, h->stream);
         return status_of(e);
     }
-    if (h->d.stats) dev_free(h->d.stats, h->stream);
+    if (h->d.stats && !in_arena(h, h->d.stats)) dev_free(h->d.stats, h->stream);
     free(h->h_stats);
     h->d.stats = dev;
     h->d.wq = reinterpret_cast<int32_t *>(dev + (size_t)ST_N * cap);
@@ -1944,7 +1949,7 @@ static int copy_stats_out(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
 {
     cudaError_t e = cudaMemcpyAsync(h->h_stats, h->d.stats, sizeof(int64_t) * ST_N * (size_t)rounds,
                                     cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = stream_wait(h->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2018,10 +2023,10 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
         // had been dropped; written from the host after the rounds, so no kernel is involved
         int64_t obj = 0;
         e = cudaMemcpyAsync(&obj, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = stream_wait(h->stream);
         obj -= 1;
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.obj, &obj, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = stream_wait(h->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
@@ -2039,7 +2044,7 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
         if (e == cudaSuccess) e = cudaMemcpyAsync(&from_phi, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&maintained, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
         if (tmp) cudaFreeAsync(tmp, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = stream_wait(h->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             return status_of(e);
@@ -2082,7 +2087,7 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     if (e == cudaSuccess) e = cudaMemcpyAsync(gain, g_d, sizeof(int64_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
     if (t_d) cudaFreeAsync(t_d, st);
     if (g_d) cudaFreeAsync(g_d, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = stream_wait(st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2097,7 +2102,7 @@ extern "C" int hgp_set_launch_shape(hgp_handle *h, int32_t gain_ctas_per_sm, int
 {
     if (!h || gain_ctas_per_sm < 0 || apply_ctas_per_sm < 0) return HGP_ERR_INVALID;
     settle(h);
-    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    const cudaError_t e = stream_wait(h->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2188,7 +2193,7 @@ extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats 
     while (pass < max_passes && e == cudaSuccess) {
         int64_t bw[64];
         e = cudaMemcpyAsync(bw, h->d.bw, sizeof(int64_t) * (size_t)h->d.k, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = stream_wait(st);
         if (e != cudaSuccess) break;
         int64_t heaviest = 0;
         for (int i = 0; i < h->d.k; ++i) heaviest = bw[i] > heaviest ? bw[i] : heaviest;
@@ -2204,7 +2209,7 @@ extern "C" int hgp_rebalance(hgp_handle *h, int32_t max_passes, hgp_round_stats 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&appr, h->d.stats + (int64_t)pass * ST_N + ST_APPR, sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = stream_wait(st);
         if (e != cudaSuccess) break;
         ph.push_back(phase);
         ++pass;
@@ -2397,7 +2402,7 @@ static int batch_stats_out(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
     const int32_t count = (int32_t)b->hs.size();
     cudaError_t e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
                                     cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = stream_wait(b->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2586,7 +2591,7 @@ int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
         e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(int64_t) * ST_N * (size_t)b->stats_cap * count,
                             cudaMemcpyDeviceToHost, b->aux);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->aux);
+    if (e == cudaSuccess) e = stream_wait(b->aux);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -2614,7 +2619,7 @@ int hgp_batch_query(hgp_batch *b, int32_t *done)
 int hgp_batch_synchronize(hgp_batch *b)
 {
     if (!b) return HGP_ERR_INVALID;
-    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    const cudaError_t e = stream_wait(b->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);

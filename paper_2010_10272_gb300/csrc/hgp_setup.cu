@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -935,6 +936,8 @@ static constexpr int kMaxPoolDevices = 64;
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pool[kMaxPoolDevices];
 
+static std::atomic<cudaMemPool_t> g_pool_ready[kMaxPoolDevices];   // set once created
+
 // the library's pool on the current device, created on first use
 cudaError_t library_pool(cudaMemPool_t *out)
 {
@@ -942,6 +945,10 @@ cudaError_t library_pool(cudaMemPool_t *out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    if (cudaMemPool_t ready = g_pool_ready[dev].load(std::memory_order_acquire)) {
+        *out = ready;
+        return cudaSuccess;
+    }
     std::lock_guard<std::mutex> lk(g_pool_mu);
     if (!g_pool[dev]) {
         cudaMemPoolProps props;
@@ -955,9 +962,44 @@ cudaError_t library_pool(cudaMemPool_t *out)
             g_pool[dev] = nullptr;
             return e;
         }
+        g_pool_ready[dev].store(g_pool[dev], std::memory_order_release);
     }
     *out = g_pool[dev];
     return cudaSuccess;
+}
+
+static std::atomic<int> g_blocking_waits{0};
+
+// a blocking-sync event per thread and device, destroyed when the thread ends
+struct WaitEvents {
+    cudaEvent_t ev[kMaxPoolDevices] = {};
+    ~WaitEvents()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        (void)cudaGetLastError();
+    }
+};
+static thread_local WaitEvents t_wait;
+
+cudaError_t stream_wait(cudaStream_t st)
+{
+    if (!g_blocking_waits.load(std::memory_order_relaxed)) return cudaStreamSynchronize(st);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    cudaEvent_t &ev = t_wait.ev[dev];
+    if (!ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ev = nullptr;
+            return e;
+        }
+    }
+    e = cudaEventRecord(ev, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev);
+    return e;
 }
 
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st)
@@ -987,6 +1029,10 @@ cudaError_t dalloc(hgp_handle *h, T **p, int64_t count)
 {
     *p = nullptr;
     if (count < 1) count = 1;
+    if (void *a = arena_take(h, (size_t)count * sizeof(T))) {
+        *p = reinterpret_cast<T *>(a);
+        return cudaSuccess;
+    }
     if (h->n_allocs >= hgp_handle::kMaxAllocs) return cudaErrorMemoryAllocation;
     void *q = nullptr;
     cudaError_t e = dev_alloc(&q, (size_t)count * sizeof(T), h->stream);
@@ -1051,6 +1097,40 @@ int init_state(hgp_handle *h, const int32_t *guard)
     return HGP_OK;
 }
 
+// Device bytes of every buffer create_impl (and the first refine) allocates for a handle made
+// from host inputs of fewer than kHostSizesMaxNets nets, each rounded up to 256 bytes: the arena
+// those buffers are carved from.  It covers the direct transpose in input net order without
+// wide nets; buffers of any other path (or beyond a miscount) come from the pool instead.
+size_t small_handle_bytes(int32_t n, int32_t m, int64_t P, int32_t k, const hgp_options &o, int32_t max_size,
+                          bool has_vw, bool has_nw)
+{
+    auto A = [](int64_t bytes) -> size_t { return (size_t)((bytes < 1 ? 1 : bytes) + 255) / 256 * 256; };
+    const int64_t n_ranges = (n + kRange - 1) / kRange, n_tiles = (n_ranges + kWarps - 1) / kWarps;
+    const int64_t S = o.subrounds, nm = n > m ? n : m;
+    const int w = o.phi_width ? o.phi_width : (max_size <= 255 ? 1 : 2);
+    const int64_t nr_ctas = m > 0 ? std::min<int64_t>((m + 2047) / 2048, 1216) : 0;
+    const int64_t scan_count = std::max<int64_t>(nm + 1, kNrRanks * nr_ctas + 1);
+    const int64_t nb = (scan_count + kScanChunk - 1) / kScanChunk;
+    size_t b = 0;
+    b += A(8 * (m + 1)) + A(4 * (m + 1)) + A(4 * P) + A(4 * (int64_t)n) + A(4 * 8);   // inputs, flags
+    if (has_vw) b += A(4 * (int64_t)n);
+    if (has_nw) b += A(4 * (int64_t)m);
+    b += A(4 * (nb + 1)) + A(4 * (nm + 1));                                          // scan scratch
+    b += A(4 * ((int64_t)n + 1)) + A(4 * P);                                         // vtx_off, inc
+    b += A(n) + A(4 * (((int64_t)m * k * w + 3) / 4)) + A((int64_t)m * (k <= 32 ? 16 : 32)) + A(8 * (2 * 64 + 8));
+    b += A(n_ranges * kRange) + A(2 * n_ranges * (S + 1)) + A(8 * n_ranges * kRange) + A(4 * n_ranges);
+    b += A(8 * 64) + A(8 * (int64_t)k * kBins) + A((int64_t)sizeof(Sel) * 64) + A(8 * (int64_t)k * n_tiles);
+    if (o.revert_negative) {
+        int64_t cap = 1024;
+        while (cap < 2 * P) cap <<= 1;
+        b += A(n_ranges * kRange) + A(16) + A(4 * (int64_t)m) + A(cap * kRvSlotBytes);
+    }
+    b += A(16);                                                                     // round state
+    b += A(8 * ST_N * 16 + 4 * kWqPerRow * 16);                                      // statistics
+    b += A(sizeof(Dev));                                                            // device Dev
+    return b;
+}
+
 int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t *pins,
                 const int32_t *vertex_w, const int32_t *net_w, int32_t k, double eps,
                 const int32_t *initial_part, const hgp_options *opt, hgp_handle **out, bool on_device)
@@ -1090,6 +1170,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     Dev &d = h->d;
     cudaGetDevice(&h->device);
     auto release = [&](void *ptr) {   // frees one of the handle's allocations before the end
+        if (in_arena(h, ptr)) return;
         for (int i = 0; i < h->n_allocs; ++i)
             if (h->allocs[i] == ptr) {
                 dev_free(h->allocs[i], h->stream);
@@ -1130,6 +1211,33 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         }                                          \
     } while (0)
 
+    // ---- small host inputs: the host checks the offsets and finds the largest net itself
+    // (cheaper than a round trip to the device, which waits behind other work on a busy GPU), so
+    // the creation is queued to its end without waiting for the device checks: the kernels after
+    // them skip flagged input (guard) and the verdict comes with the final read-back.  Their
+    // buffers are carved from one allocation (the arena), sized here.
+    const bool host_sizes = !on_device && m < kHostSizesMaxNets;
+    int32_t max_size = 0;
+    if (host_sizes) {
+        if (net_offsets[0] != 0) return fail(HGP_ERR_INVALID);
+        // branch-free smallest and largest size (vectorisable); offsets checked afterwards
+        int64_t lo = 0, hi = 0;
+        for (int32_t e = 0; e < m; ++e) {
+            const int64_t sz = net_offsets[e + 1] - net_offsets[e];
+            lo = sz < lo ? sz : lo;
+            hi = sz > hi ? sz : hi;
+        }
+        if (lo < 0) return fail(HGP_ERR_INVALID);   // then every size is at most P < 2^31
+        max_size = (int32_t)hi;
+        const size_t bytes = small_handle_bytes(n, m, P, k, o, max_size, vertex_w != nullptr, net_w != nullptr);
+        void *a = nullptr;
+        if (dev_alloc(&a, bytes, st) == cudaSuccess) {   // else every buffer comes from the pool
+            h->allocs[h->n_allocs++] = a;
+            h->arena = static_cast<char *>(a);
+            h->arena_size = bytes;
+        }
+    }
+
     // ---- inputs
     int64_t *off64 = nullptr;
     int32_t *part_in = nullptr, *tmp = nullptr, *misc32 = nullptr;
@@ -1169,24 +1277,12 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         k_check_pins<<<grid_for(m, 256), 256, 0, st>>>(net_off, pins_d, m, n, d.err, max_size_d); h->launches++;
         CKF(cudaGetLastError());
     }
-    // Small host inputs: the host checks the offsets and finds the largest net itself (cheaper
-    // than a round trip to the device, which waits behind other work on a busy GPU), so the
-    // creation is queued to its end without waiting for the device checks: the kernels after
-    // them skip flagged input (guard) and the verdict comes with the final read-back.
-    const bool host_sizes = !on_device && m < kHostSizesMaxNets;
-    int32_t max_size = 0;
     const int32_t *guard = nullptr;
     if (host_sizes) {
-        if (net_offsets[0] != 0) return fail(HGP_ERR_INVALID);
-        for (int32_t e = 0; e < m; ++e) {
-            const int64_t sz = net_offsets[e + 1] - net_offsets[e];
-            if (sz < 0) return fail(HGP_ERR_INVALID);
-            if (sz > max_size) max_size = (int32_t)sz;
-        }
         guard = d.err;
     } else {
         CKF(cudaMemcpyAsync(host_err, d.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CKF(cudaStreamSynchronize(st));
+        CKF(stream_wait(st));
         if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
         max_size = host_err[1];
     }
@@ -1228,7 +1324,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         while (((int64_t)1 << (31 - big_rank)) >= kBigNet) ++big_rank;
         int32_t mb = 0;
         CKF(cudaMemcpyAsync(&mb, base + (int64_t)big_rank * nr_ctas, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CKF(cudaStreamSynchronize(st));
+        CKF(stream_wait(st));
         k_nr_place<<<(unsigned)nr_ctas, kNrThreads, 0, st>>>(net_off, m, per_cta, base, perm, tmp); h->launches++;
         CKF(scan(tmp, off_int, m));   // sizes in internal order -> offsets (off_int[m] = P)
         k_nr_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, nw_d, m, perm, off_int,
@@ -1236,7 +1332,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         CKF(cudaGetLastError());
         CKF(cudaFreeAsync(cnt, st));
         CKF(cudaMemcpyAsync(&p_big, off_int + mb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CKF(cudaStreamSynchronize(st));
+        CKF(stream_wait(st));
         h->m_big = mb;
         h->m_big32 = (int32_t)std::min((int64_t)m, ((int64_t)mb + 31) / 32 * 32);
         release(net_off);
@@ -1266,7 +1362,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         CKF(scan(tmp, widx, m));
         int32_t nwide = 0;
         CKF(cudaMemcpyAsync(&nwide, widx + m, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CKF(cudaStreamSynchronize(st));
+        CKF(stream_wait(st));
         h->n_wide = nwide;
         d.widx = widx;
         int32_t *pw = nullptr;
@@ -1417,7 +1513,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     CKF(cudaMemcpyAsync(bw, d.bw, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, st));
     CKF(cudaMemcpyAsync(host_err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CKF(cudaMemcpyAsync(&maxw, maxw_d, sizeof(maxw), cudaMemcpyDeviceToHost, st));
-    CKF(cudaStreamSynchronize(st));
+    CKF(stream_wait(st));
     if (host_err[0] & ERR_INVALID) return fail(HGP_ERR_INVALID);
     if (host_err[0] & ERR_UNSUPPORTED) return fail(HGP_ERR_UNSUPPORTED);
     h->max_vertex_netweight = (int64_t)maxw;
@@ -1429,8 +1525,9 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
 
     // the int64 offsets and the int32 partition copy are no longer needed
     for (int i = 0; i < h->n_allocs; ++i) {
-        if (h->allocs[i] == off64 || h->allocs[i] == part_in || h->allocs[i] == block_sums ||
-            h->allocs[i] == tmp) {
+        if (h->allocs[i] && !in_arena(h, h->allocs[i]) &&
+            (h->allocs[i] == off64 || h->allocs[i] == part_in || h->allocs[i] == block_sums ||
+             h->allocs[i] == tmp)) {
             dev_free(h->allocs[i], st);
             h->allocs[i] = nullptr;
         }
@@ -1454,6 +1551,12 @@ void hgp_default_options(hgp_options *opt)
     if (!opt) return;
     memset(opt, 0, sizeof(*opt));
     opt->subrounds = 4;
+}
+
+int hgp_set_blocking_waits(int32_t on)
+{
+    hgp::g_blocking_waits.store(on ? 1 : 0, std::memory_order_relaxed);
+    return HGP_OK;
 }
 
 int hgp_set_pool_retention(int64_t bytes)
@@ -1512,8 +1615,8 @@ void hgp_destroy(hgp_handle *h)
     delete[] h->events;
     delete[] h->event_phase;
     delete[] h->event_count;
-    if (h->d.stats) dev_free(h->d.stats, h->stream);
-    if (h->d_dev) dev_free(h->d_dev, h->stream);
+    if (h->d.stats && !in_arena(h, h->d.stats)) dev_free(h->d.stats, h->stream);
+    if (h->d_dev && !in_arena(h, h->d_dev)) dev_free(h->d_dev, h->stream);
     free(h->h_stats);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     (void)cudaGetLastError();
@@ -1537,7 +1640,7 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
         k_check_vertices<<<grid_for(d.n, 256), 256, 0, st>>>(nullptr, tmp, d.n, d.k, d.err); h->launches++;
         e = cudaMemcpyAsync(&err, d.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = stream_wait(st);
     if (e == cudaSuccess && (err & ERR_INVALID)) rc = HGP_ERR_INVALID;
     if (e == cudaSuccess && rc == HGP_OK) {
         k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n); h->launches++;
@@ -1575,7 +1678,7 @@ int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t 
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(moved_nets, tmp, (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
         cudaFreeAsync(tmp, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = stream_wait(h->stream);
         CK(e);
     }
     if (next_round) *next_round = h->next_round;
@@ -1604,13 +1707,13 @@ int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_ne
             e = cudaGetLastError();
         }
         cudaFreeAsync(tmp, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = stream_wait(h->stream);
         CK(e);
     }
     k_set_round_state<<<1, 32, 0, h->stream>>>(d.rs, r, first_round ? 0 : 1);
     h->launches++;
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(h->stream));
+    CK(stream_wait(h->stream));
     h->next_round = next_round;
     h->all_eligible = first_round != 0;
     return HGP_OK;
@@ -1621,7 +1724,7 @@ int hgp_objective(hgp_handle *h, int64_t *out)
     if (!h || !out) return HGP_ERR_INVALID;
     settle(h);
     CK(cudaMemcpyAsync(out, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    CK(stream_wait(h->stream));
     return HGP_OK;
 }
 
@@ -1634,7 +1737,7 @@ int hgp_objective_from_phi(hgp_handle *h, int64_t *out)
     cudaError_t e = objective_from_phi(h, reinterpret_cast<int64_t *>(tmp));
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
 }
@@ -1648,7 +1751,7 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
     if (on_device) {
         k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, part, d.n); h->launches++;
         CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(st));
+        CK(stream_wait(st));
         return HGP_OK;
     }
     int32_t *tmp = nullptr;
@@ -1657,7 +1760,7 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(part, tmp, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(tmp, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = stream_wait(st);
     CK(e);
     return HGP_OK;
 }
@@ -1667,7 +1770,7 @@ int hgp_get_block_weights(hgp_handle *h, int64_t *w)
     if (!h || !w) return HGP_ERR_INVALID;
     settle(h);
     CK(cudaMemcpyAsync(w, h->d.bw, sizeof(int64_t) * h->d.k, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    CK(stream_wait(h->stream));
     return HGP_OK;
 }
 
@@ -1684,7 +1787,7 @@ int hgp_get_phi(hgp_handle *h, int32_t *phi)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(phi, tmp, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
 }
@@ -1702,7 +1805,7 @@ int hgp_get_lambda(hgp_handle *h, uint64_t *lam)
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, tmp, sizeof(uint64_t) * (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
     cudaFreeAsync(tmp, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
 }

@@ -121,6 +121,8 @@ def load_library():
         lib.hgp_batch_get_launch_count.argtypes = [P, P]
         lib.hgp_batch_get_stats.argtypes = [P, i32, P]
         lib.hgp_batch_query.argtypes = [P, P]
+        lib.hgp_set_blocking_waits.argtypes = [i32]
+        lib.hgp_set_blocking_waits.restype = ctypes.c_int
         for name in ("hgp_batch_create", "hgp_batch_refine", "hgp_batch_synchronize",
                      "hgp_batch_get_launch_count", "hgp_batch_get_stats", "hgp_batch_query"):
             getattr(lib, name).restype = ctypes.c_int
@@ -450,6 +452,12 @@ def set_pool_retention(nbytes: int):
     """hgp_set_pool_retention: freed device memory the library's pool of the current device
     keeps for reuse (0 = give it back at the next synchronisation)."""
     _check(load_library().hgp_set_pool_retention(int(nbytes)), "hgp_set_pool_retention")
+
+
+def set_blocking_waits(on: bool):
+    """hgp_set_blocking_waits: the library's host waits sleep on blocking-sync events (True)
+    or spin (False, the default).  Process-wide."""
+    _check(load_library().hgp_set_blocking_waits(1 if on else 0), "hgp_set_blocking_waits")
 
 
 def probe_gather(array_bytes: int = 1600 << 20, n_gathers: int = 86_000_000):

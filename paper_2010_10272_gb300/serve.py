@@ -34,7 +34,7 @@ from typing import Deque, Dict, List, Optional
 
 import numpy as np
 
-from .native import HGP, Batch
+from .native import HGP, Batch, set_blocking_waits
 
 _RANGE = 256
 _TILE = 2048
@@ -128,12 +128,14 @@ class Server:
     creators: threads that create and retire request state (0: the serving thread itself);
     ctas_per_sm: persistent grid of the batch's gain and apply kernels (0: by occupancy; fewer
     leave room on each SM for the creations' kernels); depth: ticks queued on the device at once
-    (1: each tick's results are read before the next is queued)."""
+    (1: each tick's results are read before the next is queued); blocking_waits: the library's
+    host waits sleep instead of spinning (hgp_set_blocking_waits, process-wide), so that waiting
+    creator threads leave the CPU to the others."""
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
                  memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
                  graph: bool = False, creators: int = 8, ctas_per_sm: int = 0, join_at: int = 0,
-                 depth: int = 1, clock=time.perf_counter):
+                 depth: int = 1, blocking_waits: bool = False, clock=time.perf_counter):
         import torch
         self._torch = torch
         self.stream = stream
@@ -150,6 +152,8 @@ class Server:
         if depth < 1:
             raise ValueError("depth must be at least 1")
         self.depth = int(depth)
+        if blocking_waits:
+            set_blocking_waits(True)
         self.clock = clock
         self.queue: Deque[Request] = collections.deque()
         self.staged: Deque[Request] = collections.deque()
