@@ -31,6 +31,8 @@ struct hgp_handle {
     // creation makes one pool call instead of ~25 (pool calls from many threads contend)
     char *arena = nullptr;
     size_t arena_size = 0, arena_used = 0;
+    int32_t *scratch_n = nullptr;  // int32[n] in the arena (the creation's scan scratch), reused by
+                                   // partition uploads and read-backs; nullptr without an arena
     // CUDA-graph cache: one refine() of `graph_rounds` rounds
     cudaGraphExec_t graph_exec = nullptr;
     int32_t graph_rounds = 0;

@@ -1532,6 +1532,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
             h->allocs[i] = nullptr;
         }
     }
+    if (in_arena(h, tmp)) h->scratch_n = tmp;   // max(n, m) + 1 entries, free from here on
     rc = ensure_stats(h, 16);
     if (rc != HGP_OK) return fail(rc);
     // the event a batch records its end on (see settle); made here, on the creating thread
@@ -1629,8 +1630,8 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
     settle(h);
     Dev &d = h->d;
     cudaStream_t st = h->stream;
-    int32_t *tmp = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    int32_t *tmp = h->scratch_n;
+    if (!tmp) CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
     int rc = HGP_OK;
     int32_t err = 0;
     cudaError_t e = cudaMemcpyAsync(tmp, part, sizeof(int32_t) * (size_t)d.n,
@@ -1646,7 +1647,7 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
         k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n); h->launches++;
         e = cudaGetLastError();
     }
-    cudaFreeAsync(tmp, st);
+    if (tmp != h->scratch_n) cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -1754,12 +1755,12 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
         CK(stream_wait(st));
         return HGP_OK;
     }
-    int32_t *tmp = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    int32_t *tmp = h->scratch_n;
+    if (!tmp) CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
     k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, tmp, d.n); h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(part, tmp, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(tmp, st);
+    if (tmp != h->scratch_n) cudaFreeAsync(tmp, st);
     if (e == cudaSuccess) e = stream_wait(st);
     CK(e);
     return HGP_OK;

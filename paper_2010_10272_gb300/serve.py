@@ -201,9 +201,10 @@ class Server:
                    req.net_w, subrounds=req.subrounds, seed=req.seed, stream=stream)
 
     def _retire(self, req: Request, h: HGP) -> Request:
-        """Result to the host, device state released (on the request's own stream)."""
+        """Result to the host, device state released (on the request's own stream).  The
+        objective is the last round's, from the batch statistics (no read-back of its own)."""
         req.result = h.partition()
-        req.objective = h.objective()
+        req.objective = int(req.stats[-1][0]) if req.stats is not None and len(req.stats) else h.objective()
         h.close()
         req.finished = self.clock()
         return req
