@@ -838,7 +838,7 @@ def serving_section(args, stream):
     def run(reqs, arrivals):
         srv = Server(stream=stream, creators=args.serve_creators, ctas_per_sm=args.serve_ctas,
                      join_at=args.serve_join_at, depth=args.serve_depth,
-                     blocking_waits=bool(args.serve_blocking))
+                     blocking_waits=bool(args.serve_blocking), tick_streams=args.serve_streams)
         order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
         t_start = time.perf_counter()
         nxt, done = 0, []
@@ -885,7 +885,8 @@ def serving_section(args, stream):
         "service_capacity_req_per_s": mu, "saturated_pin_rounds_per_s": sat["pin_rounds_per_s"],
         "saturated": sat, "poisson": rates, "generate_s": gen_s,
         "server": {"creators": args.serve_creators, "ctas_per_sm": args.serve_ctas, "join_at": args.serve_join_at,
-                   "depth": args.serve_depth, "blocking_waits": bool(args.serve_blocking)},
+                   "depth": args.serve_depth, "blocking_waits": bool(args.serve_blocking),
+                   "tick_streams": args.serve_streams},
         "latency": "arrival -> partition on the host",
     }
 
@@ -935,10 +936,12 @@ def main():
     ap.add_argument("--serve-seed", type=int, default=1)
     ap.add_argument("--serve-creators", type=int, default=8,
                     help="serving: threads creating and retiring request state")
-    ap.add_argument("--serve-depth", type=int, default=1,
+    ap.add_argument("--serve-depth", type=int, default=2,
                     help="serving ticks queued on the device at once (1: read each before the next)")
     ap.add_argument("--serve-blocking", type=int, default=0,
                     help="1: the library's host waits sleep instead of spinning while serving")
+    ap.add_argument("--serve-streams", type=int, default=2,
+                    help="streams the serving ticks take in turn (with --serve-depth >= 2 they overlap)")
     ap.add_argument("--serve-join-at", type=int, default=0,
                     help="serving: staged requests join only when at most this many run (0: at every round)")
     ap.add_argument("--serve-ctas", type=int, default=0,

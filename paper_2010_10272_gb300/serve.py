@@ -130,15 +130,22 @@ class Server:
     leave room on each SM for the creations' kernels); depth: ticks queued on the device at once
     (1: each tick's results are read before the next is queued); blocking_waits: the library's
     host waits sleep instead of spinning (hgp_set_blocking_waits, process-wide), so that waiting
-    creator threads leave the CPU to the others."""
+    creator threads leave the CPU to the others; tick_streams: streams the ticks take in turn
+    (with depth >= 2, consecutive ticks then run concurrently and fill each other's launch gaps;
+    a request in two ticks is ordered between them by the batches)."""
 
     def __init__(self, stream=None, reserve_bytes: int = 1 << 30,
                  memory_budget: Optional[int] = None, max_active: int = 1024, max_staged: int = 256,
                  graph: bool = False, creators: int = 8, ctas_per_sm: int = 0, join_at: int = 0,
-                 depth: int = 1, blocking_waits: bool = False, clock=time.perf_counter):
+                 depth: int = 2, blocking_waits: bool = False, tick_streams: int = 2,
+                 clock=time.perf_counter):
         import torch
         self._torch = torch
         self.stream = stream
+        self._tick_streams = [stream]
+        if stream is not None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            self._tick_streams += [torch.cuda.Stream(dev) for _ in range(int(tick_streams) - 1)]
         self.reserve = int(reserve_bytes)
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info()
@@ -260,7 +267,8 @@ class Server:
     def _launch(self):
         """Queues the next rounds of the active requests as one batch call (no host wait)."""
         members = list(self.active)
-        batch = Batch([self._handles[r.rid] for r in members], graph=self.graph, stream=self.stream,
+        batch = Batch([self._handles[r.rid] for r in members], graph=self.graph,
+                      stream=self._tick_streams[self.ticks % len(self._tick_streams)],
                       gain_ctas_per_sm=self.ctas_per_sm, apply_ctas_per_sm=self.ctas_per_sm)
         rounds = min(r.rounds - self._planned[r.rid] for r in members)
         if rounds:

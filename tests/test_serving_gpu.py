@@ -37,16 +37,18 @@ def _alone(req):
     return out
 
 
-@pytest.mark.parametrize("budget,depth,own_streams", [(None, 2, False), (96 << 20, 2, False),
-                                                      (None, 1, False), (96 << 20, 3, False),
-                                                      (None, 2, True)])
-def test_mix_equals_alone(budget, depth, own_streams):
-    """own_streams: no server stream, so every tick's batch runs on a stream of its own and the
-    requests that continue from one tick to the next are ordered across batches."""
+@pytest.mark.parametrize("budget,depth,own_streams,tick_streams",
+                         [(None, 2, False, 1), (96 << 20, 2, False, 1), (None, 1, False, 1),
+                          (96 << 20, 3, False, 1), (None, 2, True, 1), (None, 2, False, 2),
+                          (96 << 20, 3, False, 3)])
+def test_mix_equals_alone(budget, depth, own_streams, tick_streams):
+    """own_streams: no server stream, so every tick's batch runs on a stream of its own;
+    tick_streams: ticks take server streams in turn.  Either way the requests that continue
+    from one tick to the next are ordered across batches on different streams."""
     from paper_2010_10272_gb300.serve import Server
     reqs = _requests()
     s = None if own_streams else torch.cuda.Stream()
-    srv = Server(stream=s, memory_budget=budget, reserve_bytes=0, depth=depth)
+    srv = Server(stream=s, memory_budget=budget, reserve_bytes=0, depth=depth, tick_streams=tick_streams)
     done = []
     pending = list(reqs)
     # arrivals in waves while earlier requests are still running
