@@ -256,6 +256,12 @@ int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats);
  * else 0.  Does not block. */
 int hgp_batch_query(hgp_batch *b, int32_t *done);
 
+/* Partitions Pi of the members listed in `members` (count indices into the batch's handles) as
+ * they are after the batch's last hgp_batch_refine call, written back to back into host int32
+ * `out` (the members' vertex counts summed, in the listed order).  Waits for that call only;
+ * one copy and one wait for all of them (a serving loop retiring the members a call finished). */
+int hgp_batch_get_partitions(hgp_batch *b, const int32_t *members, int32_t count, int32_t *out);
+
 /* Waits for the batch's queued work. */
 int hgp_batch_synchronize(hgp_batch *b);
 

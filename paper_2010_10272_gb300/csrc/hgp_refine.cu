@@ -34,6 +34,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1580,6 +1582,13 @@ __global__ void __launch_bounds__(kThreads) k_rv_revert(const Dev d, int32_t rr)
     }
 }
 
+// Pi of one handle widened to int32 (batch partition read-back)
+__global__ void k_part_widen(const uint8_t *part, int32_t n, int32_t *out)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = part[v];
+}
+
 // thread per instance: per-round objective and heaviest block; advance the round state
 __global__ void k_round_end(const Dev *devs, int32_t n_inst, int32_t rr, int32_t advance = 1)
 {
@@ -2597,6 +2606,61 @@ int hgp_batch_get_stats(hgp_batch *b, int32_t rounds, hgp_round_stats *stats)
         return status_of(e);
     }
     return batch_stats_unpack(b, rounds, stats);
+}
+
+static std::mutex g_stage_mu;       // page-locked staging of hgp_batch_get_partitions
+static void *g_stage = nullptr;
+static size_t g_stage_cap = 0;
+
+int hgp_batch_get_partitions(hgp_batch *b, const int32_t *members, int32_t count, int32_t *out)
+{
+    if (!b || count < 0 || (count > 0 && (!members || !out))) return HGP_ERR_INVALID;
+    int64_t total = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (members[i] < 0 || members[i] >= (int32_t)b->hs.size()) return HGP_ERR_INVALID;
+        total += b->hs[members[i]]->d.n;
+    }
+    if (total == 0) return HGP_OK;
+    // after the batch's last call only (work queued on its stream later is not waited for)
+    cudaError_t e = cudaSuccess;
+    if (!b->aux) {
+        e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+        if (e != cudaSuccess) b->aux = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_end, 0);
+    int32_t *stage = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&stage), sizeof(int32_t) * (size_t)total, b->aux);
+    int64_t off = 0;
+    for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
+        const Dev &d = b->hs[members[i]]->d;
+        const int grid = (int)std::min<int64_t>((d.n + 255) / 256, 152 * 8);
+        k_part_widen<<<grid, 256, 0, b->aux>>>(d.part, d.n, stage + off);
+        e = cudaGetLastError();
+        off += d.n;
+        b->launches++;
+    }
+    // through a page-locked staging buffer of the library (grown when needed), so the copy runs
+    // at the link's rate whatever memory `out` is
+    const size_t bytes = sizeof(int32_t) * (size_t)total;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (e == cudaSuccess && g_stage_cap < bytes) {
+        if (g_stage) cudaFreeHost(g_stage);
+        g_stage = nullptr;
+        g_stage_cap = 0;
+        const size_t cap = std::max(bytes, (size_t)16 << 20);
+        e = cudaMallocHost(&g_stage, cap);
+        if (e == cudaSuccess) g_stage_cap = cap;
+        else g_stage = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_stage, stage, bytes, cudaMemcpyDeviceToHost, b->aux);
+    if (stage) dev_free(stage, b->aux);
+    if (e == cudaSuccess) e = stream_wait(b->aux);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return status_of(e);
+    }
+    memcpy(out, g_stage, bytes);
+    return HGP_OK;
 }
 
 int hgp_batch_query(hgp_batch *b, int32_t *done)

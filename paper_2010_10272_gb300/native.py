@@ -121,10 +121,12 @@ def load_library():
         lib.hgp_batch_get_launch_count.argtypes = [P, P]
         lib.hgp_batch_get_stats.argtypes = [P, i32, P]
         lib.hgp_batch_query.argtypes = [P, P]
+        lib.hgp_batch_get_partitions.argtypes = [P, P, i32, P]
         lib.hgp_set_blocking_waits.argtypes = [i32]
         lib.hgp_set_blocking_waits.restype = ctypes.c_int
         for name in ("hgp_batch_create", "hgp_batch_refine", "hgp_batch_synchronize",
-                     "hgp_batch_get_launch_count", "hgp_batch_get_stats", "hgp_batch_query"):
+                     "hgp_batch_get_launch_count", "hgp_batch_get_stats", "hgp_batch_query",
+                     "hgp_batch_get_partitions"):
             getattr(lib, name).restype = ctypes.c_int
         lib.hgp_set_pool_retention.argtypes = [i64]
         lib.hgp_set_pool_retention.restype = ctypes.c_int
@@ -408,6 +410,16 @@ class Batch:
             return _stats_array(buf, n * rounds).reshape(n, rounds, len(STAT_FIELDS))
         _check(self._lib.hgp_batch_refine(self._b, int(rounds), None), "hgp_batch_refine")
         return None
+
+    def partitions(self, members):
+        """Partitions of the listed members (indices into handles) after the last refine call,
+        with one copy and one wait: a list of int32 arrays."""
+        idx = np.ascontiguousarray(np.asarray(members, dtype=np.int32))
+        sizes = [self.handles[i].n for i in idx.tolist()]
+        out = np.empty(int(sum(sizes)), dtype=np.int32)
+        _check(self._lib.hgp_batch_get_partitions(self._b, idx.ctypes.data_as(ctypes.c_void_p), int(idx.size),
+                                                  out.ctypes.data_as(ctypes.c_void_p)), "hgp_batch_get_partitions")
+        return np.split(out, np.cumsum(sizes)[:-1]) if sizes else []
 
     def done(self) -> bool:
         """Whether the last refine call has finished on the device (does not block)."""

@@ -15,10 +15,10 @@ tick of the server
      decides how many requests run at once; the new handles are staged and join the batch at
      the next tick (a round boundary);
   3. once the oldest queued tick has finished, reads its statistics (waiting for that tick
-     only) and retires the requests it completed, on the creator threads too: each partition is
-     read back to the host and its device state released (queued behind the batch's rounds on
-     the request's own stream, without synchronising the device), and the latency (arrival ->
-     result on the host) is recorded.
+     only) and hands the requests it completed to a creator thread, which reads their
+     partitions with one copy (hgp_batch_get_partitions), records their latency (arrival ->
+     result on the host) and releases the tick's batch and their device state (queued behind
+     the batch's rounds on each request's own stream, without synchronising the device).
 Device memory comes from the library's stream-ordered pool, so creating and releasing request
 state never synchronises the device.  Each request's arithmetic is the same as refining it
 alone: batching changes only which kernel launch does the work (see tests/test_serving_gpu.py).
@@ -207,14 +207,19 @@ class Server:
         return HGP(req.n, req.m, req.net_off, req.pins, req.k, req.eps, req.part, req.vertex_w,
                    req.net_w, subrounds=req.subrounds, seed=req.seed, stream=stream)
 
-    def _retire(self, req: Request, h: HGP) -> Request:
-        """Result to the host, device state released (on the request's own stream).  The
-        objective is the last round's, from the batch statistics (no read-back of its own)."""
-        req.result = h.partition()
-        req.objective = int(req.stats[-1][0]) if req.stats is not None and len(req.stats) else h.objective()
-        h.close()
-        req.finished = self.clock()
-        return req
+    def _retire_group(self, batch, slots, reqs, handles):
+        """The partitions of the requests a tick finished, read with one copy
+        (hgp_batch_get_partitions), then the tick's batch and the requests' device state
+        released (queued on each request's own stream, behind the batch)."""
+        parts = batch.partitions(slots) if slots else [h.partition() for h in handles]
+        now = self.clock()
+        for req, part, h in zip(reqs, parts, handles):
+            req.result = part
+            req.finished = now
+            req.objective = int(req.stats[-1][0]) if len(req.stats) else h.objective()
+        batch.close()
+        for h in handles:
+            h.close()
 
     def _install(self, req: Request, h: HGP):
         req.admitted = self.clock()
@@ -290,16 +295,20 @@ class Server:
             st = batch.stats(rounds)            # waits for this tick only
             for i, req in enumerate(members):
                 self._stats[req.rid].extend(st[i])
-        batch.close()
+        slot = {r.rid: i for i, r in enumerate(members)}
+        slots = [slot[r.rid] for r in finishing] if rounds else []
+        handles = [self._handles.pop(r.rid) for r in finishing]
         for req in finishing:
-            h = self._handles.pop(req.rid)
             req.stats = np.array(self._stats.pop(req.rid), dtype=np.int64)
             self._planned.pop(req.rid)
-            if self._pool is not None:
-                self._retiring.append((req, self._pool.submit(self._retire, req, h)))
-            else:
+        if self._pool is not None and finishing:
+            fut = self._pool.submit(self._retire_group, batch, slots, finishing, handles)
+            for req in finishing:
+                self._retiring.append((req, fut))
+        else:
+            self._retire_group(batch, slots, finishing, handles)
+            for req in finishing:
                 self._retiring.append((req, None))
-                self._retire(req, h)
 
     # -- one tick
     def step(self) -> List[Request]:

@@ -49,6 +49,7 @@ def test_host_only_functions(lib):
     assert lib.hgp_set_pool_retention(-1) == 1
     assert lib.hgp_batch_get_stats(None, 1, None) == 1
     assert lib.hgp_batch_query(None, None) == 1
+    assert lib.hgp_batch_get_partitions(None, None, 0, None) == 1
 
 
 def test_struct_layout_matches_header(lib):

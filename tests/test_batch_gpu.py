@@ -199,6 +199,27 @@ def test_batches_on_different_streams_share_members():
         h.close()
 
 
+def test_batch_partitions_read_back_together():
+    """hgp_batch_get_partitions: the listed members' partitions after the last call, back to
+    back, in the listed order; equal to each handle's own read-back and to the oracle."""
+    from paper_2010_10272_gb300 import HGP, Batch
+    members = _members()[:7]
+    hs = [HGP.from_hypergraph(hg, subrounds=S, phi_width=pw, seed=6) for hg, S, pw in members]
+    b = Batch(hs, graph=False, stream=torch.cuda.Stream())
+    b.refine(2, stats=False)
+    order = [5, 0, 3, 6]
+    parts = b.partitions(order)
+    assert b.partitions([]) == []
+    for i, p in zip(order, parts):
+        o = oracle.Oracle.from_hypergraph(members[i][0], subrounds=members[i][1], seed=6)
+        o.refine(2)
+        np.testing.assert_array_equal(p, o.partition())
+        np.testing.assert_array_equal(p, hs[i].partition())
+    b.close()
+    for h in hs:
+        h.close()
+
+
 def test_pool_retention_keeps_results():
     """With the library's pool keeping freed memory (hgp_set_pool_retention), handles created
     and destroyed in a loop give the same results as without."""

@@ -45,6 +45,9 @@ class FakeBatch:
     def done(self):
         return True
 
+    def partitions(self, idx):
+        return [self.handles[i].partition() for i in idx]
+
     def synchronize(self):
         pass
 
