@@ -96,20 +96,20 @@ cudaError_t scan_excl(const T *in, int64_t len, int64_t *out, cudaStream_t st)
 {
     const int64_t tiles = len / kScanTile + 1;   // covers indices 0..len
     int64_t *sums = nullptr, *pref = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&sums), sizeof(int64_t) * (size_t)tiles, st);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&sums), sizeof(int64_t) * (size_t)tiles, st);
     if (e != cudaSuccess) return e;
     k_scan_tile<T><<<(unsigned)tiles, kScanTile, 0, st>>>(in, len, out, sums);
     e = cudaGetLastError();
     if (e == cudaSuccess && tiles > 1) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&pref), sizeof(int64_t) * (size_t)(tiles + 1), st);
+        e = dev_alloc(reinterpret_cast<void **>(&pref), sizeof(int64_t) * (size_t)(tiles + 1), st);
         if (e == cudaSuccess) e = scan_excl<int64_t>(sums, tiles, pref, st);
         if (e == cudaSuccess) {
             k_scan_add<<<(unsigned)tiles, kScanTile, 0, st>>>(out, len, pref);
             e = cudaGetLastError();
         }
-        if (pref) cudaFreeAsync(pref, st);
+        if (pref) pool_free(pref, st);
     }
-    cudaFreeAsync(sums, st);
+    pool_free(sums, st);
     return e;
 }
 
@@ -760,7 +760,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(stream_wait(st));
     if (P < 0 || (m == 0 && P != 0)) { rc = HGP_ERR_INVALID; goto done; }
     if (P >= ((int64_t)1 << 31)) { rc = HGP_ERR_UNSUPPORTED; goto done; }
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int32_t) * 2, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&err), sizeof(int32_t) * 2, st));
     CT(cudaMemsetAsync(err, 0, sizeof(int32_t) * 2, st));
     left = err + 1;
     k_ct_check<<<grid_of(P > n ? P : n, 256), 256, 0, st>>>(net_off, pins, vertex_w, net_w, n, m, P, err);
@@ -769,8 +769,8 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     CT(stream_wait(st));
     if (herr) { rc = HGP_ERR_INVALID; goto done; }
     // (1) remap the used cluster ids
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&used), sizeof(int32_t) * (size_t)n, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&cid), sizeof(int64_t) * ((size_t)n + 1), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&used), sizeof(int32_t) * (size_t)n, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&cid), sizeof(int64_t) * ((size_t)n + 1), st));
     CT(cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)n, st));
     k_ct_flag<<<grid_of(n, 256), 256, 0, st>>>(cluster, n, used, err);
     CT(cudaGetLastError());
@@ -783,18 +783,18 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     // (2) map and cluster weights
     CT(cudaMalloc(reinterpret_cast<void **>(&c->map), sizeof(int32_t) * (size_t)n));
     CT(cudaMalloc(reinterpret_cast<void **>(&c->vw), sizeof(int32_t) * (size_t)n2));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&w64), sizeof(unsigned long long) * (size_t)(n > mm ? n : mm), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&w64), sizeof(unsigned long long) * (size_t)(n > mm ? n : mm), st));
     CT(cudaMemsetAsync(w64, 0, sizeof(unsigned long long) * (size_t)n2, st));
     k_ct_map<<<grid_of(n, 256), 256, 0, st>>>(cluster, n, cid, vertex_w, c->map, w64);
     k_ct_narrow<<<grid_of(n2, 256), 256, 0, st>>>(w64, n2, c->vw, err);
     CT(cudaGetLastError());
     // (3) per-net sort + dedupe
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&a), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&b), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&size1), sizeof(int32_t) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&key), sizeof(unsigned long long) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&rep), sizeof(int32_t) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&lists), sizeof(int32_t) * kClasses * (size_t)mm + 32, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&a), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&b), sizeof(int32_t) * (size_t)(P > 0 ? P : 1), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&size1), sizeof(int32_t) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&key), sizeof(unsigned long long) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&rep), sizeof(int32_t) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&lists), sizeof(int32_t) * kClasses * (size_t)mm + 32, st));
     counts = lists + kClasses * mm;
     CT(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (kClasses + 1), st));
     if (m > 0) {
@@ -812,8 +812,8 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
         if (n_large > 0) {
             int32_t *chunks = nullptr;
             int64_t *cpre = nullptr;
-            CT(cudaMallocAsync(reinterpret_cast<void **>(&chunks), sizeof(int32_t) * ((size_t)n_large + 1), st));
-            CT(cudaMallocAsync(reinterpret_cast<void **>(&cpre), sizeof(int64_t) * ((size_t)n_large + 1), st));
+            CT(dev_alloc(reinterpret_cast<void **>(&chunks), sizeof(int32_t) * ((size_t)n_large + 1), st));
+            CT(dev_alloc(reinterpret_cast<void **>(&cpre), sizeof(int64_t) * ((size_t)n_large + 1), st));
             lg_scratch[0] = chunks;
             lg_scratch[1] = cpre;
             CT(cudaMemsetAsync(counts + kClasses, 0, sizeof(int32_t), st));
@@ -841,7 +841,7 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     if (m > 0) {
         uint64_t size = 1024;
         while (size < 2 * (uint64_t)m) size <<= 1;
-        CT(cudaMallocAsync(reinterpret_cast<void **>(&tab), sizeof(KeySlot) * size, st));
+        CT(dev_alloc(reinterpret_cast<void **>(&tab), sizeof(KeySlot) * size, st));
         for (int round = 0;; ++round) {
             if (round >= 4096) { rc = HGP_ERR_INTERNAL; goto done; }
             int32_t hleft = 0;
@@ -856,11 +856,11 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
         }
     }
     // (5) representatives in original order, their weights and offsets
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&is_rep), sizeof(int32_t) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&rep_size), sizeof(int32_t) * (size_t)mm, st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&nid), sizeof(int64_t) * ((size_t)m + 1), st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&poff), sizeof(int64_t) * ((size_t)m + 1), st));
-    CT(cudaMallocAsync(reinterpret_cast<void **>(&nw64), sizeof(unsigned long long) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&is_rep), sizeof(int32_t) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&rep_size), sizeof(int32_t) * (size_t)mm, st));
+    CT(dev_alloc(reinterpret_cast<void **>(&nid), sizeof(int64_t) * ((size_t)m + 1), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&poff), sizeof(int64_t) * ((size_t)m + 1), st));
+    CT(dev_alloc(reinterpret_cast<void **>(&nw64), sizeof(unsigned long long) * (size_t)mm, st));
     CT(cudaMemsetAsync(nw64, 0, sizeof(unsigned long long) * (size_t)mm, st));
     if (m > 0) {
         k_ct_groups<<<grid_of(m, 256), 256, 0, st>>>(rep, size1, net_w, m, is_rep, rep_size, nw64);
@@ -891,24 +891,24 @@ extern "C" int hgp_contract(int32_t n, int32_t m, const int64_t *net_off, const 
     if (herr & ERR_UNSUPPORTED) rc = HGP_ERR_UNSUPPORTED;
     else if (herr) rc = HGP_ERR_INTERNAL;
 done:
-    if (err) cudaFreeAsync(err, st);
-    if (used) cudaFreeAsync(used, st);
-    if (cid) cudaFreeAsync(cid, st);
-    if (w64) cudaFreeAsync(w64, st);
-    if (a) cudaFreeAsync(a, st);
-    if (b) cudaFreeAsync(b, st);
-    if (size1) cudaFreeAsync(size1, st);
-    if (key) cudaFreeAsync(key, st);
-    if (rep) cudaFreeAsync(rep, st);
-    if (tab) cudaFreeAsync(tab, st);
-    if (lists) cudaFreeAsync(lists, st);
+    if (err) pool_free(err, st);
+    if (used) pool_free(used, st);
+    if (cid) pool_free(cid, st);
+    if (w64) pool_free(w64, st);
+    if (a) pool_free(a, st);
+    if (b) pool_free(b, st);
+    if (size1) pool_free(size1, st);
+    if (key) pool_free(key, st);
+    if (rep) pool_free(rep, st);
+    if (tab) pool_free(tab, st);
+    if (lists) pool_free(lists, st);
     for (void *q : lg_scratch)
-        if (q) cudaFreeAsync(q, st);
-    if (is_rep) cudaFreeAsync(is_rep, st);
-    if (rep_size) cudaFreeAsync(rep_size, st);
-    if (nid) cudaFreeAsync(nid, st);
-    if (poff) cudaFreeAsync(poff, st);
-    if (nw64) cudaFreeAsync(nw64, st);
+        if (q) pool_free(q, st);
+    if (is_rep) pool_free(is_rep, st);
+    if (rep_size) pool_free(rep_size, st);
+    if (nid) pool_free(nid, st);
+    if (poff) pool_free(poff, st);
+    if (nw64) pool_free(nw64, st);
     {
         const cudaError_t e2 = stream_wait(st);
         if (e == cudaSuccess) e = e2;

@@ -161,11 +161,11 @@ extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *move
     int32_t herr = 0;
     unsigned long long hdeg = 0;
     int rc = HGP_OK;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&mv), sizeof(int32_t) * 3 * (size_t)count, st);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&mv), sizeof(int32_t) * 3 * (size_t)count, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(mv, moves, sizeof(int32_t) * 3 * (size_t)count, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&seen), sizeof(int32_t) * ((size_t)d.n + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int32_t), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&degsum), sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&seen), sizeof(int32_t) * ((size_t)d.n + 1), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&err), sizeof(int32_t), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&degsum), sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(seen, 0, sizeof(int32_t) * ((size_t)d.n + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(degsum, 0, sizeof(unsigned long long), st);
@@ -182,8 +182,8 @@ extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *move
     // at most 2 keys per incident net of a moved vertex; keep the table at most half full
     uint64_t size = 64;
     while (size < 4 * (uint64_t)hdeg) size <<= 1;
-    if (e == cudaSuccess && rc == HGP_OK) e = cudaMallocAsync(reinterpret_cast<void **>(&table), sizeof(Slot) * size, st);
-    if (e == cudaSuccess && rc == HGP_OK) e = cudaMallocAsync(reinterpret_cast<void **>(&g_d), sizeof(int64_t) * (size_t)count, st);
+    if (e == cudaSuccess && rc == HGP_OK) e = dev_alloc(reinterpret_cast<void **>(&table), sizeof(Slot) * size, st);
+    if (e == cudaSuccess && rc == HGP_OK) e = dev_alloc(reinterpret_cast<void **>(&g_d), sizeof(int64_t) * (size_t)count, st);
     if (e == cudaSuccess && rc == HGP_OK) {
         k_eg_init<<<grid_of((int64_t)size, 256), 256, 0, st>>>(table, size);
         k_eg_pass1<<<grid_of((int64_t)count * 32, 256), 256, 0, st>>>(d, mv, count, table, size - 1, err);
@@ -193,12 +193,12 @@ extern "C" int hgp_exact_gains(hgp_handle *h, int32_t count, const int32_t *move
     }
     if (e == cudaSuccess && rc == HGP_OK) e = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && rc == HGP_OK) e = cudaMemcpyAsync(gains, g_d, sizeof(int64_t) * (size_t)count, cudaMemcpyDeviceToHost, st);
-    if (mv) cudaFreeAsync(mv, st);
-    if (seen) cudaFreeAsync(seen, st);
-    if (err) cudaFreeAsync(err, st);
-    if (degsum) cudaFreeAsync(degsum, st);
-    if (table) cudaFreeAsync(table, st);
-    if (g_d) cudaFreeAsync(g_d, st);
+    if (mv) pool_free(mv, st);
+    if (seen) pool_free(seen, st);
+    if (err) pool_free(err, st);
+    if (degsum) pool_free(degsum, st);
+    if (table) pool_free(table, st);
+    if (g_d) pool_free(g_d, st);
     const cudaError_t e2 = stream_wait(st);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) {

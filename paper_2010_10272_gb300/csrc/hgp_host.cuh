@@ -81,6 +81,8 @@ cudaError_t library_pool(cudaMemPool_t *out);
 cudaError_t stream_wait(cudaStream_t st);
 cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
 void dev_free(void *p, cudaStream_t st);
+// the same for temporaries whose release status the caller checks
+inline cudaError_t pool_free(void *p, cudaStream_t st) { return p ? cudaFreeAsync(p, st) : cudaSuccess; }
 
 // Carves `bytes` (rounded up to 256) from the handle's arena; nullptr when it has no room left.
 inline void *arena_take(hgp_handle *h, size_t bytes)

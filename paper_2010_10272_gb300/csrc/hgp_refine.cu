@@ -2048,11 +2048,11 @@ int refine_rounds(hgp_handle *h, int32_t rounds, hgp_round_stats *stats)
     if (h->debug & 1) {
         int64_t *tmp = nullptr;
         int64_t from_phi = 0, maintained = 0;
-        e = cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int64_t), h->stream);
+        e = dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(int64_t), h->stream);
         if (e == cudaSuccess) e = objective_from_phi(h, tmp);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&from_phi, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&maintained, h->d.obj, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
-        if (tmp) cudaFreeAsync(tmp, h->stream);
+        if (tmp) pool_free(tmp, h->stream);
         if (e == cudaSuccess) e = stream_wait(h->stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -2077,8 +2077,8 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     Plan p = single_plan(h);
     int32_t *t_d = nullptr;
     int64_t *g_d = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&t_d), sizeof(int32_t) * (size_t)d.n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&g_d), sizeof(int64_t) * (size_t)d.n, st);
+    e = dev_alloc(reinterpret_cast<void **>(&t_d), sizeof(int32_t) * (size_t)d.n, st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&g_d), sizeof(int64_t) * (size_t)d.n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(t_d, 0xFF, sizeof(int32_t) * (size_t)d.n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g_d, 0, sizeof(int64_t) * (size_t)d.n, st);
     // the stats row written here is scratch: refine() clears the stats before use
@@ -2094,8 +2094,8 @@ int debug_candidates(hgp_handle *h, int32_t s, int32_t *target, int64_t *gain)
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(target, t_d, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(gain, g_d, sizeof(int64_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
-    if (t_d) cudaFreeAsync(t_d, st);
-    if (g_d) cudaFreeAsync(g_d, st);
+    if (t_d) pool_free(t_d, st);
+    if (g_d) pool_free(g_d, st);
     if (e == cudaSuccess) e = stream_wait(st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -1017,7 +1017,7 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st)
 
 void dev_free(void *p, cudaStream_t st)
 {
-    if (p && cudaFreeAsync(p, st) != cudaSuccess) (void)cudaGetLastError();
+    if (p && pool_free(p, st) != cudaSuccess) (void)cudaGetLastError();
 }
 
 }  // namespace hgp
@@ -1312,7 +1312,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         const int32_t per_cta = (int32_t)((m + nr_ctas - 1) / nr_ctas);
         const int32_t nslots = (int32_t)(kNrRanks * nr_ctas);
         int32_t *cnt = nullptr, *perm = nullptr, *off_int = nullptr, *pins_int = nullptr, *nw_int = nullptr;
-        CKF(cudaMallocAsync(reinterpret_cast<void **>(&cnt), sizeof(int32_t) * (2 * (size_t)nslots + 1), st));
+        CKF(dev_alloc(reinterpret_cast<void **>(&cnt), sizeof(int32_t) * (2 * (size_t)nslots + 1), st));
         int32_t *base = cnt + nslots;
         CKF(dalloc(h, &perm, m));
         CKF(dalloc(h, &off_int, (int64_t)m + 1));
@@ -1330,7 +1330,7 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         k_nr_pins<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(net_off, pins_d, nw_d, m, perm, off_int,
                                                                   pins_int, nw_int); h->launches++;
         CKF(cudaGetLastError());
-        CKF(cudaFreeAsync(cnt, st));
+        CKF(pool_free(cnt, st));
         CKF(cudaMemcpyAsync(&p_big, off_int + mb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CKF(stream_wait(st));
         h->m_big = mb;
@@ -1395,8 +1395,8 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         per_cta = per_cta < 512 ? 512 : (per_cta > kTpNetsPerCta ? kTpNetsPerCta : per_cta);
         int32_t *bk = nullptr;           // counts [nbk + 1], offsets [nbk + 1], cursors [nbk]
         unsigned long long *pairs = nullptr;
-        CKF(cudaMallocAsync(reinterpret_cast<void **>(&bk), sizeof(int32_t) * (3 * (size_t)nbk + 2), st));
-        CKF(cudaMallocAsync(reinterpret_cast<void **>(&pairs), sizeof(unsigned long long) * (size_t)P, st));
+        CKF(dev_alloc(reinterpret_cast<void **>(&bk), sizeof(int32_t) * (3 * (size_t)nbk + 2), st));
+        CKF(dev_alloc(reinterpret_cast<void **>(&pairs), sizeof(unsigned long long) * (size_t)P, st));
         int32_t *bk_cnt = bk, *bk_off = bk + nbk + 1, *bk_cur = bk + 2 * nbk + 2;
         CKF(cudaMemsetAsync(bk_cnt, 0, sizeof(int32_t) * ((size_t)nbk + 1), st));
         k_tp_hist<<<grid_for(P, 256, 152 * 8), 256, 0, st>>>(pins_d, P, bshift, nbk, bk_cnt, guard); h->launches++;
@@ -1421,8 +1421,8 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
         }
         h->launches++;
         CKF(cudaGetLastError());
-        CKF(cudaFreeAsync(pairs, st));
-        CKF(cudaFreeAsync(bk, st));
+        CKF(pool_free(pairs, st));
+        CKF(pool_free(bk, st));
     } else {
         CKF(cudaMemsetAsync(vtx_off, 0, sizeof(int32_t) * ((size_t)n + 1), st));
     }
@@ -1631,7 +1631,7 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
     Dev &d = h->d;
     cudaStream_t st = h->stream;
     int32_t *tmp = h->scratch_n;
-    if (!tmp) CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    if (!tmp) CK(dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
     int rc = HGP_OK;
     int32_t err = 0;
     cudaError_t e = cudaMemcpyAsync(tmp, part, sizeof(int32_t) * (size_t)d.n,
@@ -1647,7 +1647,7 @@ int hgp_set_partition(hgp_handle *h, const int32_t *part, int32_t on_device)
         k_copy_part<<<grid_for(d.n, 256), 256, 0, st>>>(tmp, d.part, d.n); h->launches++;
         e = cudaGetLastError();
     }
-    if (tmp != h->scratch_n) cudaFreeAsync(tmp, st);
+    if (tmp != h->scratch_n) pool_free(tmp, st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return status_of(e);
@@ -1668,7 +1668,7 @@ int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t 
     if (moved_nets && h->d.m > 0) {
         Dev &d = h->d;
         uint8_t *tmp = nullptr;
-        CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
+        CK(dev_alloc(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
         if (d.k <= 32)
             k_export_moved<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, (int32_t)h->next_round,
                                                                              h->all_eligible ? 1 : 0, tmp);
@@ -1678,7 +1678,7 @@ int hgp_export_state(hgp_handle *h, int32_t *part, uint8_t *moved_nets, int64_t 
         h->launches++;
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(moved_nets, tmp, (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
-        cudaFreeAsync(tmp, h->stream);
+        pool_free(tmp, h->stream);
         if (e == cudaSuccess) e = stream_wait(h->stream);
         CK(e);
     }
@@ -1699,7 +1699,7 @@ int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_ne
     const int32_t r = (int32_t)next_round;
     if (!first_round && d.m > 0) {
         uint8_t *tmp = nullptr;
-        CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
+        CK(dev_alloc(reinterpret_cast<void **>(&tmp), (size_t)d.m, h->stream));
         cudaError_t e = cudaMemcpyAsync(tmp, moved_nets, (size_t)d.m, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) {
             if (d.k <= 32) k_import_moved<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, r, tmp);
@@ -1707,7 +1707,7 @@ int hgp_import_state(hgp_handle *h, const int32_t *part, const uint8_t *moved_ne
             h->launches++;
             e = cudaGetLastError();
         }
-        cudaFreeAsync(tmp, h->stream);
+        pool_free(tmp, h->stream);
         if (e == cudaSuccess) e = stream_wait(h->stream);
         CK(e);
     }
@@ -1734,10 +1734,10 @@ int hgp_objective_from_phi(hgp_handle *h, int64_t *out)
     if (!h || !out) return HGP_ERR_INVALID;
     settle(h);
     unsigned long long *tmp = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(*tmp), h->stream));
+    CK(dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(*tmp), h->stream));
     cudaError_t e = objective_from_phi(h, reinterpret_cast<int64_t *>(tmp));
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream);
-    cudaFreeAsync(tmp, h->stream);
+    pool_free(tmp, h->stream);
     if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
@@ -1756,11 +1756,11 @@ int hgp_get_partition(hgp_handle *h, int32_t *part, int32_t on_device)
         return HGP_OK;
     }
     int32_t *tmp = h->scratch_n;
-    if (!tmp) CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
+    if (!tmp) CK(dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)d.n, st));
     k_part_to_i32<<<grid_for(d.n, 256), 256, 0, st>>>(d.part, tmp, d.n); h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(part, tmp, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, st);
-    if (tmp != h->scratch_n) cudaFreeAsync(tmp, st);
+    if (tmp != h->scratch_n) pool_free(tmp, st);
     if (e == cudaSuccess) e = stream_wait(st);
     CK(e);
     return HGP_OK;
@@ -1783,11 +1783,11 @@ int hgp_get_phi(hgp_handle *h, int32_t *phi)
     const int64_t total = (int64_t)d.m * d.k;
     if (total == 0) return HGP_OK;
     int32_t *tmp = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)total, h->stream));
+    CK(dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(int32_t) * (size_t)total, h->stream));
     k_widen_phi<<<grid_for(total, 256), 256, 0, h->stream>>>(d, tmp); h->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(phi, tmp, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, h->stream);
-    cudaFreeAsync(tmp, h->stream);
+    pool_free(tmp, h->stream);
     if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
@@ -1800,12 +1800,12 @@ int hgp_get_lambda(hgp_handle *h, uint64_t *lam)
     Dev &d = h->d;
     if (d.m == 0) return HGP_OK;
     uint64_t *tmp = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(uint64_t) * (size_t)d.m, h->stream));
+    CK(dev_alloc(reinterpret_cast<void **>(&tmp), sizeof(uint64_t) * (size_t)d.m, h->stream));
     if (d.k <= 32) { k_get_lambda<Rec16><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp); h->launches++; }
     else { k_get_lambda<Rec32><<<grid_for(d.m, 256), 256, 0, h->stream>>>(d, tmp); h->launches++; }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, tmp, sizeof(uint64_t) * (size_t)d.m, cudaMemcpyDeviceToHost, h->stream);
-    cudaFreeAsync(tmp, h->stream);
+    pool_free(tmp, h->stream);
     if (e == cudaSuccess) e = stream_wait(h->stream);
     CK(e);
     return HGP_OK;
