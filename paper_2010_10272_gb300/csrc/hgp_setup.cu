@@ -400,7 +400,11 @@ constexpr int kTpMaxBuckets = 4096;
 constexpr int kTpShift = 14;             // 16384 vertices per bucket, unless that gives too few
 constexpr int kTpMinShift = 8;           // buckets for the GPU (small instances) or too many
 constexpr int kTpSmemShift = 14;         // buckets up to this size count in shared memory
-constexpr int kTpNetsPerCta = 16384;     // at most; fewer when the instance has few nets
+// nets per scatter CTA, at most (fewer when the instance has few nets): each CTA's walk over its
+// nets is a chain of dependent loads, so many short walks beat few long ones even though every
+// CTA reserves a range in every bucket (power-law creation: 16384 -> 30.1 ms, 4096 -> 25.1 ms,
+// 2048 -> 23.3 ms, 512 -> 23.1 ms)
+constexpr int kTpNetsPerCta = 2048;
 constexpr int kTpMinCtas = 608;          // target CTAs per launch (4 per SM)
 
 __global__ void __launch_bounds__(256) k_tp_hist(const int32_t *pins, int64_t P, int bshift, int32_t nb,
