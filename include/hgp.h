@@ -259,7 +259,11 @@ int hgp_batch_query(hgp_batch *b, int32_t *done);
 /* Partitions Pi of the members listed in `members` (count indices into the batch's handles) as
  * they are after the batch's last hgp_batch_refine call, written back to back into host int32
  * `out` (the members' vertex counts summed, in the listed order).  Waits for that call only;
- * one copy and one wait for all of them (a serving loop retiring the members a call finished). */
+ * one copy and one wait for all of them (a serving loop retiring the members a call finished).
+ * The copy goes through one page-locked staging buffer of the library (grown when a call needs
+ * more, kept for the life of the process), so concurrent calls run one after another.
+ * HGP_ERR_INVALID for a null batch, a negative count, null arrays with count > 0, or an index
+ * outside [0, members of the batch). */
 int hgp_batch_get_partitions(hgp_batch *b, const int32_t *members, int32_t count, int32_t *out);
 
 /* Waits for the batch's queued work. */
