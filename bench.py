@@ -204,6 +204,21 @@ def traffic_from_profile(kernel: str, workload: str, phi_width: int):
     return float(m.group(1))
 
 
+def set_l2_fetch_granularity(nbytes: int):
+    """Measurement option: the current context's maximum L2 fetch granularity (32..128 bytes;
+    CU_LIMIT_MAX_L2_FETCH_GRANULARITY through the driver API).  It lasts as long as the
+    context, i.e. this process, and applies to every kernel in it."""
+    import ctypes
+    import torch
+    torch.zeros(1, device="cuda")                 # the context exists from here on
+    cuda = ctypes.CDLL("libcuda.so.1")
+    rc = cuda.cuCtxSetLimit(ctypes.c_int(5), ctypes.c_size_t(int(nbytes)))
+    got = ctypes.c_size_t(0)
+    cuda.cuCtxGetLimit(ctypes.byref(got), ctypes.c_int(5))
+    if rc != 0 or got.value != nbytes:
+        raise RuntimeError(f"could not set the L2 fetch granularity to {nbytes} (rc {rc}, now {got.value})")
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -294,6 +309,8 @@ def run_gpu(args, world, rank, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.l2_fetch_granularity:
+        set_l2_fetch_granularity(args.l2_fetch_granularity)
 
     t_gen = time.perf_counter()
     hg = load_instance(args.workload, args.scale)
@@ -968,6 +985,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-pool-retention", type=int, default=64 << 30,
                     help="device bytes the library's pool keeps between end-to-end steps (0: none)")
+    ap.add_argument("--l2-fetch-granularity", type=int, default=0,
+                    help="measurement option: the context's maximum L2 fetch granularity in bytes (0: default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
