@@ -211,15 +211,17 @@ class Server:
         """The partitions of the requests a tick finished, read with one copy
         (hgp_batch_get_partitions), then the tick's batch and the requests' device state
         released (queued on each request's own stream, behind the batch)."""
-        parts = batch.partitions(slots) if slots else [h.partition() for h in handles]
-        now = self.clock()
-        for req, part, h in zip(reqs, parts, handles):
-            req.result = part
-            req.finished = now
-            req.objective = int(req.stats[-1][0]) if len(req.stats) else h.objective()
-        batch.close()
-        for h in handles:
-            h.close()
+        try:
+            parts = batch.partitions(slots) if slots else [h.partition() for h in handles]
+            now = self.clock()
+            for req, part, h in zip(reqs, parts, handles):
+                req.result = part
+                req.finished = now
+                req.objective = int(req.stats[-1][0]) if len(req.stats) else h.objective()
+        finally:                                # released even when a read-back fails
+            batch.close()
+            for h in handles:
+                h.close()
 
     def _install(self, req: Request, h: HGP):
         req.admitted = self.clock()
