@@ -105,18 +105,6 @@ __global__ void k_scan_final(const int32_t *in, int32_t *out, int64_t count, con
 }
 
 // ------------------------------------------------------------------ validation
-__global__ void k_check_offsets(const int64_t *off64, int32_t *off32, int32_t m, int64_t P, int32_t *err)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = off64[e];
-        bool bad = (e == 0 && a != 0) || (e == m && a != P) || a < 0 || a > P;
-        if (e < m && off64[e + 1] < a) bad = true;
-        if (bad) atomicOr(err, ERR_INVALID);
-        off32[e] = (int32_t)(a < 0 ? 0 : (a > P ? P : a));
-    }
-}
-
 // warp per net: pins in range and strictly increasing; largest net size
 // Warp-wide: the pins of nets e0 .. e0 + 31 (clipped to e_hi) are contiguous; off33 receives
 // their exclusive offsets inside that run (off33[32] = its length) and the run's first pin index
@@ -150,7 +138,7 @@ __device__ __forceinline__ int pin_net(const int32_t *off33, int32_t i)
 }
 
 // pins in [0, n) and strictly increasing inside every net; the largest net size.  Runs after
-// k_check_offsets and does nothing if that found an error.  A warp walks 32 nets' pins at once,
+// k_check_inputs and does nothing if that found an error.  A warp walks 32 nets' pins at once,
 // coalesced.
 __global__ void __launch_bounds__(256) k_check_pins(const int32_t *off, const int32_t *pins, int32_t m, int32_t n,
                                                     int32_t *err, int32_t *max_size)
@@ -311,15 +299,6 @@ __global__ void k_check_vertices(const int32_t *vw, const int32_t *part_in, int3
     if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
 }
 
-__global__ void k_check_nets(const int32_t *nw, int32_t m, int32_t *err)
-{
-    bool bad = false;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x)
-        if (nw[e] < 1) bad = true;
-    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
-}
-
 // Creation queues its kernels behind the input checks without waiting for their verdict (for
 // instances whose net sizes the host reads itself, see create_impl): every kernel that indexes
 // by a pin, a vertex id or a block then returns at once when the checks flagged the input, and
@@ -328,6 +307,32 @@ __global__ void k_check_nets(const int32_t *nw, int32_t m, int32_t *err)
 __device__ __forceinline__ bool input_invalid(const int32_t *guard)
 {
     return guard && (*reinterpret_cast<const volatile int32_t *>(guard) & ERR_INVALID) != 0;
+}
+
+// The creation's checks of the offsets (converted to int32 on the way), the net and vertex
+// weights and the partition in one launch; the valid partition entries are stored as the 1-byte
+// Pi at the same time.
+__global__ void k_check_inputs(const int64_t *off64, int32_t *off32, int32_t m, int64_t P, const int32_t *nw,
+                               const int32_t *vw, const int32_t *part_in, int32_t n, int32_t k, uint8_t *part,
+                               int32_t *err)
+{
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e <= m; e += stride) {
+        const int64_t a = off64[e];
+        if ((e == 0 && a != 0) || (e == m && a != P) || a < 0 || a > P) bad = true;
+        if (e < m && off64[e + 1] < a) bad = true;
+        if (e < m && nw && nw[e] < 1) bad = true;
+        off32[e] = (int32_t)(a < 0 ? 0 : (a > P ? P : a));
+    }
+    for (int64_t v = t0; v < n; v += stride) {
+        if (vw && vw[v] < 1) bad = true;
+        const int32_t p = part_in[v];
+        if (p < 0 || p >= k) bad = true;
+        else part[v] = (uint8_t)p;
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_INVALID);
 }
 
 // ------------------------------------------------------------------ per-vertex net weight
@@ -1271,9 +1276,10 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.nw = nw_d;
 
     // ---- validation
-    k_check_offsets<<<grid_for((int64_t)m + 1, 256), 256, 0, st>>>(off64, net_off, m, P, d.err); h->launches++;
-    k_check_vertices<<<grid_for(n, 256), 256, 0, st>>>(vw_d, part_in, n, k, d.err); h->launches++;
-    if (nw_d) { k_check_nets<<<grid_for(m, 256), 256, 0, st>>>(nw_d, m, d.err); h->launches++; }
+    uint8_t *part = nullptr;
+    CKF(dalloc(h, &part, n));
+    k_check_inputs<<<grid_for(std::max<int64_t>((int64_t)m + 1, n), 256), 256, 0, st>>>(
+        off64, net_off, m, P, nw_d, vw_d, part_in, n, k, part, d.err); h->launches++;
     CKF(cudaGetLastError());
     int32_t host_err[2] = {0, 0};
     // one read-back for both checks: the pin check does nothing when the offsets were bad
@@ -1433,17 +1439,13 @@ int create_impl(int32_t n, int32_t m, const int64_t *net_offsets, const int32_t 
     d.vtx_off = vtx_off;
     d.inc = inc;
 
-    unsigned long long *maxw_d = reinterpret_cast<unsigned long long *>(misc32 + 2);
-    CKF(cudaMemsetAsync(maxw_d, 0, sizeof(unsigned long long), st));
+    unsigned long long *maxw_d = reinterpret_cast<unsigned long long *>(misc32 + 2);   // zeroed with misc32
     // the result of this check is read with the block weights at the end (nothing in between
     // depends on it)
     k_vertex_netweight<<<grid_for(n, 256), 256, 0, st>>>(vtx_off, inc, nw_d, n, d.err, maxw_d); h->launches++;
     CKF(cudaGetLastError());
 
-    // ---- state
-    uint8_t *part = nullptr;
-    CKF(dalloc(h, &part, n));
-    k_copy_part<<<grid_for(n, 256), 256, 0, st>>>(part_in, part, n); h->launches++;
+    // ---- state (Pi was stored by the input check)
     d.part = part;
     const int64_t entries = (int64_t)m * k;
     const int64_t words = (entries * w + 3) / 4;
